@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the Lottery BP + OSD-0 decoder on GB300.
+
+One step = one pass of the whole decoding path (BP with the lottery on every
+shot, OSD-0 on the shots BP leaves unconverged) over one batch of seeded
+synthetic syndromes of the rotated d=11 surface code with 11 noisy rounds
+(space-time H 660 x 1931, nnz 3620), p_data = p_meas = 0.003, 10^6 shots,
+max 100 iterations, binary32 messages.
+
+Prints one JSON line (rank 0).  `value` is decoded shots per second over all
+ranks with inputs resident in HBM; `e2e` is the same through the host-buffer
+entry point with the copies inside the timed region.  `--impl reference`
+times the CPU oracle instead (on a bounded sample of the same workload).
+Under torchrun each rank decodes its own shots (weak scaling; no data-path
+collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "decoded shots/sec and p99 decode latency at matched logical error rate; HBM GB/s"
+UNIT = "shots/s"
+N_BATCHES = 3        # rotating input batches: 3 x 88 MB of syndromes > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--shots", type=int, default=1_000_000, help="shots per step per rank")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle shots for cpu_baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(shots):
+    from paper_2605_00038_gb300.inputs import workloads
+    return workloads.c2_d11_spacetime(shots=shots, osd=1)
+
+
+def roofline_model(w, iters_total, shots):
+    """Algorithmic work of K_bp ('Roofline'): per shot-iteration
+    8 E + 2 m + n operations; per shot the syndrome in and results out."""
+    E, m, n = w.h.nnz, w.h.m, w.h.n
+    ops = float(iters_total) * (8 * E + 2 * m + n)
+    io = shots * (8 * ((m + 63) // 64) + 8 * ((n + 63) // 64) + 1 + 1 + 4)
+    return ops, io
+
+
+def alu_peak_ops(sm_mhz):
+    # 152 SMs x 4 sub-partitions x 32 lanes, one instruction per lane per clock.
+    return 152 * 4 * 32 * sm_mhz * 1e6
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2605_00038_gb300.inputs import sampler
+    w = workload(args.shots)
+    cores = os.cpu_count() or 1
+    sample = max(1, min(args.cpu_sample, w.shots))
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=sample)
+    S = sampler.unpack(syn, w.h.m)
+    prm = oracle.OracleParams(max_iter=100, lottery=True, lottery_skip=6, osd=True,
+                              prec=oracle.PREC_F64, seed=w.seed)
+    for _ in range(args.warmup):
+        oracle.decode(w.h, w.priors, S[: max(1, sample // 20)], prm, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.decode(w.h, w.priors, S, prm, nthreads=cores)
+    dt = time.perf_counter() - t0
+    v = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "shots_per_step": sample, "decoder": "lottery_bp+osd0",
+                   "max_iter": 100, "parallelism": "cpu threads"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d shots of %s per step (FP64 oracle, %d threads)"
+                                   % (sample, w.name, cores)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def logical_failures(w, err_words, est_words, conv, osd):
+    """Logical failure per shot: the residual's data part, summed over rounds,
+    hits a logical operator; or BP did not converge and OSD did not apply."""
+    import torch
+    from paper_2605_00038_gb300.inputs.codes import logical_operators, rotated_surface
+    hz, hx = rotated_surface(11)
+    L = torch.from_numpy(logical_operators(hz, hx).astype(np.float32)).cuda()
+    T, nq = 11, hz.n
+    fails = 0
+    B = err_words.shape[0]
+    shifts = torch.arange(64, device="cuda", dtype=torch.int64)
+    for lo in range(0, B, 50_000):
+        r = torch.bitwise_xor(err_words[lo:lo + 50_000], est_words[lo:lo + 50_000])
+        bits = torch.bitwise_and(torch.bitwise_right_shift(r.unsqueeze(-1), shifts), 1)
+        bits = bits.reshape(r.shape[0], -1)[:, : w.h.n]
+        data = bits[:, : T * nq].reshape(-1, T, nq).sum(1).remainder(2).float()
+        hit = (data @ L.T).remainder(2).sum(1) > 0
+        bad = (conv[lo:lo + 50_000] == 0) & (osd[lo:lo + 50_000] != 1)
+        fails += int((hit | bad).sum().item())
+    return fails
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_00038_gb300 import lbp
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler
+
+    w = workload(args.shots)
+    B = w.shots
+    dec = Decoder(w.h, w.priors, device="cuda:%d" % local)
+    wm, wn = (w.h.m + 63) // 64, (w.h.n + 63) // 64
+
+    # Inputs: N_BATCHES distinct batches per rank, resident on the device.
+    syn_h, err_h, syn_d, prms = [], [], [], []
+    for k in range(N_BATCHES):
+        off = (rank * N_BATCHES + k) * B
+        e, s = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=B, shot_offset=off)
+        err_h.append(e)
+        syn_h.append(s)
+        syn_d.append(torch.from_numpy(s.view(np.int64)).cuda())
+        prms.append(dec.params(**w.decoder, seed=w.seed, shot_offset=off))
+    outs = [dec.alloc(B) for _ in range(N_BATCHES)]
+    ws = dec.workspace(prms[0], B)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        lbp.lbp_decode(dec.code, prms[k % N_BATCHES], B, syn_d[k % N_BATCHES], outs[k % N_BATCHES].err,
+                       outs[k % N_BATCHES].converged, outs[k % N_BATCHES].osd,
+                       outs[k % N_BATCHES].iters, None, ws, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    lbp.lbp_timing_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    ev1.record(stream)
+    barrier()
+    clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    bp_ms, bp_n, osd_ms, osd_n = lbp.lbp_timing_read()
+    lbp.lbp_timing_enable(False)
+    t = torch.tensor([elapsed_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * B * args.steps / (max_ms / 1e3)
+
+    # Work actually done in the timed steps (iterations, OSD invocations).
+    iters_total = 0
+    osd_total = 0
+    for k in range(args.steps):
+        o = outs[k % N_BATCHES]
+        iters_total += int(o.iters.sum().item())
+        osd_total += int((o.osd != 0).sum().item())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "code": "rotated surface d=11, 11 rounds, H_st 660x1931 nnz 3620",
+                   "noise": "iid p_data=p_meas=0.003", "shots_per_step_per_rank": B,
+                   "decoder": "lottery_bp(skip 6, adaptive scale, I=100) + osd0",
+                   "msg": "f32", "l2": "3 rotating input batches (%d MB syndromes) > L2" % (
+                       N_BATCHES * B * wm * 8 // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "clocks": clocks.summary(),
+        "gpu_launches": int(bp_n + osd_n),
+    }
+    sm_mhz = line["clocks"]["sm_mhz"] or 2070.0
+    ops, io = roofline_model(w, iters_total / args.steps, B)
+    bp_avg_s = bp_ms / max(bp_n, 1) / 1e3
+    peak = alu_peak_ops(sm_mhz)
+    line["roofline"] = {"bound": "alu", "achieved": ops / bp_avg_s / 1e12, "peak": peak / 1e12,
+                        "unit": "Tops/s", "frac": (ops / bp_avg_s) / peak, "traffic": None,
+                        "kernel": "bp_kernel", "avg_launch_ms": bp_avg_s * 1e3,
+                        "ops_per_launch": ops, "io_bytes_per_launch": io,
+                        "io_gbs": io / bp_avg_s / 1e9,
+                        "peak_basis": "152 SMs x 128 lanes x median SM clock %.0f MHz" % sm_mhz}
+    line["kernels"] = {"bp_ms_per_step": bp_ms / args.steps, "osd_ms_per_step": osd_ms / args.steps,
+                       "mean_iters": iters_total / (B * args.steps),
+                       "osd_invoke_rate": osd_total / (B * args.steps)}
+
+    # End to end through the host-buffer entry point (pinned memory).
+    if not args.no_e2e:
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+        hs = []
+        for k in range(N_BATCHES):
+            p = pin(syn_h[k].shape, torch.int64)
+            p.numpy()[:] = syn_h[k].view(np.int64)
+            hs.append(p)
+        ho = dict(err=pin((B, wn), torch.int64), converged=pin(B, torch.uint8), osd=pin(B, torch.uint8),
+                  iters=pin(B, torch.int32))
+        hws = dec.workspace(prms[0], B, host=True)
+
+        def hstep(k):
+            lbp.lbp_decode_host(dec.code, prms[k % N_BATCHES], B, hs[k % N_BATCHES], ho["err"],
+                                ho["converged"], ho["osd"], ho["iters"], None, hws, stream)
+
+        hstep(0)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            hstep(k)
+        e1.record(stream)
+        barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * B * args.steps / (float(t.item()) / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": B * wm * 8,
+                       "d2h_bytes_per_step": B * (wn * 8 + 1 + 1 + 4)}
+
+    if not args.no_extras and rank == 0:
+        # Per-batch latency at small batch sizes (outside the timed region).
+        lat = {}
+        for bs in (1, 64, 4096):
+            sub = syn_d[0][:bs].contiguous()
+            o = dec.alloc(bs)
+            wsb = dec.workspace(prms[0], bs)
+            times = []
+            for r in range(60):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lbp.lbp_decode(dec.code, prms[0], bs, sub, o.err, o.converged, o.osd, o.iters, None,
+                               wsb, stream)
+                b.record(stream)
+                b.synchronize()
+                if r >= 10:
+                    times.append(a.elapsed_time(b))
+            times.sort()
+            lat["batch_%d" % bs] = {"p50_ms": times[len(times) // 2],
+                                    "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))]}
+        lat["batch_%d" % B] = {"p50_ms": line["ms_per_step"], "p99_ms": None}
+        line["latency"] = lat
+        # Logical error rate of batch 0 (true errors known from the sampler).
+        o = outs[0]
+        step(0)
+        torch.cuda.synchronize()
+        fails = logical_failures(w, torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err,
+                                 o.converged, o.osd)
+        line["quality"] = {"ler": fails / B, "shots": B, "logical_failures": fails}
+
+    if not args.no_extras and rank == 0 and world == 1:
+        import oracle
+        cores = os.cpu_count() or 1
+        S = sampler.unpack(syn_h[0][: args.cpu_sample], w.h.m)
+        prm = oracle.OracleParams(max_iter=100, lottery=True, lottery_skip=6, osd=True,
+                                  prec=oracle.PREC_F64, seed=w.seed, shot_offset=0)
+        t0 = time.perf_counter()
+        oracle.decode(w.h, w.priors, S, prm, nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d shots of %s (FP64 oracle, %d threads, %.1f s)"
+                                          % (S.shape[0], w.name, cores, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dec.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

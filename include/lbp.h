@@ -1,0 +1,156 @@
+/* lbp.h — C ABI of the GB300 Lottery BP (+ OSD-0) syndrome decoder.
+ *
+ * The library decodes batches of syndromes s of one sparse GF(2) check
+ * matrix H (m checks x n columns) into error estimates e_hat with
+ * H e_hat = s (mod 2) when decoding succeeds.  The problem statement is the
+ * one of Alg. 1 (inputs H, max iterations I, error rates p, syndrome s;
+ * output e_hat) and of Alg. 2 (inputs H, BP output LLRs, s; output the
+ * OSD-0 estimate), Sec. II-B and Sec. III-B of the paper.
+ *
+ * Conventions for every call:
+ *  - Plain pointers and sizes only.  "device" pointers address memory of the
+ *    current CUDA device; "host" pointers ordinary (preferably pinned) host
+ *    memory.  The caller owns every buffer it passes and the stream.
+ *  - Bits pack little-endian into 64-bit words: bit j of word w is index
+ *    64 w + j; bits past the end of a row are zero on output and ignored on
+ *    input.
+ *  - Calls that take a stream only enqueue work on it (asynchronous); the
+ *    caller synchronises.  lbp_load_code and lbp_free_code are synchronous.
+ *  - Return value 0 on success, a negative LBP_E* code otherwise; nothing is
+ *    enqueued when an argument check fails.  No C++ exception crosses the ABI.
+ *  - A code object is bound to the device that was current at load time and
+ *    may be used from several host threads at once (it is read-only after
+ *    load); a workspace must not be shared by two calls in flight.
+ */
+#ifndef LBP_H
+#define LBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBP_OK          0
+#define LBP_EINVAL    (-22)   /* malformed H, priors, parameters or sizes */
+#define LBP_ENOMEM    (-12)   /* device allocation failed, or workspace too small */
+#define LBP_ENOSYS    (-38)   /* this code / precision combination is not supported */
+#define LBP_ECUDA     (-5)    /* a CUDA runtime call failed */
+
+/* Per-shot OSD status written to osd_out. */
+#define LBP_OSD_NOT_RUN     0  /* BP converged, or OSD disabled */
+#define LBP_OSD_APPLIED     1  /* OSD-0 estimate replaced the BP estimate */
+#define LBP_OSD_NO_SOLUTION 2  /* s is outside the column space of H; BP estimate kept */
+
+/* Storage type of the check-to-variable messages beta (Alg. 1 CN update).
+ * Arithmetic is binary32 in every mode; channel LLRs mu and posteriors
+ * lambda stay binary32 (Sec. VI-C quantisation study). */
+#define LBP_MSG_F32 0          /* IEEE binary32 */
+#define LBP_MSG_F16 1          /* IEEE binary16, round to nearest even */
+#define LBP_MSG_I8  2          /* Int3.4 fixed point: q = clamp(rne(16 x), -127, 127), value q/16 */
+
+/* Normalisation factor of the min-sum CN update. */
+#define LBP_SCALE_CONST    0   /* scale_const at every iteration */
+#define LBP_SCALE_ADAPTIVE 1   /* 1 - 2^-(i+1) at iteration i (Alg. 1) */
+
+typedef struct lbp_code lbp_code;   /* opaque, device-resident Tanner graph + mu */
+
+typedef struct {
+    int32_t  max_iter;      /* I >= 1 (Alg. 1); at most 2^24 - 1 */
+    int32_t  scale_mode;    /* LBP_SCALE_* */
+    float    scale_const;   /* used when scale_mode == LBP_SCALE_CONST, in (0, 1] */
+    int32_t  lottery;       /* 1: apply the lottery sign flip of Alg. 3 */
+    int32_t  lottery_skip;  /* first iteration index (0-based) at which it may run; 6 in Sec. III-B */
+    int32_t  osd;           /* 1: OSD-0 (Alg. 2) on shots BP did not converge on */
+    int32_t  msg;           /* LBP_MSG_* */
+    int32_t  reserved;      /* must be 0 */
+    uint64_t seed;          /* key of the lottery's random draws */
+    uint64_t shot_offset;   /* global index of shot 0 of this call: the draws of shot b
+                               depend only on (seed, shot_offset + b), never on batching */
+} lbp_params;
+
+/* Fill *p with the paper's Lottery BP defaults: I = 100, adaptive scale,
+ * lottery on with skip 6, OSD off, binary32 messages, seed 0. */
+void lbp_params_default(lbp_params *p);
+
+/* Load the check matrix H and the per-column error probabilities p_v.
+ *
+ * H is given in CSR form on the host: row_ptr[m+1] (row_ptr[0] = 0,
+ * nondecreasing, row_ptr[m] = nnz), col_idx[nnz] strictly increasing within
+ * each row, each in [0, n).  A row with exactly one nonzero is rejected
+ * (its exclusive minimum in the CN update would range over an empty set);
+ * rows with more than 32 nonzeros are rejected.  priors[n] are p_v in (0, 1);
+ * the prior LLR mu_v = ln((1 - p_v) / p_v) (Alg. 1) is computed in binary64
+ * on the host and rounded once to binary32.
+ *
+ * The library copies what it needs (host buffers may be freed on return),
+ * allocates the device-resident graph with cudaMalloc on the current device
+ * and returns an opaque handle in *out.  Errors: LBP_EINVAL, LBP_ENOMEM,
+ * LBP_ECUDA; *out is set to NULL on error. */
+int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                  const double *priors, lbp_code **out);
+
+/* Release a code object (synchronous; no call using it may be in flight). */
+int lbp_free_code(lbp_code *code);
+
+/* Sizes of a loaded code (any pointer may be NULL). */
+int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
+
+/* Bytes of device workspace lbp_decode needs for num_shots shots with these
+ * parameters (0 on invalid input).  The size grows linearly with num_shots
+ * only when params->osd is set (the LLRs of shots handed to OSD). */
+size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
+
+/* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).
+ *
+ * Device buffers, all [num_shots][...] row-major:
+ *   syndromes   in   [B][ceil(m/64)] uint64, packed s
+ *   err_out     out  [B][ceil(n/64)] uint64, packed e_hat
+ *   converged   out  [B] uint8: 1 iff BP reached s_hat == s (early termination)
+ *   osd_out     out  [B] uint8: LBP_OSD_* status (may be NULL)
+ *   iters_out   out  [B] int32: BP iterations executed (i + 1 at convergence, else I)
+ *   llr_out     out  [B][n] float: final posterior lambda (may be NULL)
+ *   workspace        lbp_workspace_size() bytes, 256-byte aligned, owned by the
+ *                    caller; contents on entry are ignored.
+ * Shot b's result depends only on its syndrome, the code, the parameters and
+ * shot_offset + b (not on num_shots or on other shots).  Errors: LBP_EINVAL,
+ * LBP_ENOMEM (workspace too small), LBP_ENOSYS, LBP_ECUDA. */
+int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+               const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+               uint8_t *osd_out, int32_t *iters_out, float *llr_out,
+               void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of device workspace lbp_decode_host needs: lbp_workspace_size plus
+ * device staging for the inputs and outputs.  When llr_out is requested the
+ * call needs 4 * n * num_shots more bytes, rounded up to a multiple of 256. */
+size_t lbp_host_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
+
+/* Same as lbp_decode with HOST buffers (same shapes; llr_out and osd_out may
+ * be NULL): enqueues the host-to-device copy of the syndromes, the decode and
+ * the device-to-host copies of the results on `stream`, using `workspace`
+ * (device, lbp_host_workspace_size bytes) for staging.  Pinned host memory
+ * makes the copies asynchronous; the caller synchronises the stream before
+ * reading the outputs. */
+int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+                    const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                    uint8_t *osd_out, int32_t *iters_out, float *llr_out,
+                    void *workspace, size_t workspace_bytes, void *stream);
+
+/* Kernel timing instrumentation, off by default.  While enabled, every
+ * decode records a CUDA event pair on its stream around each kernel launch
+ * (the BP kernel, K_bp, and the OSD kernel, K_osd); lbp_timing_read waits for
+ * the recorded events, returns the summed milliseconds and launch counts
+ * since the last read, and forgets them.  Enabling or disabling also forgets
+ * them.  Any output pointer may be NULL.  Thread-safe; meant for benchmarks. */
+int lbp_timing_enable(int on);
+int lbp_timing_read(double *bp_ms, int64_t *bp_launches, double *osd_ms, int64_t *osd_launches);
+
+/* Static text for an LBP_* code. */
+const char *lbp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBP_H */

@@ -70,7 +70,7 @@ def build_lbp(force: bool = False, verbose_ptxas: bool = False) -> Path:
         cmds.append(cmd)
     _run(cmds)
     tmp = LIBLBP.with_suffix(".so.tmp")
-    _run([[nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart", "-lpthread"]])
+    _run([[nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lpthread"]])
     os.replace(tmp, LIBLBP)
     return LIBLBP
 

@@ -1,0 +1,43 @@
+// Internal definitions shared by the host and device parts of liblbp.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lbp.h"
+
+namespace lbp {
+
+constexpr int kMaxRowDeg = 32;      // a check's neighbours fit one warp / one 32-bit mask
+constexpr int kMaxIter = (1 << 24) - 1;
+
+// Byte offsets of the compact graph image that each decoding CTA copies into
+// shared memory.  All index arrays are uint16 (the image exists only when
+// m, n and nnz are all below 65536); mu is binary32.
+struct GraphImage {
+    uint32_t bytes;          // total, a multiple of 16
+    uint32_t off_row_ptr;    // u16[m+1]   CSR row starts
+    uint32_t off_col_idx;    // u16[nnz]   CSR column of each edge
+    uint32_t off_col_ptr;    // u16[n+1]   CSC column starts
+    uint32_t off_csc_edge;   // u16[nnz]   CSR edge id of each CSC entry (rows ascending)
+    uint32_t off_csc_row;    // u16[nnz]   check of each CSC entry
+    uint32_t off_mu;         // f32[n]     prior LLR
+};
+
+}  // namespace lbp
+
+struct lbp_code {
+    int device;
+    int sm_count;
+    int smem_optin;          // max dynamic shared memory per block
+    int32_t m, n, nnz;
+    int32_t max_row_deg, max_col_deg;
+    // Compact image (device), NULL when the sizes do not fit 16-bit indices.
+    uint8_t *d_image;
+    lbp::GraphImage img;
+    // 32-bit device copies, used by OSD.
+    int32_t *d_row_ptr, *d_col_idx;
+    float *d_mu;
+};

@@ -1,0 +1,163 @@
+// Host side of lbp_load_code / lbp_free_code and the small helpers of lbp.h.
+//
+// lbp_load_code validates H (CSR), derives the variable-major (CSC) view the
+// LLR update walks, computes the prior LLR mu_v = ln((1 - p_v) / p_v) of
+// Alg. 1 in binary64 and rounds it to binary32, and uploads a compact 16-bit
+// image of the whole Tanner graph that the decode kernels stage into shared
+// memory once per CTA.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+void release(lbp_code *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaFree(c->d_image);
+    cudaFree(c->d_row_ptr);
+    cudaFree(c->d_col_idx);
+    cudaFree(c->d_mu);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" void lbp_params_default(lbp_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->max_iter = 100;
+    p->scale_mode = LBP_SCALE_ADAPTIVE;
+    p->scale_const = 0.625f;
+    p->lottery = 1;
+    p->lottery_skip = 6;
+    p->osd = 0;
+    p->msg = LBP_MSG_F32;
+}
+
+extern "C" const char *lbp_strerror(int code) {
+    switch (code) {
+        case LBP_OK: return "success";
+        case LBP_EINVAL: return "invalid argument (malformed H, priors, parameters or sizes)";
+        case LBP_ENOMEM: return "out of device memory or workspace too small";
+        case LBP_ENOSYS: return "code / precision combination not supported";
+        case LBP_ECUDA: return "CUDA runtime error";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                             const double *priors, lbp_code **out) {
+    if (!out) return LBP_EINVAL;
+    *out = nullptr;
+    if (m < 0 || n < 0 || !row_ptr || (n > 0 && !priors)) return LBP_EINVAL;
+    if (row_ptr[0] != 0) return LBP_EINVAL;
+    int maxdeg = 0;
+    for (int32_t c = 0; c < m; ++c) {
+        const int32_t a = row_ptr[c], b = row_ptr[c + 1];
+        if (b < a) return LBP_EINVAL;
+        const int32_t deg = b - a;
+        if (deg == 1 || deg > lbp::kMaxRowDeg) return LBP_EINVAL;
+        for (int32_t e = a; e < b; ++e) {
+            if (!col_idx || col_idx[e] < 0 || col_idx[e] >= n) return LBP_EINVAL;
+            if (e > a && col_idx[e] <= col_idx[e - 1]) return LBP_EINVAL;
+        }
+        if (deg > maxdeg) maxdeg = deg;
+    }
+    const int32_t nnz = row_ptr[m];
+    for (int32_t v = 0; v < n; ++v)
+        if (!(priors[v] > 0.0 && priors[v] < 1.0)) return LBP_EINVAL;
+
+    // Variable-major view: per column, its checks in ascending row order and
+    // the CSR edge holding each message.
+    std::vector<int32_t> col_ptr(static_cast<size_t>(n) + 1, 0), csc_row(nnz), csc_edge(nnz);
+    for (int32_t e = 0; e < nnz; ++e) col_ptr[col_idx[e] + 1]++;
+    int maxcol = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        if (col_ptr[v + 1] > maxcol) maxcol = col_ptr[v + 1];
+        col_ptr[v + 1] += col_ptr[v];
+    }
+    {
+        std::vector<int32_t> fill(n, 0);
+        for (int32_t c = 0; c < m; ++c)
+            for (int32_t e = row_ptr[c]; e < row_ptr[c + 1]; ++e) {
+                const int32_t v = col_idx[e];
+                const int32_t k = col_ptr[v] + fill[v]++;
+                csc_row[k] = c;
+                csc_edge[k] = e;
+            }
+    }
+    // Alg. 1 prior LLR, binary64 then one rounding to binary32.
+    std::vector<float> mu(n);
+    for (int32_t v = 0; v < n; ++v) mu[v] = static_cast<float>(std::log((1.0 - priors[v]) / priors[v]));
+
+    lbp_code *c = new (std::nothrow) lbp_code();
+    if (!c) return LBP_ENOMEM;
+    std::memset(c, 0, sizeof(*c));
+    c->m = m; c->n = n; c->nnz = nnz;
+    c->max_row_deg = maxdeg; c->max_col_deg = maxcol;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LBP_ECUDA; }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> int {
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) { cudaGetLastError(); return LBP_ENOMEM; }
+        if (src && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return LBP_ECUDA;
+        return LBP_OK;
+    };
+    int rc = upload(reinterpret_cast<void **>(&c->d_row_ptr), row_ptr, sizeof(int32_t) * (static_cast<size_t>(m) + 1));
+    if (rc == LBP_OK && nnz > 0) rc = upload(reinterpret_cast<void **>(&c->d_col_idx), col_idx, sizeof(int32_t) * nnz);
+    if (rc == LBP_OK) rc = upload(reinterpret_cast<void **>(&c->d_mu), n ? mu.data() : nullptr, sizeof(float) * n);
+
+    // Compact 16-bit image for shared-memory staging.
+    if (rc == LBP_OK && m < 65535 && n < 65535 && nnz < 65535) {
+        lbp::GraphImage &g = c->img;
+        uint32_t off = 0;
+        g.off_row_ptr = off;  off = align16(off + 2u * (m + 1));
+        g.off_col_idx = off;  off = align16(off + 2u * nnz);
+        g.off_col_ptr = off;  off = align16(off + 2u * (n + 1));
+        g.off_csc_edge = off; off = align16(off + 2u * nnz);
+        g.off_csc_row = off;  off = align16(off + 2u * nnz);
+        g.off_mu = off;       off = align16(off + 4u * n);
+        g.bytes = off;
+        std::vector<uint8_t> img(off, 0);
+        auto put16 = [&](uint32_t base, const int32_t *src, size_t cnt) {
+            uint16_t *d = reinterpret_cast<uint16_t *>(img.data() + base);
+            for (size_t i = 0; i < cnt; ++i) d[i] = static_cast<uint16_t>(src[i]);
+        };
+        put16(g.off_row_ptr, row_ptr, static_cast<size_t>(m) + 1);
+        put16(g.off_col_idx, col_idx, nnz);
+        put16(g.off_col_ptr, col_ptr.data(), static_cast<size_t>(n) + 1);
+        put16(g.off_csc_edge, csc_edge.data(), nnz);
+        put16(g.off_csc_row, csc_row.data(), nnz);
+        if (n) std::memcpy(img.data() + g.off_mu, mu.data(), 4u * n);
+        rc = upload(reinterpret_cast<void **>(&c->d_image), img.data(), off);
+    }
+    if (rc != LBP_OK) { release(c); return rc; }
+    *out = c;
+    return LBP_OK;
+}
+
+extern "C" int lbp_free_code(lbp_code *code) {
+    if (!code) return LBP_EINVAL;
+    release(code);
+    return LBP_OK;
+}
+
+extern "C" int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz) {
+    if (!code) return LBP_EINVAL;
+    if (m) *m = code->m;
+    if (n) *n = code->n;
+    if (nnz) *nnz = code->nnz;
+    return LBP_OK;
+}

@@ -1,0 +1,335 @@
+// lbp_decode / lbp_decode_host: launch planning for K_bp and K_osd.
+//
+// K_bp runs persistent: one CTA per SM, S groups of G threads per CTA, the
+// graph image plus S shots' state in shared memory.  S and G are chosen here
+// from the shared-memory budget (the largest S that fits, then the widest G
+// that keeps S * G <= 1024 threads).  K_osd follows on the same stream and
+// drains the queue K_bp filled; no host round trip separates them.
+//
+// Workspace (caller-owned device memory), 256-byte aligned sections:
+//   counters   u32[64]  [0] next shot, [1] OSD queue length
+//   osd_list   u32[B]   shots handed to OSD            (osd only)
+//   osd_llr    f32[B][n] their final lambda            (osd only)
+//   osd_mat    u64[grid][m][ceil(n/64)] dense matrices (osd only, when they
+//                                                     do not fit shared memory)
+#include <cstring>
+
+#include <cuda_fp16.h>
+
+#include "bp_kernel.cuh"
+#include "internal.h"
+#include "osd_kernel.cuh"
+#include "timing.h"
+
+namespace {
+
+using namespace lbp;
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+uint32_t align16u(uint32_t x) { return (x + 15u) & ~15u; }
+
+int msg_bytes(int msg) { return msg == LBP_MSG_F32 ? 4 : (msg == LBP_MSG_F16 ? 2 : 1); }
+
+struct BpPlan {
+    int groups = 0, G = 0, grid = 0;
+    uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
+    size_t smem = 0;
+};
+
+struct OsdPlan {
+    bool smem_mat = false;
+    int grid = 0, n_pad = 1, wn = 0;
+    uint32_t off_keys = 0, off_inv = 0, off_flags = 0, off_piv = 0, off_ebits = 0, off_mat = 0;
+    size_t smem = 0;
+};
+
+struct WsLayout {
+    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, total = 0;
+};
+
+int validate_params(const lbp_params *p) {
+    if (!p) return LBP_EINVAL;
+    if (p->max_iter < 1 || p->max_iter > kMaxIter) return LBP_EINVAL;
+    if (p->scale_mode != LBP_SCALE_CONST && p->scale_mode != LBP_SCALE_ADAPTIVE) return LBP_EINVAL;
+    if (p->scale_mode == LBP_SCALE_CONST && !(p->scale_const > 0.0f && p->scale_const <= 1.0f)) return LBP_EINVAL;
+    if (p->lottery != 0 && p->lottery != 1) return LBP_EINVAL;
+    if (p->lottery_skip < 0) return LBP_EINVAL;
+    if (p->osd != 0 && p->osd != 1) return LBP_EINVAL;
+    if (p->msg != LBP_MSG_F32 && p->msg != LBP_MSG_F16 && p->msg != LBP_MSG_I8) return LBP_EINVAL;
+    if (p->reserved != 0) return LBP_EINVAL;
+    return LBP_OK;
+}
+
+// Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
+// group does not fit in shared memory.
+int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out) {
+    if (!c->d_image) return LBP_ENOSYS;
+    const int W32 = (c->m + 31) / 32;
+    BpPlan p;
+    uint32_t off = 0;
+    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->nnz);
+    p.off_lam = off;  off = align16u(off + 4u * c->n);
+    p.off_s = off;    off = align16u(off + 4u * W32);
+    p.off_shat = off; off = align16u(off + 12u * W32);
+    p.off_misc = off; off = align16u(off + 16u);
+    p.state_bytes = off;
+    const size_t budget = static_cast<size_t>(c->smem_optin);
+    if (c->img.bytes + static_cast<size_t>(p.state_bytes) > budget) return LBP_ENOSYS;
+    int S = static_cast<int>((budget - c->img.bytes) / p.state_bytes);
+    // Threads per group: enough to cover the checks, at most 256.
+    int G = 32;
+    while (G < 256 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
+    if (S * G > 1024) S = 1024 / G;
+    if (G > 32 && S > 15) S = 15;     // named barriers 1..15
+    if (S < 1) S = 1;
+    p.groups = S;
+    p.G = G;
+    p.smem = c->img.bytes + static_cast<size_t>(S) * p.state_bytes;
+    const int64_t need = (num_shots + S - 1) / S;
+    p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
+    if (p.grid < 1) p.grid = 1;
+    *out = p;
+    return LBP_OK;
+}
+
+int plan_osd(const lbp_code *c, int64_t num_shots, OsdPlan *out) {
+    OsdPlan p;
+    p.wn = (c->n + 63) / 64;
+    while (p.n_pad < c->n) p.n_pad <<= 1;
+    uint32_t off = 0;
+    p.off_keys = off;  off = align16u(off + 8u * p.n_pad);
+    p.off_inv = off;   off = align16u(off + 4u * c->n);
+    p.off_flags = off; off = align16u(off + 3u * c->m);
+    p.off_piv = off;   off = align16u(off + 4u * (4 + 2 * c->m));
+    p.off_ebits = off; off = align16u(off + 8u * p.wn);
+    p.off_mat = off;
+    const size_t mat = 8ull * c->m * p.wn;
+    if (off > static_cast<size_t>(c->smem_optin)) return LBP_ENOSYS;
+    p.smem_mat = off + mat <= static_cast<size_t>(c->smem_optin);
+    p.smem = p.smem_mat ? off + mat : off;
+    const int64_t g = num_shots < c->sm_count ? num_shots : c->sm_count;
+    p.grid = static_cast<int>(g < 1 ? 1 : g);
+    *out = p;
+    return LBP_OK;
+}
+
+WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, const OsdPlan *op) {
+    WsLayout w;
+    size_t off = 0;
+    w.counters = off; off = align256(off + 256);
+    if (prm->osd) {
+        w.osd_list = off; off = align256(off + 4ull * num_shots);
+        w.osd_llr = off;  off = align256(off + 4ull * num_shots * c->n);
+        if (op && !op->smem_mat) {
+            w.osd_mat = off;
+            off = align256(off + 8ull * op->grid * c->m * op->wn);
+        }
+    }
+    w.total = off;
+    return w;
+}
+
+template <typename K>
+int set_smem(K kernel, size_t bytes) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBP_ECUDA;
+    }
+    return LBP_OK;
+}
+
+template <typename MsgT, int G>
+int launch_bp_g(const BpPlan &p, const BpArgs &a, cudaStream_t s) {
+    auto k = bp_kernel<MsgT, G>;
+    int rc = set_smem(k, p.smem);
+    if (rc) return rc;
+    k<<<p.grid, p.groups * G, p.smem, s>>>(a);
+    return LBP_OK;
+}
+
+template <typename MsgT>
+int launch_bp_t(const BpPlan &p, const BpArgs &a, cudaStream_t s) {
+    switch (p.G) {
+        case 32: return launch_bp_g<MsgT, 32>(p, a, s);
+        case 64: return launch_bp_g<MsgT, 64>(p, a, s);
+        case 128: return launch_bp_g<MsgT, 128>(p, a, s);
+        case 256: return launch_bp_g<MsgT, 256>(p, a, s);
+        default: return LBP_ENOSYS;
+    }
+}
+
+int check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBP_OK : LBP_ECUDA;
+}
+
+int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
+                  uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
+                  void *ws, size_t ws_bytes, cudaStream_t stream) {
+    BpPlan bp;
+    int rc = plan_bp(c, prm->msg, B, &bp);
+    if (rc) return rc;
+    OsdPlan op;
+    if (prm->osd) {
+        rc = plan_osd(c, B, &op);
+        if (rc) return rc;
+    }
+    const WsLayout w = layout(c, prm, B, prm->osd ? &op : nullptr);
+    if (!ws || ws_bytes < w.total) return LBP_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return LBP_EINVAL;
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    unsigned int *counters = reinterpret_cast<unsigned int *>(base + w.counters);
+    if (cudaMemsetAsync(counters, 0, 256, stream) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
+
+    BpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.image = c->d_image;
+    a.img = c->img;
+    a.m = c->m; a.n = c->n;
+    a.max_iter = prm->max_iter; a.scale_mode = prm->scale_mode; a.scale_const = prm->scale_const;
+    a.lottery = prm->lottery; a.lottery_skip = prm->lottery_skip; a.osd = prm->osd;
+    a.seed = prm->seed; a.shot_offset = prm->shot_offset;
+    a.num_shots = B;
+    a.syn = syn; a.err = err; a.conv = conv; a.osd_out = osd_out; a.iters = iters; a.llr = llr;
+    a.counters = counters;
+    a.osd_list = prm->osd ? reinterpret_cast<uint32_t *>(base + w.osd_list) : nullptr;
+    a.osd_llr = prm->osd ? reinterpret_cast<float *>(base + w.osd_llr) : nullptr;
+    a.state_bytes = bp.state_bytes;
+    a.off_beta = bp.off_beta; a.off_lam = bp.off_lam; a.off_s = bp.off_s;
+    a.off_shat = bp.off_shat; a.off_misc = bp.off_misc;
+    void *tk = timing_begin(stream);
+    switch (prm->msg) {
+        case LBP_MSG_F32: rc = launch_bp_t<float>(bp, a, stream); break;
+        case LBP_MSG_F16: rc = launch_bp_t<__half>(bp, a, stream); break;
+        default: rc = launch_bp_t<int8_t>(bp, a, stream); break;
+    }
+    timing_end(tk, stream, kTimeBp);
+    if (rc) return rc;
+    rc = check_launch();
+    if (rc) return rc;
+    if (prm->osd) {
+        OsdArgs o;
+        std::memset(&o, 0, sizeof(o));
+        o.m = c->m; o.n = c->n;
+        o.row_ptr = c->d_row_ptr; o.col_idx = c->d_col_idx;
+        o.syn = syn; o.err = err; o.osd_out = osd_out;
+        o.counters = counters;
+        o.osd_list = a.osd_list; o.osd_llr = a.osd_llr;
+        o.gmat = op.smem_mat ? nullptr : reinterpret_cast<uint64_t *>(base + w.osd_mat);
+        o.n_pad = op.n_pad; o.wn = op.wn;
+        o.off_keys = op.off_keys; o.off_inv = op.off_inv; o.off_flags = op.off_flags;
+        o.off_piv = op.off_piv; o.off_ebits = op.off_ebits; o.off_mat = op.off_mat;
+        rc = set_smem(op.smem_mat ? osd_kernel<true> : osd_kernel<false>, op.smem);
+        if (rc) return rc;
+        void *to = timing_begin(stream);
+        if (op.smem_mat) {
+            osd_kernel<true><<<op.grid, 1024, op.smem, stream>>>(o);
+        } else {
+            osd_kernel<false><<<op.grid, 1024, op.smem, stream>>>(o);
+        }
+        timing_end(to, stream, kTimeOsd);
+        rc = check_launch();
+    }
+    return rc;
+}
+
+int check_common(const lbp_code *c, const lbp_params *prm, int64_t B) {
+    if (!c) return LBP_EINVAL;
+    int rc = validate_params(prm);
+    if (rc) return rc;
+    if (B < 0 || B > (1ll << 31)) return LBP_EINVAL;
+    return LBP_OK;
+}
+
+}  // namespace
+
+extern "C" size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots) {
+    if (check_common(code, params, num_shots)) return 0;
+    OsdPlan op;
+    if (params->osd && plan_osd(code, num_shots, &op)) return 0;
+    return layout(code, params, num_shots, params->osd ? &op : nullptr).total;
+}
+
+extern "C" int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+                          const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                          uint8_t *osd_out, int32_t *iters_out, float *llr_out,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_common(code, params, num_shots);
+    if (rc) return rc;
+    if (num_shots == 0) return LBP_OK;
+    if (!syndromes || !err_out || !converged || !iters_out) return LBP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != code->device) return LBP_EINVAL;
+    return decode_device(code, params, num_shots, syndromes, err_out, converged, osd_out, iters_out,
+                         llr_out, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+namespace {
+
+struct HostStage {
+    size_t syn, err, conv, osd, iters, decode_ws, total, llr, total_llr;
+};
+
+HostStage host_stage(const lbp_code *c, const lbp_params *prm, int64_t B) {
+    HostStage h;
+    const size_t wm = (c->m + 63) / 64, wn = (c->n + 63) / 64;
+    size_t off = 0;
+    h.syn = off;   off = align256(off + 8ull * wm * B);
+    h.err = off;   off = align256(off + 8ull * wn * B);
+    h.conv = off;  off = align256(off + static_cast<size_t>(B));
+    h.osd = off;   off = align256(off + static_cast<size_t>(B));
+    h.iters = off; off = align256(off + 4ull * B);
+    h.decode_ws = off;
+    h.total = align256(off + lbp_workspace_size(c, prm, B));
+    h.llr = h.total;
+    h.total_llr = h.llr + align256(4ull * c->n * B);
+    return h;
+}
+
+}  // namespace
+
+extern "C" size_t lbp_host_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots) {
+    if (check_common(code, params, num_shots)) return 0;
+    if (lbp_workspace_size(code, params, num_shots) == 0) return 0;
+    return host_stage(code, params, num_shots).total;
+}
+
+extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+                               const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                               uint8_t *osd_out, int32_t *iters_out, float *llr_out,
+                               void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_common(code, params, num_shots);
+    if (rc) return rc;
+    if (num_shots == 0) return LBP_OK;
+    if (!syndromes || !err_out || !converged || !iters_out || !workspace) return LBP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != code->device) return LBP_EINVAL;
+    const HostStage h = host_stage(code, params, num_shots);
+    if (workspace_bytes < (llr_out ? h.total_llr : h.total)) return LBP_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return LBP_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    const int64_t B = num_shots;
+    const size_t wm = (code->m + 63) / 64, wn = (code->n + 63) / 64;
+    uint64_t *d_syn = reinterpret_cast<uint64_t *>(base + h.syn);
+    uint64_t *d_err = reinterpret_cast<uint64_t *>(base + h.err);
+    uint8_t *d_conv = base + h.conv;
+    uint8_t *d_osd = base + h.osd;
+    int32_t *d_iters = reinterpret_cast<int32_t *>(base + h.iters);
+    float *d_llr = llr_out ? reinterpret_cast<float *>(base + h.llr) : nullptr;
+    if (cudaMemcpyAsync(d_syn, syndromes, 8ull * wm * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return LBP_ECUDA;
+    }
+    rc = decode_device(code, params, B, d_syn, d_err, d_conv, d_osd, d_iters, d_llr,
+                       base + h.decode_ws, h.total - h.decode_ws, s);
+    if (rc) return rc;
+    bool ok = cudaMemcpyAsync(err_out, d_err, 8ull * wn * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(converged, d_conv, static_cast<size_t>(B), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(iters_out, d_iters, 4ull * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    if (osd_out) ok = ok && cudaMemcpyAsync(osd_out, d_osd, static_cast<size_t>(B), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    if (llr_out) ok = ok && cudaMemcpyAsync(llr_out, d_llr, 4ull * code->n * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return LBP_ECUDA; }
+    return LBP_OK;
+}

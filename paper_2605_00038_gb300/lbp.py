@@ -1,0 +1,212 @@
+"""Python binding of liblbp (include/lbp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device buffers
+are torch CUDA tensors (packed bit words travel as int64 tensors holding the
+uint64 bit patterns); host buffers are numpy arrays or pinned CPU tensors.
+Every step of decoding runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is not built, or a call fails, this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+LIB_PATH = _HERE / "liblbp.so"
+
+LBP_OK, LBP_EINVAL, LBP_ENOMEM, LBP_ENOSYS, LBP_ECUDA = 0, -22, -12, -38, -5
+LBP_OSD_NOT_RUN, LBP_OSD_APPLIED, LBP_OSD_NO_SOLUTION = 0, 1, 2
+LBP_MSG_F32, LBP_MSG_F16, LBP_MSG_I8 = 0, 1, 2
+LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
+
+EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info",
+            "lbp_workspace_size", "lbp_decode", "lbp_host_workspace_size", "lbp_decode_host",
+            "lbp_timing_enable", "lbp_timing_read", "lbp_strerror"]
+
+
+class lbp_params(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("scale_mode", ctypes.c_int32),
+                ("scale_const", ctypes.c_float), ("lottery", ctypes.c_int32),
+                ("lottery_skip", ctypes.c_int32), ("osd", ctypes.c_int32),
+                ("msg", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("shot_offset", ctypes.c_uint64)]
+
+
+class LbpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s failed: %s (%d)" % (where, lbp_strerror(code), code))
+        self.code = code
+
+
+_L = None
+
+
+def lib():
+    """Load liblbp.so (raises if it has not been built)."""
+    global _L
+    if _L is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError("liblbp.so is not built (run __graft_entry__.build() or "
+                               "paper_2605_00038_gb300._build.build_lbp())")
+        L = ctypes.CDLL(str(LIB_PATH))
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        P = ctypes.POINTER(lbp_params)
+        L.lbp_params_default.restype = None
+        L.lbp_params_default.argtypes = [P]
+        L.lbp_load_code.restype = ctypes.c_int
+        L.lbp_load_code.argtypes = [i32, i32, vp, vp, vp, ctypes.POINTER(vp)]
+        L.lbp_free_code.restype = ctypes.c_int
+        L.lbp_free_code.argtypes = [vp]
+        L.lbp_code_info.restype = ctypes.c_int
+        L.lbp_code_info.argtypes = [vp, vp, vp, vp]
+        L.lbp_workspace_size.restype = sz
+        L.lbp_workspace_size.argtypes = [vp, P, i64]
+        L.lbp_host_workspace_size.restype = sz
+        L.lbp_host_workspace_size.argtypes = [vp, P, i64]
+        dec = [vp, P, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.lbp_decode.restype = ctypes.c_int
+        L.lbp_decode.argtypes = dec
+        L.lbp_decode_host.restype = ctypes.c_int
+        L.lbp_decode_host.argtypes = dec
+        L.lbp_timing_enable.restype = ctypes.c_int
+        L.lbp_timing_enable.argtypes = [ctypes.c_int]
+        L.lbp_timing_read.restype = ctypes.c_int
+        L.lbp_timing_read.argtypes = [vp, vp, vp, vp]
+        L.lbp_strerror.restype = ctypes.c_char_p
+        L.lbp_strerror.argtypes = [ctypes.c_int]
+        _L = L
+    return _L
+
+
+def lbp_strerror(code: int) -> str:
+    return lib().lbp_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != LBP_OK:
+        raise LbpError(rc, where)
+
+
+def lbp_params_default(**overrides) -> lbp_params:
+    p = lbp_params()
+    lib().lbp_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Code:
+    """Owning handle of an lbp_code (frees it on close / garbage collection)."""
+
+    def __init__(self, ptr: int, m: int, n: int, nnz: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.m, self.n, self.nnz = m, n, nnz
+
+    def close(self):
+        if self.ptr:
+            lbp_free_code(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbp_load_code(m: int, n: int, row_ptr, col_idx, priors) -> Code:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    if rp.shape != (m + 1,) or pr.shape != (n,):
+        raise ValueError("row_ptr must have m+1 entries and priors n entries")
+    out = ctypes.c_void_p()
+    _check(lib().lbp_load_code(m, n, rp.ctypes.data, ci.ctypes.data if ci.size else None,
+                               pr.ctypes.data if pr.size else None, ctypes.byref(out)),
+           "lbp_load_code")
+    return Code(out.value, m, n, int(rp[-1]))
+
+
+def lbp_free_code(code: Code):
+    if code.ptr:
+        rc = lib().lbp_free_code(code.ptr)
+        code.ptr = ctypes.c_void_p()
+        _check(rc, "lbp_free_code")
+
+
+def lbp_code_info(code: Code):
+    m, n, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbp_code_info(code.ptr, ctypes.byref(m), ctypes.byref(n), ctypes.byref(nnz)),
+           "lbp_code_info")
+    return m.value, n.value, nnz.value
+
+
+def lbp_workspace_size(code: Code, params: lbp_params, num_shots: int) -> int:
+    return int(lib().lbp_workspace_size(code.ptr, ctypes.byref(params), num_shots))
+
+
+def lbp_host_workspace_size(code: Code, params: lbp_params, num_shots: int) -> int:
+    return int(lib().lbp_host_workspace_size(code.ptr, ctypes.byref(params), num_shots))
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host buffers must be C-contiguous")
+        return a.ctypes.data
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("host buffers must be contiguous CPU tensors")
+    return a.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def lbp_decode(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
+               osd_out, iters_out, llr_out, workspace, stream=None):
+    """Enqueue a decode on `stream` (default: torch's current stream)."""
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().lbp_decode(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
+                            _dptr(err_out), _dptr(converged), _dptr(osd_out), _dptr(iters_out),
+                            _dptr(llr_out), _dptr(workspace), ws_bytes, _stream_handle(stream)),
+           "lbp_decode")
+
+
+def lbp_decode_host(code: Code, params: lbp_params, num_shots: int, syndromes, err_out,
+                    converged, osd_out, iters_out, llr_out, workspace, stream=None):
+    """Host-buffer variant: copies in, decodes and copies out on `stream`."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().lbp_decode_host(code.ptr, ctypes.byref(params), num_shots, _hptr(syndromes),
+                                 _hptr(err_out), _hptr(converged), _hptr(osd_out),
+                                 _hptr(iters_out), _hptr(llr_out), _dptr(workspace), ws_bytes,
+                                 _stream_handle(stream)),
+           "lbp_decode_host")
+
+
+def lbp_timing_enable(on: bool):
+    _check(lib().lbp_timing_enable(int(bool(on))), "lbp_timing_enable")
+
+
+def lbp_timing_read():
+    """Returns (bp_ms, bp_launches, osd_ms, osd_launches) since the last read."""
+    bm, bl, om, ol = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().lbp_timing_read(ctypes.byref(bm), ctypes.byref(bl), ctypes.byref(om),
+                                 ctypes.byref(ol)), "lbp_timing_read")
+    return bm.value, bl.value, om.value, ol.value

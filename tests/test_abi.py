@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol that
+include/lbp.h declares; host-side argument checks run before any CUDA call."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2605_00038_gb300 import _build, lbp
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build_lbp()
+    return lbp.lib()
+
+
+def declared_functions():
+    text = (ROOT / "include" / "lbp.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbp_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert set(names) == set(lbp.EXPORTED)
+    for name in names:
+        assert hasattr(L, name), name
+        ctypes.cast(getattr(L, name), ctypes.c_void_p)
+
+
+def test_params_default_matches_paper(L):
+    p = lbp.lbp_params_default()
+    assert (p.max_iter, p.scale_mode, p.lottery, p.lottery_skip, p.osd, p.msg) == (
+        100, lbp.LBP_SCALE_ADAPTIVE, 1, 6, 0, lbp.LBP_MSG_F32)
+    assert ctypes.sizeof(lbp.lbp_params) == 48
+
+
+def test_strerror(L):
+    for c in (lbp.LBP_OK, lbp.LBP_EINVAL, lbp.LBP_ENOMEM, lbp.LBP_ENOSYS, lbp.LBP_ECUDA):
+        assert lbp.lbp_strerror(c)
+    assert lbp.lbp_strerror(12345) == "unknown error"
+
+
+@pytest.mark.parametrize("rows,n,pri", [
+    ([0, 1, 3], [0, 0, 1], [0.1, 0.1]),            # weight-1 row
+    ([0, 2, 4], [1, 0, 0, 1], [0.1, 0.1]),         # unsorted row
+    ([0, 2, 4], [0, 1, 0, 2], [0.1, 0.1]),         # column out of range
+    ([0, 2, 4], [0, 1, 0, 1], [0.1, 0.0]),         # prior 0
+    ([0, 2, 4], [0, 1, 0, 1], [0.1, 1.0]),         # prior 1
+    ([1, 2, 4], [0, 1, 0, 1], [0.1, 0.1]),         # row_ptr[0] != 0
+])
+def test_load_code_rejects_malformed_input(L, rows, n, pri):
+    m = len(rows) - 1
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_load_code(m, 2, np.array(rows), np.array(n), np.array(pri))
+    assert ei.value.code == lbp.LBP_EINVAL
+
+
+def test_rejects_row_heavier_than_32(L):
+    n = 33
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_load_code(1, n, np.array([0, 33]), np.arange(33), np.full(n, 0.1))
+
+
+def test_decode_rejects_bad_params_without_gpu(L):
+    # Parameter validation precedes any device access.
+    bad = lbp.lbp_params_default(max_iter=0)
+    rc = L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(bad), 1, None, None, None, None, None,
+                      None, None, 0, None)
+    assert rc == lbp.LBP_EINVAL
+    for kw in (dict(msg=7), dict(scale_mode=5), dict(lottery=2), dict(reserved=1),
+               dict(scale_mode=0, scale_const=0.0), dict(lottery_skip=-1)):
+        p = lbp.lbp_params_default(**kw)
+        assert L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(p), 1, None, None, None, None, None,
+                            None, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_workspace_size(ctypes.c_void_p(1), ctypes.byref(bad), 10) == 0

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (from the decoder's specification): with the same seeded inputs, hard
+decisions, convergence flags, iteration counts and OSD outputs are
+bit-identical to the oracle run in the same message precision; the final
+LLRs agree to 1e-5 relative (they are in fact expected to be bit-identical,
+since both sides perform the same IEEE binary32 operations in the same
+order).  Against the FP64 oracle, decisions agree except on shots whose
+LLRs pass within 1e-6 of a tie, which are counted.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2605_00038_gb300 import lbp
+from paper_2605_00038_gb300.decoder import Decoder
+from paper_2605_00038_gb300.inputs import sampler, workloads
+from paper_2605_00038_gb300.inputs.codes import (SparseH, bb_code, rotated_surface, spacetime,
+                                                 spacetime_priors)
+
+pytestmark = pytest.mark.gpu
+
+PREC = {lbp.LBP_MSG_F32: oracle.PREC_F32, lbp.LBP_MSG_F16: oracle.PREC_F16,
+        lbp.LBP_MSG_I8: oracle.PREC_I8}
+LLR_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def gpu_decode(h, pri, syn, want_llr=True, **kw):
+    dec = Decoder(h, pri)
+    prm = dec.params(**kw)
+    out = dec.decode(torch.from_numpy(np.ascontiguousarray(syn).view(np.int64)).cuda(), prm,
+                     want_llr=want_llr)
+    torch.cuda.synchronize()
+    r = dict(err=sampler.unpack(out.err.cpu().numpy().view(np.uint64), h.n),
+             err_words=out.err.cpu().numpy().view(np.uint64),
+             conv=out.converged.cpu().numpy(), osd=out.osd.cpu().numpy(),
+             iters=out.iters.cpu().numpy(),
+             llr=out.llr.cpu().numpy() if want_llr else None)
+    dec.close()
+    return r
+
+
+def oracle_decode(h, pri, syn, prec=None, **kw):
+    msg = kw.get("msg", 0)
+    p = oracle.OracleParams(max_iter=kw.get("max_iter", 100), scale_mode=kw.get("scale_mode", 1),
+                            scale_const=kw.get("scale_const", 0.625),
+                            lottery=bool(kw.get("lottery", 1)), lottery_skip=kw.get("lottery_skip", 6),
+                            osd=bool(kw.get("osd", 0)), prec=PREC[msg] if prec is None else prec,
+                            seed=kw.get("seed", 0), shot_offset=kw.get("shot_offset", 0))
+    return oracle.decode(h, pri, sampler.unpack(syn, h.m), p, want_llr=True)
+
+
+def assert_parity(g, r):
+    assert np.array_equal(g["conv"], r.converged), "convergence flags differ"
+    assert np.array_equal(g["iters"], r.iters), "iteration counts differ"
+    bad = np.nonzero((g["err"] != r.err).any(1))[0]
+    assert bad.size == 0, "error estimates differ on %d shots, first %s" % (bad.size, bad[:5])
+    osd_ref = np.where(r.osd_used == 1, lbp.LBP_OSD_APPLIED,
+                       np.where(r.osd_nosol == 1, lbp.LBP_OSD_NO_SOLUTION, lbp.LBP_OSD_NOT_RUN))
+    assert np.array_equal(g["osd"], osd_ref), "OSD status differs"
+    if g["llr"] is not None:
+        ref = r.llr
+        diff = np.abs(g["llr"].astype(np.float64) - ref)
+        assert np.all(diff <= LLR_RTOL * np.abs(ref) + 1e-30), "LLR beyond 1e-5 relative"
+
+
+# ----------------------------------------------------------------- configs
+
+def test_c1_d3_code_capacity_fp32_vs_oracle():
+    w = workloads.c1_d3_code_capacity()
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    g = gpu_decode(w.h, w.priors, syn, **w.decoder)
+    assert_parity(g, oracle_decode(w.h, w.priors, syn, **w.decoder))
+    # FP64 oracle: decisions identical except near-ties.
+    r64 = oracle_decode(w.h, w.priors, syn, prec=oracle.PREC_F64, **w.decoder)
+    diff = (g["err"] != r64.err).any(1) | (g["conv"] != r64.converged)
+    near = (np.abs(r64.llr) < 1e-6 * np.abs(np.log(0.95 / 0.05))).any(1)
+    assert not np.any(diff & ~near), "FP32 vs FP64 decisions differ away from ties"
+
+
+@pytest.mark.parametrize("osd", [0, 1])
+def test_c2_d11_spacetime_lottery_fp32(osd):
+    w = workloads.c2_d11_spacetime(shots=3000, osd=osd)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, seed=11)
+    g = gpu_decode(w.h, w.priors, syn, **kw)
+    r = oracle_decode(w.h, w.priors, syn, **kw)
+    assert_parity(g, r)
+    assert (r.converged == 0).sum() > 0 or osd == 0
+
+
+@pytest.mark.parametrize("p", [0.01, 0.03, 0.05])
+def test_c3_bb144_lottery_osd_fp16(p):
+    w = workloads.c3_bb144(p, shots=4000)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, seed=3)
+    g = gpu_decode(w.h, w.priors, syn, **kw)
+    r = oracle_decode(w.h, w.priors, syn, **kw)
+    assert_parity(g, r)
+    if p >= 0.03:
+        assert (g["osd"] == lbp.LBP_OSD_APPLIED).sum() > 0
+
+
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
+def test_precisions_on_d7_spacetime(msg):
+    hz, _ = rotated_surface(7)
+    st = spacetime(hz, 7)
+    pri = spacetime_priors(hz, 7, 0.006, 0.006)
+    _, syn = sampler.sample(st, pri, seed=77, num_shots=2500)
+    kw = dict(max_iter=80, lottery=1, osd=1, msg=msg, seed=2)
+    assert_parity(gpu_decode(st, pri, syn, **kw), oracle_decode(st, pri, syn, **kw))
+
+
+def test_osd_bit_exact_on_gpu_llrs():
+    """OSD fed with the GPU's exported LLRs gives the GPU's OSD output."""
+    hx, _ = bb_code("bb72")
+    pri = np.full(hx.n, 0.07)
+    _, syn = sampler.sample(hx, pri, seed=8, num_shots=3000)
+    g = gpu_decode(hx, pri, syn, max_iter=30, lottery=0, osd=1, msg=0)
+    S = sampler.unpack(syn, hx.m)
+    idx = np.nonzero(g["osd"] != lbp.LBP_OSD_NOT_RUN)[0]
+    assert idx.size > 20
+    for b in idx[:200]:
+        e, _, _ = oracle.osd0(hx, g["llr"][b].astype(np.float64), S[b])
+        if e is None:
+            assert g["osd"][b] == lbp.LBP_OSD_NO_SOLUTION
+        else:
+            assert g["osd"][b] == lbp.LBP_OSD_APPLIED
+            assert np.array_equal(g["err"][b], e)
+
+
+# -------------------------------------------------------------- edge cases
+
+def test_ragged_sizes_and_tails():
+    """Batch sizes that are not multiples of the groups; m, n not multiples of 64."""
+    hz, _ = rotated_surface(9)                    # m = 40, n = 81
+    pri = np.full(hz.n, 0.04)
+    for B in (1, 2, 31, 33, 257, 1001):
+        _, syn = sampler.sample(hz, pri, seed=B, num_shots=B)
+        kw = dict(max_iter=40, lottery=1, lottery_skip=0, osd=1, seed=B)
+        g = gpu_decode(hz, pri, syn, **kw)
+        assert_parity(g, oracle_decode(hz, pri, syn, **kw))
+        tail = g["err_words"][:, -1] >> np.uint64(hz.n % 64)
+        assert not tail.any(), "bits past n must be zero"
+
+
+def test_garbage_past_m_is_ignored():
+    hz, _ = rotated_surface(5)                    # m = 12
+    pri = np.full(hz.n, 0.05)
+    _, syn = sampler.sample(hz, pri, seed=4, num_shots=300)
+    dirty = syn.copy()
+    dirty[:, -1] |= np.uint64(0xFFFF_F000_0000_0000)
+    kw = dict(max_iter=30, seed=1)
+    a = gpu_decode(hz, pri, syn, **kw)
+    b = gpu_decode(hz, pri, dirty, **kw)
+    assert np.array_equal(a["err"], b["err"]) and np.array_equal(a["iters"], b["iters"])
+
+
+def test_degenerate_codes_and_zero_syndromes():
+    # Empty rows, one iteration, all-zero syndromes.
+    h = SparseH.from_rows([[0, 1], [], [1, 2, 3], []], 4)
+    pri = np.full(4, 0.1)
+    syn = np.zeros((5, 1), dtype=np.uint64)
+    syn[1, 0] = 1
+    syn[2, 0] = 2          # a syndrome bit on an empty row: never satisfiable
+    for I in (1, 3):
+        kw = dict(max_iter=I, lottery=1, lottery_skip=0, osd=1, seed=1)
+        g = gpu_decode(h, pri, syn, **kw)
+        assert_parity(g, oracle_decode(h, pri, syn, **kw))
+    assert g["conv"][0] == 1 and g["iters"][0] == 1 and not g["err"][0].any()
+    assert g["osd"][2] == lbp.LBP_OSD_NO_SOLUTION
+
+
+def test_shot_offset_and_batch_independence():
+    w = workloads.c3_bb144(0.05, shots=1200)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, seed=9)
+    full = gpu_decode(w.h, w.priors, syn, **kw)
+    part = gpu_decode(w.h, w.priors, syn[700:], shot_offset=700, **kw)
+    for k in ("err", "conv", "iters", "osd"):
+        assert np.array_equal(full[k][700:], part[k])
+
+
+def test_host_buffer_entry_point_matches_device():
+    w = workloads.c2_d11_spacetime(shots=600)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    g = gpu_decode(w.h, w.priors, syn, **w.decoder)
+    dec = Decoder(w.h, w.priors)
+    prm = dec.params(**w.decoder)
+    B = w.shots
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+    hs = pin(syn.shape, torch.int64)
+    hs.numpy()[:] = syn.view(np.int64)
+    out = dict(err=pin((B, g["err_words"].shape[1]), torch.int64), converged=pin(B, torch.uint8),
+               osd=pin(B, torch.uint8), iters=pin(B, torch.int32), llr=pin((B, w.h.n), torch.float32))
+    dec.decode_host(hs, prm, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out["err"].numpy().view(np.uint64), g["err_words"])
+    assert np.array_equal(out["converged"].numpy(), g["conv"])
+    assert np.array_equal(out["iters"].numpy(), g["iters"])
+    assert np.array_equal(out["osd"].numpy(), g["osd"])
+    assert np.array_equal(out["llr"].numpy(), g["llr"])
+    dec.close()
+
+
+def test_bench_launch_config_full_size_sampled():
+    """c2 at its full batch (10^6 shots) in the bench's launch configuration:
+    sampled shots match the oracle one by one; on every shot the converged or
+    OSD estimate reproduces the syndrome (checked on the GPU)."""
+    w = workloads.c2_d11_spacetime()
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    g = gpu_decode(w.h, w.priors, syn, want_llr=False, **w.decoder)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(w.shots, size=400, replace=False))
+    fails = np.nonzero(g["conv"] == 0)[0][:100]
+    pick = np.unique(np.concatenate([pick, fails]))
+    for lo in range(0, pick.size, 100):
+        sel = pick[lo:lo + 100]
+        for b in sel:
+            r = oracle_decode(w.h, w.priors, syn[b:b + 1], shot_offset=int(b), **w.decoder)
+            assert g["conv"][b] == r.converged[0] and g["iters"][b] == r.iters[0]
+            assert np.array_equal(g["err"][b], r.err[0])
+    # H e_hat == s on every converged / OSD shot, via a dense GF(2) product on the GPU.
+    Hd = torch.from_numpy(w.h.to_dense().astype(np.float32)).cuda()
+    ok = (g["conv"] == 1) | (g["osd"] == lbp.LBP_OSD_APPLIED)
+    assert ok.mean() > 0.99
+    for lo in range(0, w.shots, 100_000):
+        e = torch.from_numpy(g["err"][lo:lo + 100_000].astype(np.float32)).cuda()
+        s = torch.from_numpy(sampler.unpack(syn[lo:lo + 100_000], w.h.m).astype(np.float32)).cuda()
+        shat = torch.remainder(e @ Hd.T, 2)
+        bad = (shat != s).any(1).cpu().numpy() & ok[lo:lo + 100_000]
+        assert not bad.any()
