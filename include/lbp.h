@@ -99,7 +99,14 @@ int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
 
 /* Bytes of device workspace lbp_decode needs for num_shots shots with these
  * parameters (0 on invalid input).  The size grows linearly with num_shots
- * only when params->osd is set (the LLRs of shots handed to OSD). */
+ * only when params->osd is set (the LLRs of shots handed to OSD).
+ *
+ * Tuning: OSD keeps rows of H sparse until an elimination changes them; the
+ * changed rows take dense copies from a per-warp pool of min(m, 192) rows.
+ * The environment variable LBP_OSD_POOL_ROWS (read at every call) lowers that
+ * bound; a shot that needs more rows is solved by the block-wide OSD kernel
+ * instead, with the same result.  Set it identically for lbp_workspace_size
+ * and lbp_decode. */
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).

@@ -1,0 +1,82 @@
+// Device helpers shared by the BP kernels: message storage types, group
+// barriers, the lottery's counter-based generator and the normalisation
+// factor.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace lbp {
+
+// ------------------------------------------------------------ message types
+
+template <typename T> struct Msg;
+template <> struct Msg<float> {
+    static __device__ __forceinline__ float load(float x) { return x; }
+    static __device__ __forceinline__ float store(float x) { return x; }
+};
+template <> struct Msg<__half> {
+    static __device__ __forceinline__ float load(__half x) { return __half2float(x); }
+    static __device__ __forceinline__ __half store(float x) { return __float2half_rn(x); }
+};
+// Int3.4: q = clamp(rne(16 x), -127, 127), value q / 16.
+template <> struct Msg<int8_t> {
+    static __device__ __forceinline__ float load(int8_t q) { return __fmul_rn(static_cast<float>(q), 0.0625f); }
+    static __device__ __forceinline__ int8_t store(float x) {
+        int q = __float2int_rn(__fmul_rn(16.0f, x));
+        q = q > 127 ? 127 : (q < -127 ? -127 : q);
+        return static_cast<int8_t>(q);
+    }
+};
+
+// -------------------------------------------------------------- group sync
+
+template <int G>
+__device__ __forceinline__ void group_sync(int bar) {
+    if (G == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(G) : "memory");
+    }
+}
+
+// Barrier that also ORs a predicate over the group.
+template <int G>
+__device__ __forceinline__ bool group_sync_or(int bar, bool p) {
+    if (G == 32) {
+        return __any_sync(0xffffffffu, p);
+    } else {
+        unsigned r;
+        asm volatile(
+            "{\n\t.reg .pred pi, po;\n\t"
+            "setp.ne.u32 pi, %1, 0;\n\t"
+            "bar.red.or.pred po, %2, %3, pi;\n\t"
+            "selp.u32 %0, 1, 0, po;\n\t}"
+            : "=r"(r)
+            : "r"(static_cast<unsigned>(p)), "r"(bar), "r"(G)
+            : "memory");
+        return r != 0;
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), output number counter+1 of the stream
+// whose state starts at seed.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counter) {
+    uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Normalisation factor at iteration i, binary32: the constant, or
+// 1 - 2^-(i+1) rounded to nearest (exact for i + 1 <= 24, 1.0 beyond).
+__device__ __forceinline__ float scale_at(int mode, float c, int i) {
+    if (mode == LBP_SCALE_CONST) return c;
+    const int k = i + 1;
+    if (k >= 25) return 1.0f;
+    return __fsub_rn(1.0f, __int_as_float((127 - k) << 23));
+}
+
+}  // namespace lbp

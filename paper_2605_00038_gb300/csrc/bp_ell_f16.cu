@@ -1,0 +1,10 @@
+// bp_ell_kernel instantiations for __half messages.
+#include "bp_ell_launch.cuh"
+
+namespace lbp {
+
+int launch_bp_ell_f16(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
+    return launch_ell<__half>(s, a, DC, DV, st);
+}
+
+}  // namespace lbp

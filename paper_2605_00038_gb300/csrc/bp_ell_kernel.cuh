@@ -1,0 +1,289 @@
+// K_bp (bounded degree): the same Alg. 1 + Alg. 3 iteration as bp_kernel,
+// specialised for codes whose checks have at most DC ones and whose columns
+// at most DV ones (every surface-code space-time matrix: DC = 6, DV = 2; BB
+// codes: DC = 6, DV = 3).
+//
+// What changes against the general kernel is layout and instruction count:
+//  * Check side in ELL form, slot-major: cidx[k][c] is the k-th column of
+//    check c (ascending), padded with column n, whose prior and posterior are
+//    +inf (a neutral element of the check update: positive sign, never the
+//    minimum).  beta[k][c] (row length m + 1) is the message on that slot.
+//    Thread c reads slot k of consecutive checks from consecutive words: no
+//    bank conflicts, and loops over the DC slots unroll completely.
+//  * Column side in ELL form, slot-major: vent[k][v] packs (slot << 13 | check)
+//    of v's k-th check, ascending, padded with check m, slot 0, whose message
+//    beta[0][m] is +0 (x + 0 == x for every partial sum, which is never -0), so
+//    the LLR update sums exactly the oracle's sequence of binary32 additions.
+//  * The lottery reads V(c*) and C(v) from the same ELL arrays.
+// Everything else (groups of G threads per shot, named barriers, s_hat
+// scatter, early termination, lottery, outputs, OSD hand-off) is as in
+// bp_kernel.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "bp_common.cuh"
+#include "internal.h"
+
+namespace lbp {
+
+struct BpEllArgs {
+    const uint8_t *image;     // ELL graph image (global), copied to shared memory
+    EllImage img;
+    int32_t m, n;
+    int32_t max_iter, scale_mode;
+    float scale_const;
+    int32_t lottery, lottery_skip, osd;
+    uint64_t seed, shot_offset;
+    int64_t num_shots;
+    const uint64_t *syn;
+    uint64_t *err;
+    uint8_t *conv;
+    uint8_t *osd_out;
+    int32_t *iters;
+    float *llr;
+    unsigned int *counters;
+    uint32_t *osd_list;
+    float *osd_llr;
+    uint32_t state_bytes;
+    uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
+};
+
+template <typename MsgT, int G, int DC, int DV>
+__global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
+    static_assert(DC <= 8 && DV <= 8, "slot ids are packed in 3 bits");
+    extern __shared__ __align__(16) uint8_t smem[];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(a.image);
+        int4 *dst = reinterpret_cast<int4 *>(smem);
+        const int words = static_cast<int>(a.img.bytes >> 4);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    const int m = a.m, n = a.n, I = a.max_iter;
+    const int m1s = m + 1;                     // beta row stride
+    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(smem + a.img.off_cidx);
+    const uint16_t *vent = reinterpret_cast<const uint16_t *>(smem + a.img.off_vent);
+    const float *mu = reinterpret_cast<const float *>(smem + a.img.off_mu);
+
+    const int grp = threadIdx.x / G;
+    const int t = threadIdx.x % G;
+    const int lane = threadIdx.x & 31;
+    const int bar = grp + 1;
+    uint8_t *st = smem + a.img.bytes + static_cast<size_t>(grp) * a.state_bytes;
+    MsgT *beta = reinterpret_cast<MsgT *>(st + a.off_beta);
+    float *lam = reinterpret_cast<float *>(st + a.off_lam);
+    uint32_t *s_w = reinterpret_cast<uint32_t *>(st + a.off_s);
+    uint32_t *shat = reinterpret_cast<uint32_t *>(st + a.off_shat);
+    volatile uint32_t *misc = reinterpret_cast<volatile uint32_t *>(st + a.off_misc);
+    if (t == 0) {
+        beta[m] = Msg<MsgT>::store(0.0f);                 // column-side padding message
+        lam[n] = __int_as_float(0x7f800000);              // check-side padding column
+    }
+    __syncthreads();
+
+    const int W32 = (m + 31) >> 5;
+    const int wm64 = (m + 63) >> 6;
+    const int wn64 = (n + 63) >> 6;
+    const uint32_t last_mask = (m & 31) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
+
+    while (true) {
+        if (t == 0) misc[0] = atomicAdd(&a.counters[0], 1u);
+        group_sync<G>(bar);
+        const uint32_t b = misc[0];
+        if (static_cast<int64_t>(b) >= a.num_shots) break;
+
+        const uint32_t *syn32 = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
+        for (int w = t; w < W32; w += G) {
+            uint32_t x = __ldg(syn32 + w);
+            if (w == W32 - 1) x &= last_mask;
+            s_w[w] = x;
+            shat[w] = 0u;
+            shat[W32 + w] = 0u;
+            shat[2 * W32 + w] = 0u;
+        }
+        group_sync<G>(bar);
+
+        int prev = 0, cur = 1, nxt = 2;
+        bool converged = false;
+        int it = 0;
+        for (; it < I; ++it) {
+            const float f = scale_at(a.scale_mode, a.scale_const, it);
+            // ---- C2V -------------------------------------------------------
+            for (int c = t; c < m; c += G) {
+                float al[DC];
+                if (it == 0) {
+                    #pragma unroll
+                    for (int k = 0; k < DC; ++k) al[k] = mu[cidx[k * m + c]];
+                } else {
+                    #pragma unroll
+                    for (int k = 0; k < DC; ++k)
+                        al[k] = __fsub_rn(lam[cidx[k * m + c]], Msg<MsgT>::load(beta[k * m1s + c]));
+                }
+                unsigned parity = (s_w[c >> 5] >> (c & 31)) & 1u;
+                unsigned negmask = 0u;
+                float min1 = __int_as_float(0x7f800000), min2 = min1;
+                int pos = 0;
+                #pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const unsigned ng = al[k] < 0.0f ? 1u : 0u;
+                    negmask |= ng << k;
+                    parity ^= ng;
+                    const float aa = fabsf(al[k]);
+                    const bool lt = aa < min1;
+                    min2 = lt ? min1 : fminf(min2, aa);
+                    pos = lt ? k : pos;
+                    min1 = lt ? aa : min1;
+                }
+                const float m1 = __fmul_rn(f, min1);
+                const float m2 = __fmul_rn(f, min2);
+                #pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const float mag = (k == pos) ? m2 : m1;
+                    const unsigned ng = (parity ^ (negmask >> k)) & 1u;
+                    beta[k * m1s + c] = Msg<MsgT>::store(ng ? -mag : mag);
+                }
+            }
+            group_sync<G>(bar);
+            // ---- LLR update, hard decision, syndrome scatter -------------------
+            uint32_t *sh_cur = shat + cur * W32;
+            for (int v = t; v < n; v += G) {
+                unsigned ent[DV];
+                float acc = mu[v];
+                #pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    ent[k] = vent[k * n + v];
+                    acc = __fadd_rn(acc, Msg<MsgT>::load(beta[(ent[k] >> 13) * m1s + (ent[k] & 0x1fffu)]));
+                }
+                lam[v] = acc;
+                if (acc <= 0.0f) {
+                    #pragma unroll
+                    for (int k = 0; k < DV; ++k) {
+                        const unsigned r = ent[k] & 0x1fffu;
+                        if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
+                    }
+                }
+            }
+            group_sync<G>(bar);
+            // ---- early termination ------------------------------------------
+            bool mism = false;
+            uint32_t *sh_nxt = shat + nxt * W32;
+            for (int w = t; w < W32; w += G) {
+                mism |= (sh_cur[w] != s_w[w]);
+                sh_nxt[w] = 0u;
+            }
+            if (!group_sync_or<G>(bar, mism)) { converged = true; break; }
+            // ---- lottery (Alg. 3) ---------------------------------------------
+            if (a.lottery && it >= a.lottery_skip && it < I - 1) {
+                if (t < 32) {
+                    const uint32_t *sp = shat + prev * W32;
+                    // N = |U| and c* = member k of U, from per-word prefix counts.
+                    uint32_t base = 0;
+                    int cstar = -1;
+                    uint32_t N = 0;
+                    for (int w0 = 0; w0 < W32; w0 += 32) {
+                        const int w = w0 + lane;
+                        const uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
+                        uint32_t pc = __popc(word);
+                        #pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
+                        N += pc;
+                    }
+                    if (N > 0) {
+                        const uint64_t g = a.shot_offset + b;
+                        const uint32_t u = static_cast<uint32_t>(
+                            splitmix64_at(a.seed, (g << 24) + static_cast<uint64_t>(it)));
+                        const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(u) * N) >> 32);
+                        for (int w0 = 0; w0 < W32 && cstar < 0; w0 += 32) {
+                            const int w = w0 + lane;
+                            uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
+                            const uint32_t pc = __popc(word);
+                            uint32_t incl = pc;
+                            #pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            const uint32_t excl = incl - pc;
+                            const bool mine = (k >= base + excl) && (k < base + incl);
+                            const unsigned own = __ballot_sync(0xffffffffu, mine);
+                            if (own) {
+                                int pick = 0;
+                                if (mine) {
+                                    uint32_t r = k - base - excl;
+                                    while (r--) word &= word - 1u;
+                                    pick = w * 32 + (__ffs(word) - 1);
+                                }
+                                cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
+                            }
+                            base += __shfl_sync(0xffffffffu, incl, 31);
+                        }
+                        // v*: most unsatisfied checks, least |lambda|, lowest column.
+                        int bc = -1, bv = 0x7fffffff;
+                        float ba = 0.0f;
+                        if (lane < DC) {
+                            const int v = cidx[lane * m + cstar];
+                            if (v < n) {
+                                bv = v;
+                                bc = 0;
+                                #pragma unroll
+                                for (int kk = 0; kk < DV; ++kk) {
+                                    const unsigned r = vent[kk * n + v] & 0x1fffu;
+                                    if (r < static_cast<unsigned>(m))
+                                        bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
+                                }
+                                ba = fabsf(lam[v]);
+                            }
+                        }
+                        #pragma unroll
+                        for (int o = 4; o > 0; o >>= 1) {
+                            const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                            const float oa = __shfl_xor_sync(0xffffffffu, ba, o);
+                            const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                            const bool better = oc > bc || (oc == bc && (oa < ba || (oa == ba && ov < bv)));
+                            if (better) { bc = oc; ba = oa; bv = ov; }
+                        }
+                        if (lane == 0 && bc >= 0) lam[bv] = -lam[bv];
+                    }
+                }
+                group_sync<G>(bar);
+            }
+            const int tmp = prev; prev = cur; cur = nxt; nxt = tmp;
+        }
+
+        // ---- results ------------------------------------------------------------
+        {
+            const int nw = G / 32;
+            const int gw = t >> 5;
+            uint32_t *err32 = reinterpret_cast<uint32_t *>(a.err + static_cast<size_t>(b) * wn64);
+            for (int w = gw; w < 2 * wn64; w += nw) {
+                const int v = w * 32 + lane;
+                const bool e = (v < n) && (lam[v] <= 0.0f);
+                const unsigned bits = __ballot_sync(0xffffffffu, e);
+                if (lane == 0) err32[w] = bits;
+            }
+            if (a.llr) {
+                float *dst = a.llr + static_cast<size_t>(b) * n;
+                for (int v = t; v < n; v += G) dst[v] = lam[v];
+            }
+            if (t == 0) {
+                a.conv[b] = converged ? 1 : 0;
+                a.iters[b] = converged ? it + 1 : I;
+                if (a.osd_out) a.osd_out[b] = LBP_OSD_NOT_RUN;
+            }
+            if (!converged && a.osd) {
+                if (t == 0) {
+                    const uint32_t slot = atomicAdd(&a.counters[1], 1u);
+                    a.osd_list[slot] = b;
+                    misc[1] = slot;
+                }
+                group_sync<G>(bar);
+                float *dst = a.osd_llr + static_cast<size_t>(misc[1]) * n;
+                for (int v = t; v < n; v += G) dst[v] = lam[v];
+            }
+        }
+        group_sync<G>(bar);
+    }
+}
+
+}  // namespace lbp

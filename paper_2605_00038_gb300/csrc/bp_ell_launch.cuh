@@ -1,0 +1,40 @@
+// Dispatch of bp_ell_kernel over the group width G and the degree bounds
+// (DC, DV) for one message type.
+#pragma once
+
+#include "launch.h"
+
+namespace lbp {
+
+template <typename MsgT, int G, int DC, int DV>
+int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    auto k = bp_ell_kernel<MsgT, G, DC, DV>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(s.smem)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBP_ECUDA;
+    }
+    k<<<s.grid, s.groups * G, s.smem, st>>>(a);
+    return LBP_OK;
+}
+
+template <typename MsgT, int DC, int DV>
+int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    switch (s.G) {
+        case 32: return launch_ell_one<MsgT, 32, DC, DV>(s, a, st);
+        case 64: return launch_ell_one<MsgT, 64, DC, DV>(s, a, st);
+        case 128: return launch_ell_one<MsgT, 128, DC, DV>(s, a, st);
+        case 256: return launch_ell_one<MsgT, 256, DC, DV>(s, a, st);
+        default: return LBP_ENOSYS;
+    }
+}
+
+template <typename MsgT>
+int launch_ell(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
+    if (DC == 6 && DV == 2) return launch_ell_g<MsgT, 6, 2>(s, a, st);
+    if (DC == 6 && DV == 3) return launch_ell_g<MsgT, 6, 3>(s, a, st);
+    if (DC == 8 && DV == 4) return launch_ell_g<MsgT, 8, 4>(s, a, st);
+    return LBP_ENOSYS;
+}
+
+}  // namespace lbp

@@ -26,6 +26,17 @@ struct GraphImage {
     uint32_t off_mu;         // f32[n]     prior LLR
 };
 
+// ELL image for bounded-degree codes (bp_ell_kernel): check side cidx[DC][m]
+// (column ids, padding n) and column side vent[DV][n] (slot << 13 | check,
+// padding m), both slot-major uint16, then mu[n + 1] with mu[n] = +inf.
+// Exists when every check has <= 8 ones, every column <= 4, m < 8191 and
+// n < 65535.
+struct EllImage {
+    uint32_t bytes;
+    uint32_t off_cidx, off_vent, off_mu;
+    int32_t DC, DV;
+};
+
 }  // namespace lbp
 
 struct lbp_code {
@@ -37,6 +48,9 @@ struct lbp_code {
     // Compact image (device), NULL when the sizes do not fit 16-bit indices.
     uint8_t *d_image;
     lbp::GraphImage img;
+    // ELL image (device), NULL when the code's degrees or sizes exceed it.
+    uint8_t *d_ell;
+    lbp::EllImage ell;
     // 32-bit device copies, used by OSD.
     int32_t *d_row_ptr, *d_col_idx;
     float *d_mu;

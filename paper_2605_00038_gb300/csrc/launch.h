@@ -1,0 +1,20 @@
+// Launch entry points of the BP kernels (one translation unit per message
+// type, so that nvcc compiles the instantiations in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bp_ell_kernel.cuh"
+
+namespace lbp {
+
+struct LaunchShape {
+    int grid, groups, G;
+    size_t smem;
+};
+
+int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+int launch_bp_ell_f16(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+int launch_bp_ell_i8(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+
+}  // namespace lbp

@@ -23,6 +23,7 @@ void release(lbp_code *c) {
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     cudaFree(c->d_image);
+    cudaFree(c->d_ell);
     cudaFree(c->d_row_ptr);
     cudaFree(c->d_col_idx);
     cudaFree(c->d_mu);
@@ -142,6 +143,43 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         put16(g.off_csc_row, csc_row.data(), nnz);
         if (n) std::memcpy(img.data() + g.off_mu, mu.data(), 4u * n);
         rc = upload(reinterpret_cast<void **>(&c->d_image), img.data(), off);
+    }
+    // ELL image for the bounded-degree kernel.
+    if (rc == LBP_OK && maxdeg <= 8 && maxcol <= 4 && m < 8191 && n < 65535) {
+        lbp::EllImage &e = c->ell;
+        // Supported (DC, DV) shapes: (6, 2), (6, 3), (8, 4).
+        if (maxdeg <= 6 && maxcol <= 2) { e.DC = 6; e.DV = 2; }
+        else if (maxdeg <= 6 && maxcol <= 3) { e.DC = 6; e.DV = 3; }
+        else { e.DC = 8; e.DV = 4; }
+        uint32_t off = 0;
+        e.off_cidx = off; off = align16(off + 2u * e.DC * m);
+        e.off_vent = off; off = align16(off + 2u * e.DV * n);
+        e.off_mu = off;   off = align16(off + 4u * (n + 1));
+        e.bytes = off;
+        std::vector<uint8_t> img(off, 0);
+        uint16_t *ci = reinterpret_cast<uint16_t *>(img.data() + e.off_cidx);
+        uint16_t *ve = reinterpret_cast<uint16_t *>(img.data() + e.off_vent);
+        float *mu_e = reinterpret_cast<float *>(img.data() + e.off_mu);
+        for (int32_t r = 0; r < m; ++r) {
+            const int32_t a = row_ptr[r], deg = row_ptr[r + 1] - a;
+            for (int k = 0; k < e.DC; ++k)
+                ci[static_cast<size_t>(k) * m + r] = static_cast<uint16_t>(k < deg ? col_idx[a + k] : n);
+        }
+        for (int32_t v = 0; v < n; ++v) {
+            const int32_t a = col_ptr[v], deg = col_ptr[v + 1] - a;
+            for (int k = 0; k < e.DV; ++k) {
+                uint16_t ent = static_cast<uint16_t>(m);          // padding: check m, slot 0
+                if (k < deg) {
+                    const int32_t r = csc_row[a + k];
+                    const int32_t slot = csc_edge[a + k] - row_ptr[r];
+                    ent = static_cast<uint16_t>((slot << 13) | r);
+                }
+                ve[static_cast<size_t>(k) * n + v] = ent;
+            }
+        }
+        for (int32_t v = 0; v < n; ++v) mu_e[v] = mu[v];
+        mu_e[n] = INFINITY;
+        rc = upload(reinterpret_cast<void **>(&c->d_ell), img.data(), off);
     }
     if (rc != LBP_OK) { release(c); return rc; }
     *out = c;

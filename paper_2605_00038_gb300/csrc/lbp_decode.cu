@@ -6,19 +6,28 @@
 // that keeps S * G <= 1024 threads).  K_osd follows on the same stream and
 // drains the queue K_bp filled; no host round trip separates them.
 //
+// With OSD on, K_osd_warp (one warp per shot, sparse-aware) drains the queue
+// first; K_osd (one CTA per shot, dense) then takes the shots it handed over.
+//
 // Workspace (caller-owned device memory), 256-byte aligned sections:
-//   counters   u32[64]  [0] next shot, [1] OSD queue length
+//   counters   u32[64]  [0] next shot, [1] OSD queue length, [2] handed over
 //   osd_list   u32[B]   shots handed to OSD            (osd only)
 //   osd_llr    f32[B][n] their final lambda            (osd only)
-//   osd_mat    u64[grid][m][ceil(n/64)] dense matrices (osd only, when they
-//                                                     do not fit shared memory)
+//   overflow   u32[B]   queue positions K_osd_warp handed over (osd only)
+//   osd_mat    u64[grid][m][ceil(n/64)] K_osd dense matrices (when they do
+//                                                     not fit shared memory)
+//   slots      u64[warps][C][ceil(n/64)] K_osd_warp dense-row pools
+//   gkeys      u64[warps][n_pad] K_osd_warp sort keys (when not in shared memory)
+#include <cstdlib>
 #include <cstring>
 
 #include <cuda_fp16.h>
 
 #include "bp_kernel.cuh"
 #include "internal.h"
+#include "launch.h"
 #include "osd_kernel.cuh"
+#include "osd_warp_kernel.cuh"
 #include "timing.h"
 
 namespace {
@@ -31,6 +40,7 @@ uint32_t align16u(uint32_t x) { return (x + 15u) & ~15u; }
 int msg_bytes(int msg) { return msg == LBP_MSG_F32 ? 4 : (msg == LBP_MSG_F16 ? 2 : 1); }
 
 struct BpPlan {
+    bool ell = false;
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -43,8 +53,18 @@ struct OsdPlan {
     size_t smem = 0;
 };
 
+struct OsdWarpPlan {
+    bool ok = false, keys_smem = false;
+    int warps = 0, grid = 0, C = 0, wn = 0, n_pad = 1;
+    uint32_t region = 0, off_perm = 0, off_inv = 0, off_rflag = 0, off_pivb = 0, off_saug = 0,
+             off_x = 0, off_ebits = 0, off_low = 0, off_mlist = 0, off_pcol = 0, off_prow = 0,
+             off_keys = 0;
+    size_t smem = 0;
+};
+
 struct WsLayout {
-    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, total = 0;
+    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, overflow = 0, slots = 0, gkeys = 0,
+           total = 0;
 };
 
 int validate_params(const lbp_params *p) {
@@ -63,19 +83,32 @@ int validate_params(const lbp_params *p) {
 // Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
 // group does not fit in shared memory.
 int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out) {
-    if (!c->d_image) return LBP_ENOSYS;
     const int W32 = (c->m + 31) / 32;
     BpPlan p;
+    // Bounded-degree ELL kernel when the code has an ELL image that fits.
     uint32_t off = 0;
-    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->nnz);
-    p.off_lam = off;  off = align16u(off + 4u * c->n);
+    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * (c->m + 1));
+    p.off_lam = off;  off = align16u(off + 4u * (c->n + 1));
     p.off_s = off;    off = align16u(off + 4u * W32);
     p.off_shat = off; off = align16u(off + 12u * W32);
     p.off_misc = off; off = align16u(off + 16u);
     p.state_bytes = off;
+    size_t image = c->ell.bytes;
+    p.ell = c->d_ell != nullptr && image + off <= static_cast<size_t>(c->smem_optin);
+    if (!p.ell) {
+        if (!c->d_image) return LBP_ENOSYS;
+        off = 0;
+        p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->nnz);
+        p.off_lam = off;  off = align16u(off + 4u * c->n);
+        p.off_s = off;    off = align16u(off + 4u * W32);
+        p.off_shat = off; off = align16u(off + 12u * W32);
+        p.off_misc = off; off = align16u(off + 16u);
+        p.state_bytes = off;
+        image = c->img.bytes;
+    }
     const size_t budget = static_cast<size_t>(c->smem_optin);
-    if (c->img.bytes + static_cast<size_t>(p.state_bytes) > budget) return LBP_ENOSYS;
-    int S = static_cast<int>((budget - c->img.bytes) / p.state_bytes);
+    if (image + static_cast<size_t>(p.state_bytes) > budget) return LBP_ENOSYS;
+    int S = static_cast<int>((budget - image) / p.state_bytes);
     // Threads per group: enough to cover the checks, at most 256.
     int G = 32;
     while (G < 256 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
@@ -84,7 +117,7 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out) {
     if (S < 1) S = 1;
     p.groups = S;
     p.G = G;
-    p.smem = c->img.bytes + static_cast<size_t>(S) * p.state_bytes;
+    p.smem = image + static_cast<size_t>(S) * p.state_bytes;
     const int64_t need = (num_shots + S - 1) / S;
     p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
     if (p.grid < 1) p.grid = 1;
@@ -113,16 +146,76 @@ int plan_osd(const lbp_code *c, int64_t num_shots, OsdPlan *out) {
     return LBP_OK;
 }
 
-WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, const OsdPlan *op) {
+// K_osd_warp plan: per-warp shared region [perm | inv | union(keys, state)].
+void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
+    OsdWarpPlan p;
+    if (!c->d_image || c->n < 1) { *out = p; return; }
+    p.wn = (c->n + 63) / 64;
+    while (p.n_pad < c->n) p.n_pad <<= 1;
+    p.C = c->m < 192 ? c->m : 192;
+    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
+        const int v = std::atoi(env);
+        if (v > 0 && v < p.C) p.C = v;
+    }
+    if (p.C < 1) p.C = 1;
+    const int W32 = (c->m + 31) / 32;
+    uint32_t off = 0;
+    p.off_perm = off; off = align16u(off + 2u * c->n);
+    p.off_inv = off;  off = align16u(off + 2u * c->n);
+    const uint32_t u0 = off;
+    p.off_rflag = off; off = align16u(off + 2u * c->m);
+    p.off_pivb = off;  off = align16u(off + 4u * W32);
+    p.off_saug = off;  off = align16u(off + 4u * W32);
+    p.off_x = off;     off = align16u(off + 8u * p.wn);
+    p.off_ebits = off; off = align16u(off + 8u * p.wn);
+    p.off_low = off;   off = align16u(off + 2u * p.C);
+    p.off_mlist = off; off = align16u(off + 2u * p.C);
+    p.off_pcol = off;  off = align16u(off + 2u * c->m);
+    p.off_prow = off;  off = align16u(off + 2u * c->m);
+    const uint32_t state_end = off;
+    p.off_keys = u0;
+    const uint32_t keys_end = u0 + 8u * static_cast<uint32_t>(p.n_pad);
+    const size_t budget = static_cast<size_t>(c->smem_optin) - c->img.bytes;
+    const uint32_t with_keys = align16u(keys_end > state_end ? keys_end : state_end);
+    const uint32_t without = align16u(state_end);
+    // Prefer keys in shared memory when at least 4 warps fit that way.
+    if (static_cast<size_t>(with_keys) * 4 <= budget) {
+        p.keys_smem = true;
+        p.region = with_keys;
+    } else if (static_cast<size_t>(without) * 2 <= budget) {
+        p.keys_smem = false;
+        p.region = without;
+    } else {
+        *out = p;
+        return;
+    }
+    p.warps = static_cast<int>(budget / p.region);
+    if (p.warps > 8) p.warps = 8;
+    p.smem = c->img.bytes + static_cast<size_t>(p.warps) * p.region;
+    const int64_t need = (num_shots + p.warps - 1) / p.warps;
+    p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
+    if (p.grid < 1) p.grid = 1;
+    p.ok = true;
+    *out = p;
+}
+
+WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, const OsdPlan *op,
+                const OsdWarpPlan *wp) {
     WsLayout w;
     size_t off = 0;
     w.counters = off; off = align256(off + 256);
     if (prm->osd) {
         w.osd_list = off; off = align256(off + 4ull * num_shots);
         w.osd_llr = off;  off = align256(off + 4ull * num_shots * c->n);
+        w.overflow = off; off = align256(off + 4ull * num_shots);
         if (op && !op->smem_mat) {
             w.osd_mat = off;
             off = align256(off + 8ull * op->grid * c->m * op->wn);
+        }
+        if (wp && wp->ok) {
+            const size_t warps = static_cast<size_t>(wp->grid) * wp->warps;
+            w.slots = off; off = align256(off + 8ull * warps * wp->C * wp->wn);
+            if (!wp->keys_smem) { w.gkeys = off; off = align256(off + 8ull * warps * wp->n_pad); }
         }
     }
     w.total = off;
@@ -171,11 +264,13 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
     int rc = plan_bp(c, prm->msg, B, &bp);
     if (rc) return rc;
     OsdPlan op;
+    OsdWarpPlan wp;
     if (prm->osd) {
         rc = plan_osd(c, B, &op);
         if (rc) return rc;
+        plan_osd_warp(c, B, &wp);
     }
-    const WsLayout w = layout(c, prm, B, prm->osd ? &op : nullptr);
+    const WsLayout w = layout(c, prm, B, prm->osd ? &op : nullptr, prm->osd ? &wp : nullptr);
     if (!ws || ws_bytes < w.total) return LBP_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) & 255u) return LBP_EINVAL;
     uint8_t *base = static_cast<uint8_t *>(ws);
@@ -199,22 +294,73 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
     a.off_beta = bp.off_beta; a.off_lam = bp.off_lam; a.off_s = bp.off_s;
     a.off_shat = bp.off_shat; a.off_misc = bp.off_misc;
     void *tk = timing_begin(stream);
-    switch (prm->msg) {
-        case LBP_MSG_F32: rc = launch_bp_t<float>(bp, a, stream); break;
-        case LBP_MSG_F16: rc = launch_bp_t<__half>(bp, a, stream); break;
-        default: rc = launch_bp_t<int8_t>(bp, a, stream); break;
+    if (bp.ell) {
+        BpEllArgs e;
+        std::memset(&e, 0, sizeof(e));
+        e.image = c->d_ell;
+        e.img = c->ell;
+        e.m = a.m; e.n = a.n; e.max_iter = a.max_iter; e.scale_mode = a.scale_mode;
+        e.scale_const = a.scale_const; e.lottery = a.lottery; e.lottery_skip = a.lottery_skip;
+        e.osd = a.osd; e.seed = a.seed; e.shot_offset = a.shot_offset; e.num_shots = a.num_shots;
+        e.syn = a.syn; e.err = a.err; e.conv = a.conv; e.osd_out = a.osd_out; e.iters = a.iters;
+        e.llr = a.llr; e.counters = a.counters; e.osd_list = a.osd_list; e.osd_llr = a.osd_llr;
+        e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
+        e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
+        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem};
+        switch (prm->msg) {
+            case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, e, c->ell.DC, c->ell.DV, stream); break;
+            case LBP_MSG_F16: rc = launch_bp_ell_f16(shp, e, c->ell.DC, c->ell.DV, stream); break;
+            default: rc = launch_bp_ell_i8(shp, e, c->ell.DC, c->ell.DV, stream); break;
+        }
+    } else {
+        switch (prm->msg) {
+            case LBP_MSG_F32: rc = launch_bp_t<float>(bp, a, stream); break;
+            case LBP_MSG_F16: rc = launch_bp_t<__half>(bp, a, stream); break;
+            default: rc = launch_bp_t<int8_t>(bp, a, stream); break;
+        }
     }
     timing_end(tk, stream, kTimeBp);
     if (rc) return rc;
     rc = check_launch();
     if (rc) return rc;
     if (prm->osd) {
+        if (wp.ok) {
+            OsdWarpArgs ow;
+            std::memset(&ow, 0, sizeof(ow));
+            ow.image = c->d_image;
+            ow.img = c->img;
+            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.n_pad = wp.n_pad; ow.C = wp.C;
+            ow.syn = syn; ow.err = err; ow.osd_out = osd_out;
+            ow.counters = counters;
+            ow.osd_list = a.osd_list; ow.osd_llr = a.osd_llr;
+            ow.overflow = reinterpret_cast<uint32_t *>(base + w.overflow);
+            ow.slots = reinterpret_cast<uint64_t *>(base + w.slots);
+            ow.gkeys = wp.keys_smem ? nullptr : reinterpret_cast<uint64_t *>(base + w.gkeys);
+            ow.region_bytes = wp.region;
+            ow.off_perm = wp.off_perm; ow.off_inv = wp.off_inv; ow.off_rflag = wp.off_rflag;
+            ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
+            ow.off_ebits = wp.off_ebits; ow.off_low = wp.off_low; ow.off_mlist = wp.off_mlist;
+            ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_keys = wp.off_keys;
+            rc = set_smem(wp.keys_smem ? osd_warp_kernel<true> : osd_warp_kernel<false>, wp.smem);
+            if (rc) return rc;
+            void *tw = timing_begin(stream);
+            if (wp.keys_smem) {
+                osd_warp_kernel<true><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
+            } else {
+                osd_warp_kernel<false><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
+            }
+            timing_end(tw, stream, kTimeOsd);
+            rc = check_launch();
+            if (rc) return rc;
+        }
         OsdArgs o;
         std::memset(&o, 0, sizeof(o));
         o.m = c->m; o.n = c->n;
         o.row_ptr = c->d_row_ptr; o.col_idx = c->d_col_idx;
         o.syn = syn; o.err = err; o.osd_out = osd_out;
         o.counters = counters;
+        o.count_slot = wp.ok ? 2 : 1;
+        o.qmap = wp.ok ? reinterpret_cast<const uint32_t *>(base + w.overflow) : nullptr;
         o.osd_list = a.osd_list; o.osd_llr = a.osd_llr;
         o.gmat = op.smem_mat ? nullptr : reinterpret_cast<uint64_t *>(base + w.osd_mat);
         o.n_pad = op.n_pad; o.wn = op.wn;
@@ -247,8 +393,12 @@ int check_common(const lbp_code *c, const lbp_params *prm, int64_t B) {
 extern "C" size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots) {
     if (check_common(code, params, num_shots)) return 0;
     OsdPlan op;
-    if (params->osd && plan_osd(code, num_shots, &op)) return 0;
-    return layout(code, params, num_shots, params->osd ? &op : nullptr).total;
+    OsdWarpPlan wp;
+    if (params->osd) {
+        if (plan_osd(code, num_shots, &op)) return 0;
+        plan_osd_warp(code, num_shots, &wp);
+    }
+    return layout(code, params, num_shots, params->osd ? &op : nullptr, params->osd ? &wp : nullptr).total;
 }
 
 extern "C" int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots,

@@ -1,7 +1,7 @@
-// K_osd: OSD-0 (Alg. 2) on the shots BP did not converge on.
-//
-// One CTA per failed shot (persistent over the OSD queue the BP kernel
-// filled).  Per shot:
+// K_osd: OSD-0 (Alg. 2), one CTA per shot, dense rows.  This is the general
+// path: it serves codes whose sizes do not fit the 16-bit shared-memory
+// image, and the shots K_osd_warp hands over because their elimination
+// needed more dense rows than its pool holds.  Per shot:
 //   1. sort lambda ascending, ties by column (bitonic sort of 64-bit keys
 //      (order-preserving bits of lambda, column) in shared memory), which
 //      defines the permutation pi of the LLR sorting step;
@@ -38,7 +38,9 @@ struct OsdArgs {
     const uint64_t *syn;       // [B][wm64]
     uint64_t *err;             // [B][wn64]
     uint8_t *osd_out;          // [B] or null
-    const unsigned int *counters;   // [1] = queue length
+    const unsigned int *counters;   // queue lengths
+    int count_slot;            // counters[count_slot] = entries to process
+    const uint32_t *qmap;      // entry -> OSD queue position (null: identity)
     const uint32_t *osd_list;
     const float *osd_llr;
     uint64_t *gmat;            // per-CTA dense matrices when not in shared memory
@@ -70,9 +72,10 @@ __global__ void __launch_bounds__(1024, 1) osd_kernel(const OsdArgs a) {
 
     const int m = a.m, n = a.n, wn = a.wn, T = blockDim.x, tid = threadIdx.x;
     const int wm64 = (m + 63) >> 6;
-    const uint32_t queue = a.counters[1];
+    const uint32_t queue = a.counters[a.count_slot];
 
-    for (uint32_t q = blockIdx.x; q < queue; q += gridDim.x) {
+    for (uint32_t qi = blockIdx.x; qi < queue; qi += gridDim.x) {
+        const uint32_t q = a.qmap ? a.qmap[qi] : qi;
         const uint32_t b = a.osd_list[q];
         const float *lam = a.osd_llr + static_cast<size_t>(q) * n;
 

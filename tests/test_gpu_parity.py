@@ -140,6 +140,39 @@ def test_osd_bit_exact_on_gpu_llrs():
             assert np.array_equal(g["err"][b], e)
 
 
+@pytest.mark.parametrize("pool", ["1", "3"])
+def test_osd_pool_overflow_falls_back_to_block_kernel(pool, monkeypatch):
+    """A tiny dense-row pool sends most OSD shots to the block-wide kernel;
+    results stay bit-identical."""
+    monkeypatch.setenv("LBP_OSD_POOL_ROWS", pool)
+    for h, pri, msg in [(workloads.c3_bb144(0.05).h, np.full(144, 0.05), lbp.LBP_MSG_F16),
+                        (workloads.c2_d11_spacetime().h, workloads.c2_d11_spacetime().priors,
+                         lbp.LBP_MSG_F32)]:
+        _, syn = sampler.sample(h, pri, seed=31, num_shots=800)
+        kw = dict(max_iter=60, lottery=1, osd=1, msg=msg, seed=4)
+        g = gpu_decode(h, pri, syn, **kw)
+        assert_parity(g, oracle_decode(h, pri, syn, **kw))
+        assert (g["osd"] != lbp.LBP_OSD_NOT_RUN).sum() > 10
+
+
+def test_general_kernel_on_high_degree_code():
+    """Row weights up to 12 and column weights up to 7 exceed the bounded-degree
+    layout, so this runs the general CSR kernel."""
+    rng = np.random.default_rng(5)
+    m, n = 60, 150
+    rows = []
+    for r in range(m):
+        w = int(rng.integers(2, 13))
+        rows.append(sorted(rng.choice(n, size=w, replace=False).tolist()))
+    h = SparseH.from_rows(rows, n)
+    assert h.row_weights().max() > 8 and h.col_weights().max() > 4
+    pri = np.full(n, 0.03)
+    _, syn = sampler.sample(h, pri, seed=12, num_shots=1500)
+    for msg in (lbp.LBP_MSG_F32, lbp.LBP_MSG_I8):
+        kw = dict(max_iter=50, lottery=1, lottery_skip=2, osd=1, msg=msg, seed=6)
+        assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
+
+
 # -------------------------------------------------------------- edge cases
 
 def test_ragged_sizes_and_tails():
