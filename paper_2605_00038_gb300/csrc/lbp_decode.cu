@@ -17,7 +17,6 @@
 //   osd_mat    u64[grid][m][ceil(n/64)] K_osd dense matrices (when they do
 //                                                     not fit shared memory)
 //   slots      u64[warps][C][ceil(n/64)] K_osd_warp dense-row pools
-//   gkeys      u64[warps][n_pad] K_osd_warp sort keys (when not in shared memory)
 #include <cstdlib>
 #include <cstring>
 
@@ -54,17 +53,15 @@ struct OsdPlan {
 };
 
 struct OsdWarpPlan {
-    bool ok = false, keys_smem = false;
-    int warps = 0, grid = 0, C = 0, wn = 0, n_pad = 1;
-    uint32_t region = 0, off_perm = 0, off_inv = 0, off_rflag = 0, off_pivb = 0, off_saug = 0,
-             off_x = 0, off_ebits = 0, off_low = 0, off_mlist = 0, off_pcol = 0, off_prow = 0,
-             off_keys = 0;
+    bool ok = false;
+    int warps = 0, grid = 0, C = 0, wn = 0, m_pad = 1;
+    uint32_t image = 0, region = 0, off_keys = 0, off_rflag = 0, off_pivk = 0, off_pivb = 0,
+             off_saug = 0, off_x = 0, off_pcol = 0, off_prow = 0, off_pend = 0;
     size_t smem = 0;
 };
 
 struct WsLayout {
-    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, overflow = 0, slots = 0, gkeys = 0,
-           total = 0;
+    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, overflow = 0, slots = 0, total = 0;
 };
 
 int validate_params(const lbp_params *p) {
@@ -146,52 +143,37 @@ int plan_osd(const lbp_code *c, int64_t num_shots, OsdPlan *out) {
     return LBP_OK;
 }
 
-// K_osd_warp plan: per-warp shared region [perm | inv | union(keys, state)].
+// K_osd_warp plan: CSR prefix of the 16-bit image, then one region per warp.
+constexpr int kOsdMaxWarps = 16;
+
 void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     OsdWarpPlan p;
-    if (!c->d_image || c->n < 1) { *out = p; return; }
+    if (!c->d_image || c->m < 1 || c->n < 1) { *out = p; return; }
     p.wn = (c->n + 63) / 64;
-    while (p.n_pad < c->n) p.n_pad <<= 1;
+    while (p.m_pad < c->m) p.m_pad <<= 1;
     p.C = c->m < 192 ? c->m : 192;
     if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
         const int v = std::atoi(env);
         if (v > 0 && v < p.C) p.C = v;
     }
-    if (p.C < 1) p.C = 1;
     const int W32 = (c->m + 31) / 32;
     uint32_t off = 0;
-    p.off_perm = off; off = align16u(off + 2u * c->n);
-    p.off_inv = off;  off = align16u(off + 2u * c->n);
-    const uint32_t u0 = off;
+    p.off_keys = off;  off = align16u(off + 8u * p.m_pad);
     p.off_rflag = off; off = align16u(off + 2u * c->m);
+    p.off_pivk = off;  off = align16u(off + 2u * c->n);
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);
     p.off_x = off;     off = align16u(off + 8u * p.wn);
-    p.off_ebits = off; off = align16u(off + 8u * p.wn);
-    p.off_low = off;   off = align16u(off + 2u * p.C);
-    p.off_mlist = off; off = align16u(off + 2u * p.C);
     p.off_pcol = off;  off = align16u(off + 2u * c->m);
     p.off_prow = off;  off = align16u(off + 2u * c->m);
-    const uint32_t state_end = off;
-    p.off_keys = u0;
-    const uint32_t keys_end = u0 + 8u * static_cast<uint32_t>(p.n_pad);
-    const size_t budget = static_cast<size_t>(c->smem_optin) - c->img.bytes;
-    const uint32_t with_keys = align16u(keys_end > state_end ? keys_end : state_end);
-    const uint32_t without = align16u(state_end);
-    // Prefer keys in shared memory when at least 4 warps fit that way.
-    if (static_cast<size_t>(with_keys) * 4 <= budget) {
-        p.keys_smem = true;
-        p.region = with_keys;
-    } else if (static_cast<size_t>(without) * 2 <= budget) {
-        p.keys_smem = false;
-        p.region = without;
-    } else {
-        *out = p;
-        return;
-    }
+    p.off_pend = off;  off = align16u(off + 8u * p.C);
+    p.region = off;
+    p.image = c->img.off_col_ptr;             // row_ptr and col_idx only
+    const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
+    if (static_cast<size_t>(p.region) * 2 > budget) { *out = p; return; }
     p.warps = static_cast<int>(budget / p.region);
-    if (p.warps > 8) p.warps = 8;
-    p.smem = c->img.bytes + static_cast<size_t>(p.warps) * p.region;
+    if (p.warps > kOsdMaxWarps) p.warps = kOsdMaxWarps;
+    p.smem = p.image + static_cast<size_t>(p.warps) * p.region;
     const int64_t need = (num_shots + p.warps - 1) / p.warps;
     p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
     if (p.grid < 1) p.grid = 1;
@@ -215,7 +197,6 @@ WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, con
         if (wp && wp->ok) {
             const size_t warps = static_cast<size_t>(wp->grid) * wp->warps;
             w.slots = off; off = align256(off + 8ull * warps * wp->C * wp->wn);
-            if (!wp->keys_smem) { w.gkeys = off; off = align256(off + 8ull * warps * wp->n_pad); }
         }
     }
     w.total = off;
@@ -329,26 +310,21 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
             std::memset(&ow, 0, sizeof(ow));
             ow.image = c->d_image;
             ow.img = c->img;
-            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.n_pad = wp.n_pad; ow.C = wp.C;
+            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.m_pad = wp.m_pad; ow.C = wp.C;
             ow.syn = syn; ow.err = err; ow.osd_out = osd_out;
             ow.counters = counters;
             ow.osd_list = a.osd_list; ow.osd_llr = a.osd_llr;
             ow.overflow = reinterpret_cast<uint32_t *>(base + w.overflow);
             ow.slots = reinterpret_cast<uint64_t *>(base + w.slots);
-            ow.gkeys = wp.keys_smem ? nullptr : reinterpret_cast<uint64_t *>(base + w.gkeys);
+            ow.image_bytes = wp.image;
             ow.region_bytes = wp.region;
-            ow.off_perm = wp.off_perm; ow.off_inv = wp.off_inv; ow.off_rflag = wp.off_rflag;
+            ow.off_keys = wp.off_keys; ow.off_rflag = wp.off_rflag; ow.off_pivk = wp.off_pivk;
             ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
-            ow.off_ebits = wp.off_ebits; ow.off_low = wp.off_low; ow.off_mlist = wp.off_mlist;
-            ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_keys = wp.off_keys;
-            rc = set_smem(wp.keys_smem ? osd_warp_kernel<true> : osd_warp_kernel<false>, wp.smem);
+            ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
+            rc = set_smem(osd_warp_kernel<kOsdMaxWarps>, wp.smem);
             if (rc) return rc;
             void *tw = timing_begin(stream);
-            if (wp.keys_smem) {
-                osd_warp_kernel<true><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
-            } else {
-                osd_warp_kernel<false><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
-            }
+            osd_warp_kernel<kOsdMaxWarps><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
             timing_end(tw, stream, kTimeOsd);
             rc = check_launch();
             if (rc) return rc;

@@ -1,26 +1,37 @@
-// K_osd_warp: OSD-0 (Alg. 2), one warp per shot, exploiting that H stays
-// sparse during the elimination.
+// K_osd_warp: OSD-0 (Alg. 2), one warp per shot, event-driven elimination.
 //
-// Per shot:
-//  1. LLR sorting: warp bitonic sort of 64-bit keys (order-preserving bits of
-//     lambda, column) gives pi: perm[j] = column at position j, inv = pi^-1.
-//  2. Basis selection with the L/U factorisation folded in (forward
-//     elimination in permuted column order): at position j the candidates are
-//     the non-pivot rows with a one there.  The lowest such row becomes the
-//     pivot of j (so j joins the basis S, the first rank(H) independent
-//     columns) and every other candidate is replaced by its sum with the
-//     pivot row, syndrome bit included (forward substitution).  Non-pivot
-//     rows never hold a one left of j, so "row r has a one at j" is "j is
-//     r's lowest position".
-//  3. Backward substitution over the pivots in reverse order:
-//     e_S[k] = s'[p_k] xor <row p_k, e_S at later positions>; positions
-//     outside S are zero; the estimate maps back through pi.
-// A row that no elimination touched is still a row of H: its ones are the
-// positions inv[v] of its columns, read from the CSR image in shared memory.
-// Only rows that an elimination changes get a dense 64-bit copy, from a
-// per-warp pool of C rows in the workspace (measured: about 40 rows per shot
-// on the d=11 space-time code, 35 on BB [[144,12,12]]).  A shot that needs
-// more than C dense rows is handed to the block-wide kernel K_osd unchanged.
+// Alg. 2 sorts the columns by lambda (pi), takes the first rank(H) columns of
+// H P_pi that are independent (basis S), solves H_S e_S = s by LU with
+// forward and backward substitution and sets every other column to zero.
+// This kernel computes exactly that e, without materialising P_pi:
+//
+//  * Column order.  Column v has the key K(v) = (order-preserving bits of
+//    lambda_v, v): ascending K is the sorted order of Alg. 2 (ties by column).
+//  * Forward elimination as events.  Scanning columns in K order, a row of H
+//    first meets the scan at the smallest key among its columns; a row that
+//    an elimination changed meets it again at the smallest key among its new
+//    columns.  At the column v of an event, the rows meeting there are the
+//    candidates: the lowest-numbered becomes the pivot of v (v joins S) and
+//    every other candidate becomes its sum with the pivot row, syndrome bit
+//    included, then waits for its next event.  Columns where no row meets are
+//    dependent on earlier ones and skipped.  So the scan costs one event per
+//    row plus one per elimination, not one step per column.
+//  * Rows are sorted once by their first key (warp bitonic sort of
+//    (K, row) pairs).  Runs of events that concern a single row, with no
+//    changed row waiting at or before them, commit 32 at a time: each lane's
+//    row becomes the pivot of its column.  Events with several rows are
+//    handled one at a time.
+//  * Only changed rows are stored densely (bits by original column), in a
+//    per-warp pool of C rows in the workspace; untouched rows are read from
+//    the CSR image of H.  Measured: about 40 changed rows per shot on the d=11
+//    space-time code.  A shot that needs more than C rows goes to the
+//    block-wide kernel K_osd, which computes the same e.
+//  * Backward substitution over the pivots in reverse order, 32 per batch:
+//    each lane folds in the solution bits of later batches and records which
+//    pivots of its own batch its row touches; a 32-step scan then resolves the
+//    batch from its last pivot down.  The solution bits sit at the original
+//    column indices, so they are the output directly (no inverse
+//    permutation).
 #pragma once
 
 #include <cstdint>
@@ -30,69 +41,71 @@
 namespace lbp {
 
 struct OsdWarpArgs {
-    const uint8_t *image;
+    const uint8_t *image;          // CSR image (GraphImage layout); only row_ptr / col_idx are read
     GraphImage img;
-    int32_t m, n, wn, n_pad, C;
+    int32_t m, n, wn, m_pad, C;
     const uint64_t *syn;
     uint64_t *err;
     uint8_t *osd_out;
-    unsigned int *counters;        // [1] queue length, [2] overflow count
+    unsigned int *counters;        // [1] queue length, [2] handed over to K_osd
     const uint32_t *osd_list;
     const float *osd_llr;
     uint32_t *overflow;            // queue positions handed to K_osd
     uint64_t *slots;               // [total warps][C][wn] dense rows
-    uint64_t *gkeys;               // [total warps][n_pad] sort keys when not in shared memory
+    uint32_t image_bytes;          // bytes of the image prefix staged (row_ptr + col_idx)
     uint32_t region_bytes;         // per-warp shared memory
-    uint32_t off_perm, off_inv, off_rflag, off_pivb, off_saug, off_x, off_ebits, off_low,
-        off_mlist, off_pcol, off_prow, off_keys;
+    uint32_t off_keys, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow, off_pend;
 };
 
-__device__ __forceinline__ uint32_t osd_order_bits(float x) {
-    const uint32_t u = __float_as_uint(__fadd_rn(x, 0.0f));   // -0 -> +0
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+constexpr uint64_t kNoKey = ~0ull;
+
+// 48-bit column key: order-preserving bits of lambda (ties: column index).
+__device__ __forceinline__ uint64_t col_key(const float *lam, int v) {
+    const uint32_t u = __float_as_uint(__fadd_rn(__ldg(lam + v), 0.0f));   // -0 -> +0
+    const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return (static_cast<uint64_t>(o) << 16) | static_cast<uint32_t>(v);
 }
 
-__device__ __forceinline__ unsigned warp_parity(unsigned bit) {
-    return __popc(__ballot_sync(0xffffffffu, bit & 1u)) & 1u;
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
 }
 
-template <bool kKeysSmem>
-__global__ void __launch_bounds__(256) osd_warp_kernel(const OsdWarpArgs a) {
+template <int MaxWarps>
+__global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
         int4 *dst = reinterpret_cast<int4 *>(smem);
-        const int words = static_cast<int>(a.img.bytes >> 4);
+        const int words = static_cast<int>(a.image_bytes >> 4);
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
     const uint16_t *row_ptr = reinterpret_cast<const uint16_t *>(smem + a.img.off_row_ptr);
     const uint16_t *col_idx = reinterpret_cast<const uint16_t *>(smem + a.img.off_col_idx);
-    const uint16_t *col_ptr = reinterpret_cast<const uint16_t *>(smem + a.img.off_col_ptr);
-    const uint16_t *csc_row = reinterpret_cast<const uint16_t *>(smem + a.img.off_csc_row);
 
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
     const int total = gridDim.x * (blockDim.x >> 5);
-    uint8_t *reg = smem + a.img.bytes + static_cast<size_t>(wid) * a.region_bytes;
-    uint16_t *perm = reinterpret_cast<uint16_t *>(reg + a.off_perm);
-    uint16_t *inv = reinterpret_cast<uint16_t *>(reg + a.off_inv);
-    uint16_t *rflag = reinterpret_cast<uint16_t *>(reg + a.off_rflag);   // 0xffff: still a row of H
-    uint32_t *pivb = reinterpret_cast<uint32_t *>(reg + a.off_pivb);
-    uint32_t *saug = reinterpret_cast<uint32_t *>(reg + a.off_saug);
-    uint64_t *X = reinterpret_cast<uint64_t *>(reg + a.off_x);
+    uint8_t *reg = smem + a.image_bytes + static_cast<size_t>(wid) * a.region_bytes;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(reg + a.off_keys);     // [m_pad] (K << 16 | row)
+    uint16_t *rflag = reinterpret_cast<uint16_t *>(reg + a.off_rflag);   // [m] dense slot or 0xffff
+    uint16_t *pivk = reinterpret_cast<uint16_t *>(reg + a.off_pivk);     // [n] pivot index of column
+    uint32_t *pivb = reinterpret_cast<uint32_t *>(reg + a.off_pivb);     // [W32] row is a pivot
+    uint32_t *saug = reinterpret_cast<uint32_t *>(reg + a.off_saug);     // [W32] reduced syndrome
+    uint64_t *X = reinterpret_cast<uint64_t *>(reg + a.off_x);           // [wn] solution by column
     uint32_t *X32 = reinterpret_cast<uint32_t *>(X);
-    uint32_t *ebits = reinterpret_cast<uint32_t *>(reg + a.off_ebits);
-    uint16_t *low = reinterpret_cast<uint16_t *>(reg + a.off_low);      // per slot: lowest position
-    uint16_t *mlist = reinterpret_cast<uint16_t *>(reg + a.off_mlist);  // dense non-pivot rows
-    uint16_t *pcol = reinterpret_cast<uint16_t *>(reg + a.off_pcol);
-    uint16_t *prow = reinterpret_cast<uint16_t *>(reg + a.off_prow);
-    uint64_t *keys = kKeysSmem ? reinterpret_cast<uint64_t *>(reg + a.off_keys)
-                               : a.gkeys + static_cast<size_t>(gw) * a.n_pad;
+    uint16_t *pcol = reinterpret_cast<uint16_t *>(reg + a.off_pcol);     // [m] column of pivot k
+    uint16_t *prow = reinterpret_cast<uint16_t *>(reg + a.off_prow);     // [m] row of pivot k
+    uint64_t *pend = reinterpret_cast<uint64_t *>(reg + a.off_pend);     // [C] waiting changed rows
     uint64_t *slots = a.slots + static_cast<size_t>(gw) * a.C * a.wn;
 
-    const int m = a.m, n = a.n, wn = a.wn, C = a.C;
+    const int m = a.m, n = a.n, wn = a.wn, C = a.C, m_pad = a.m_pad;
     const int W32 = (m + 31) >> 5;
     const int wm64 = (m + 63) >> 6;
     const uint32_t queue = a.counters[1];
@@ -101,14 +114,32 @@ __global__ void __launch_bounds__(256) osd_warp_kernel(const OsdWarpArgs a) {
         const uint32_t b = a.osd_list[q];
         const float *lam = a.osd_llr + static_cast<size_t>(q) * n;
 
-        // ---- 1. sort -------------------------------------------------------
-        for (int j = lane; j < a.n_pad; j += 32)
-            keys[j] = (j < n) ? ((static_cast<uint64_t>(osd_order_bits(lam[j])) << 32) | static_cast<uint32_t>(j))
-                              : ~0ull;
+        // ---- rows keyed by their first column, sorted -----------------------
+        for (int r = lane; r < m_pad; r += 32) {
+            uint64_t k = kNoKey;
+            if (r < m) {
+                for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                    const uint64_t kc = col_key(lam, col_idx[e]);
+                    k = kc < k ? kc : k;
+                }
+                if (k != kNoKey) k = (k << 16) | static_cast<uint32_t>(r);
+            }
+            keys[r] = k;
+        }
+        for (int r = lane; r < m; r += 32) rflag[r] = 0xffffu;
+        for (int v = lane; v < n; v += 32) pivk[v] = 0xffffu;
+        const uint32_t *sp = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
+        for (int w = lane; w < W32; w += 32) {
+            uint32_t x = sp[w];
+            if (w == W32 - 1 && (m & 31)) x &= (1u << (m & 31)) - 1u;
+            saug[w] = x;
+            pivb[w] = 0u;
+        }
+        for (int w = lane; w < wn; w += 32) X[w] = 0ull;
         __syncwarp();
-        for (int k = 2; k <= a.n_pad; k <<= 1) {
+        for (int k = 2; k <= m_pad; k <<= 1) {
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int i = lane; i < a.n_pad; i += 32) {
+                for (int i = lane; i < m_pad; i += 32) {
                     const int l = i ^ jj;
                     if (l > i) {
                         const uint64_t x = keys[i], y = keys[l];
@@ -118,159 +149,176 @@ __global__ void __launch_bounds__(256) osd_warp_kernel(const OsdWarpArgs a) {
                 __syncwarp();
             }
         }
-        for (int j = lane; j < n; j += 32) {
-            const uint16_t v = static_cast<uint16_t>(keys[j]);
-            perm[j] = v;
-            inv[v] = static_cast<uint16_t>(j);
-        }
-        __syncwarp();
 
-        // ---- 2. state ----------------------------------------------------------
-        const uint32_t *sp = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
-        for (int r = lane; r < m; r += 32) rflag[r] = 0xffffu;
-        for (int w = lane; w < W32; w += 32) {
-            uint32_t x = sp[w];
-            if (w == W32 - 1 && (m & 31)) x &= (1u << (m & 31)) - 1u;
-            saug[w] = x;
-            pivb[w] = 0u;
-        }
-        for (int w = lane; w < wn; w += 32) X[w] = 0ull;
-        __syncwarp();
-
-        int rank = 0, M = 0, nslots = 0;
+        // ---- forward elimination, event by event ------------------------------
+        int ptr = 0, rank = 0, npend = 0, nslots = 0;
+        uint64_t pmin = kNoKey;          // smallest key among waiting changed rows
         bool overflow = false;
-
-        // ---- 3. forward elimination in permuted order ------------------------
-        for (int j = 0; j < n && rank < m && !overflow; ++j) {
-            const int v = perm[j];
-            const int c0 = col_ptr[v], cw = col_ptr[v + 1] - c0;
-            // Lowest candidate row p (rows of H's column v that are untouched
-            // and not pivots; dense non-pivot rows whose lowest one is at j).
+        while (!overflow) {
+            const int i = ptr + lane;
+            const uint64_t ki = (i < m_pad) ? keys[i] : kNoKey;
+            const uint64_t Ki = ki == kNoKey ? kNoKey : (ki >> 16);
+            uint64_t Kprev = __shfl_up_sync(0xffffffffu, Ki, 1);
+            if (lane == 0) Kprev = (ptr > 0) ? (keys[ptr - 1] >> 16) : kNoKey - 1;
+            uint64_t Knext = __shfl_down_sync(0xffffffffu, Ki, 1);
+            if (lane == 31) {
+                const uint64_t kn = (i + 1 < m_pad) ? keys[i + 1] : kNoKey;
+                Knext = kn == kNoKey ? kNoKey : (kn >> 16);
+            }
+            const bool single = Ki != kNoKey && Ki != Kprev && Ki != Knext &&
+                                (pmin == kNoKey || Ki < (pmin >> 16));
+            const unsigned notsingle = __ballot_sync(0xffffffffu, !single);
+            const int L = notsingle ? __ffs(notsingle) - 1 : 32;
+            if (L > 0) {
+                if (lane < L) {
+                    const int r = static_cast<int>(ki & 0xffffu);
+                    const int v = static_cast<int>(Ki & 0xffffu);
+                    pcol[rank + lane] = static_cast<uint16_t>(v);
+                    prow[rank + lane] = static_cast<uint16_t>(r);
+                    pivk[v] = static_cast<uint16_t>(rank + lane);
+                    atomicOr(&pivb[r >> 5], 1u << (r & 31));
+                }
+                rank += L;
+                ptr += L;
+                __syncwarp();
+                continue;
+            }
+            // The event at the smallest pending key: sorted rows and waiting rows.
+            const uint64_t K0 = __shfl_sync(0xffffffffu, Ki, 0);
+            const uint64_t Kev = (pmin != kNoKey && (pmin >> 16) < K0) ? (pmin >> 16) : K0;
+            if (Kev == kNoKey) break;
+            const int v = static_cast<int>(Kev & 0xffffu);
+            // Candidates among the sorted run starting at ptr ...
+            int nsorted = 0;
+            while (true) {
+                const int j = ptr + nsorted + lane;
+                const uint64_t kj = (j < m_pad) ? keys[j] : kNoKey;
+                const bool eq = kj != kNoKey && (kj >> 16) == Kev;
+                const unsigned bal = __ballot_sync(0xffffffffu, eq);
+                const int run = (~bal) ? __ffs(~bal) - 1 : 32;
+                nsorted += run;
+                if (run < 32) break;
+            }
+            // ... and among the waiting rows.
             int best = 0x7fffffff;
-            int ncand = 0;
-            for (int k0 = 0; k0 < cw; k0 += 32) {
-                const int k = k0 + lane;
-                int r = 0x7fffffff;
-                if (k < cw) {
-                    const int rr = csc_row[c0 + k];
-                    if (rflag[rr] == 0xffffu && !((pivb[rr >> 5] >> (rr & 31)) & 1u)) r = rr;
-                }
-                ncand += __popc(__ballot_sync(0xffffffffu, r != 0x7fffffff));
-                best = min(best, r);
+            for (int j0 = 0; j0 < nsorted; j0 += 32) {
+                const int j = j0 + lane;
+                if (j < nsorted) best = min(best, static_cast<int>(keys[ptr + j] & 0xffffu));
             }
-            for (int i0 = 0; i0 < M; i0 += 32) {
-                const int i = i0 + lane;
-                int r = 0x7fffffff;
-                if (i < M) {
-                    const int rr = mlist[i];
-                    if (low[rflag[rr]] == j) r = rr;
-                }
-                ncand += __popc(__ballot_sync(0xffffffffu, r != 0x7fffffff));
-                best = min(best, r);
+            for (int j0 = 0; j0 < npend; j0 += 32) {
+                const int j = j0 + lane;
+                if (j < npend && (pend[j] >> 16) == Kev) best = min(best, static_cast<int>(pend[j] & 0xffffu));
             }
-            if (ncand == 0) continue;
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
             const int p = best;
-
-            if (ncand > 1) {
-                // Replace every other candidate r by r + row p (rare).
-                const unsigned sp_bit = (saug[p >> 5] >> (p & 31)) & 1u;
-                const int pslot = rflag[p];
-                for (int pass = 0; pass < 2 && !overflow; ++pass) {
-                    const int cnt = pass == 0 ? cw : M;
-                    // Rows that pass 0 turns dense join mlist; after the sum with
-                    // row p their lowest one lies right of j, so pass 1 skips them.
-                    for (int i0 = 0; i0 < cnt && !overflow; i0 += 32) {
-                        const int i = i0 + lane;
-                        int r = -1;
-                        if (i < cnt) {
-                            if (pass == 0) {
-                                const int rr = csc_row[c0 + i];
-                                if (rr != p && rflag[rr] == 0xffffu && !((pivb[rr >> 5] >> (rr & 31)) & 1u)) r = rr;
-                            } else {
-                                const int rr = mlist[i];
-                                if (rr != p && low[rflag[rr]] == j) r = rr;
-                            }
-                        }
-                        unsigned todo = __ballot_sync(0xffffffffu, r >= 0);
-                        while (todo) {
-                            const int src = __ffs(todo) - 1;
-                            todo &= todo - 1;
-                            const int rr = __shfl_sync(0xffffffffu, r, src);
-                            int s = rflag[rr];
-                            if (s == 0xffff) {
-                                // Give rr a dense copy built from its row of H.
-                                if (nslots >= C) { overflow = true; break; }
-                                s = nslots++;
-                                uint64_t *row = slots + static_cast<size_t>(s) * wn;
-                                for (int w = lane; w < wn; w += 32) row[w] = 0ull;
-                                __syncwarp();
-                                const int e0 = row_ptr[rr], deg = row_ptr[rr + 1] - e0;
-                                if (lane < deg) {
-                                    const uint32_t pos = inv[col_idx[e0 + lane]];
-                                    atomicOr(reinterpret_cast<unsigned int *>(row) + (pos >> 5), 1u << (pos & 31));
-                                }
-                                __syncwarp();
-                                if (lane == 0) {
-                                    rflag[rr] = static_cast<uint16_t>(s);
-                                    mlist[M] = static_cast<uint16_t>(rr);
-                                }
-                                ++M;
-                            }
-                            uint64_t *row = slots + static_cast<size_t>(s) * wn;
-                            if (pslot == 0xffff) {
-                                const int e0 = row_ptr[p], deg = row_ptr[p + 1] - e0;
-                                if (lane < deg) {
-                                    const uint32_t pos = inv[col_idx[e0 + lane]];
-                                    atomicXor(reinterpret_cast<unsigned int *>(row) + (pos >> 5), 1u << (pos & 31));
-                                }
-                            } else {
-                                const uint64_t *prw = slots + static_cast<size_t>(pslot) * wn;
-                                for (int w = (j >> 6) + lane; w < wn; w += 32) row[w] ^= prw[w];
-                            }
-                            __syncwarp();
-                            if (lane == 0 && sp_bit) saug[rr >> 5] ^= 1u << (rr & 31);
-                            // New lowest position of rr (0xffff when the row vanished).
-                            int lo = 0xffff;
-                            for (int w0 = j >> 6; w0 < wn; w0 += 32) {
-                                const int w = w0 + lane;
-                                const uint64_t x = (w < wn) ? row[w] : 0ull;
-                                const unsigned nz = __ballot_sync(0xffffffffu, x != 0ull);
-                                if (nz) {
-                                    const int src2 = __ffs(nz) - 1;
-                                    const uint64_t xx = __shfl_sync(0xffffffffu, x, src2);
-                                    lo = (w0 + src2) * 64 + __ffsll(static_cast<long long>(xx)) - 1;
-                                    break;
-                                }
-                            }
-                            if (lane == 0) low[s] = static_cast<uint16_t>(lo);
-                            __syncwarp();
+            const unsigned sp_bit = (saug[p >> 5] >> (p & 31)) & 1u;
+            const int pslot = rflag[p];
+            // Every other candidate r: r <- r + row p, then it waits at its next
+            // key (appended to pend; those entries have keys above Kev, so the
+            // scan of pass 1 skips them).  Pass 0: rows of H from the sorted run;
+            // pass 1: changed rows waiting at Kev.
+            const int npend0 = npend;
+            for (int pass = 0; pass < 2 && !overflow; ++pass) {
+                const int cnt = pass == 0 ? nsorted : npend0;
+                for (int j0 = 0; j0 < cnt && !overflow; j0 += 32) {
+                    const int j = j0 + lane;
+                    int r = -1;
+                    if (j < cnt) {
+                        if (pass == 0) {
+                            const int rr = static_cast<int>(keys[ptr + j] & 0xffffu);
+                            if (rr != p) r = rr;
+                        } else {
+                            const uint64_t e = pend[j];
+                            const int rr = static_cast<int>(e & 0xffffu);
+                            if ((e >> 16) == Kev && rr != p) r = rr;
                         }
                     }
+                    unsigned todo = __ballot_sync(0xffffffffu, r >= 0);
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int rr = __shfl_sync(0xffffffffu, r, src);
+                        int s = rflag[rr];
+                        uint64_t *row;
+                        if (s == 0xffff) {
+                            if (nslots >= C) { overflow = true; break; }
+                            s = nslots++;
+                            row = slots + static_cast<size_t>(s) * wn;
+                            for (int w = lane; w < wn; w += 32) row[w] = 0ull;
+                            __syncwarp();
+                            for (int e = row_ptr[rr] + lane; e < row_ptr[rr + 1]; e += 32) {
+                                const uint32_t u = col_idx[e];
+                                atomicOr(reinterpret_cast<unsigned int *>(row) + (u >> 5), 1u << (u & 31));
+                            }
+                            if (lane == 0) rflag[rr] = static_cast<uint16_t>(s);
+                            __syncwarp();
+                        } else {
+                            row = slots + static_cast<size_t>(s) * wn;
+                        }
+                        if (pslot == 0xffff) {
+                            for (int e = row_ptr[p] + lane; e < row_ptr[p + 1]; e += 32) {
+                                const uint32_t u = col_idx[e];
+                                atomicXor(reinterpret_cast<unsigned int *>(row) + (u >> 5), 1u << (u & 31));
+                            }
+                        } else {
+                            const uint64_t *prw = slots + static_cast<size_t>(pslot) * wn;
+                            for (int w = lane; w < wn; w += 32) row[w] ^= prw[w];
+                        }
+                        __syncwarp();
+                        if (lane == 0 && sp_bit) saug[rr >> 5] ^= 1u << (rr & 31);
+                        // Next key of rr: the smallest key among its remaining columns
+                        // (all above Kev).  A row that vanished waits no more.
+                        uint64_t kmin = kNoKey;
+                        for (int w = lane; w < wn; w += 32) {
+                            uint64_t x = row[w];
+                            while (x) {
+                                const int bit = __ffsll(static_cast<long long>(x)) - 1;
+                                x &= x - 1;
+                                const uint64_t kc = col_key(lam, w * 64 + bit);
+                                kmin = kc < kmin ? kc : kmin;
+                            }
+                        }
+                        kmin = warp_min_u64(kmin);
+                        if (kmin != kNoKey) {
+                            if (npend >= C) { overflow = true; break; }
+                            if (lane == 0) pend[npend] = (kmin << 16) | static_cast<uint32_t>(rr);
+                            ++npend;
+                        }
+                        __syncwarp();
+                    }
                 }
-                if (overflow) break;
             }
-            // p becomes the pivot of position j.
+            // Drop the waiting entries consumed by this event.
+            if (!overflow) {
+                int kept = 0;
+                for (int j0 = 0; j0 < npend; j0 += 32) {
+                    const int j = j0 + lane;
+                    const uint64_t e = (j < npend) ? pend[j] : kNoKey;
+                    const bool keep = j < npend && (e >> 16) != Kev;
+                    const unsigned bk = __ballot_sync(0xffffffffu, keep);
+                    __syncwarp();
+                    if (keep) pend[kept + __popc(bk & ((1u << lane) - 1u))] = e;
+                    kept += __popc(bk);
+                    __syncwarp();
+                }
+                npend = kept;
+            }
+            if (overflow) break;
+            // p becomes the pivot of v.
             if (lane == 0) {
-                pivb[p >> 5] |= 1u << (p & 31);
-                pcol[rank] = static_cast<uint16_t>(j);
+                pcol[rank] = static_cast<uint16_t>(v);
                 prow[rank] = static_cast<uint16_t>(p);
-            }
-            if (rflag[p] != 0xffffu) {
-                // Drop p from the dense non-pivot list.
-                int at = -1;
-                for (int i0 = 0; i0 < M; i0 += 32) {
-                    const int i = i0 + lane;
-                    const unsigned hit = __ballot_sync(0xffffffffu, i < M && mlist[i] == p);
-                    if (hit) { at = i0 + __ffs(hit) - 1; break; }
-                }
-                __syncwarp();
-                if (lane == 0 && at >= 0) mlist[at] = mlist[M - 1];
-                --M;
+                pivk[v] = static_cast<uint16_t>(rank);
+                pivb[p >> 5] |= 1u << (p & 31);
             }
             ++rank;
+            ptr += nsorted;
+            // Smallest waiting key.
+            uint64_t mn = kNoKey;
+            for (int j = lane; j < npend; j += 32) mn = pend[j] < mn ? pend[j] : mn;
             __syncwarp();
+            pmin = warp_min_u64(mn);
         }
 
         if (overflow) {
@@ -282,48 +330,60 @@ __global__ void __launch_bounds__(256) osd_warp_kernel(const OsdWarpArgs a) {
             continue;
         }
 
-        // ---- 4. consistency: rows without a pivot must end with s' = 0 ---------
+        // ---- consistency: rows without a pivot must end with s' = 0 ---------------
         unsigned bad = 0u;
         for (int w = lane; w < W32; w += 32) bad |= saug[w] & ~pivb[w];
         const bool nosol = __any_sync(0xffffffffu, bad != 0u);
 
         if (!nosol) {
-            // ---- 5. backward substitution ---------------------------------------
-            for (int k = rank - 1; k >= 0; --k) {
-                const int p = prow[k], j = pcol[k];
-                unsigned par;
-                const int s = rflag[p];
-                if (s == 0xffff) {
-                    const int e0 = row_ptr[p], deg = row_ptr[p + 1] - e0;
-                    unsigned bit = 0u;
-                    if (lane < deg) {
-                        const uint32_t pos = inv[col_idx[e0 + lane]];
-                        bit = (X32[pos >> 5] >> (pos & 31)) & 1u;
+            // ---- backward substitution, 32 pivots per batch -------------------
+            for (int hi = rank; hi > 0;) {
+                const int lo = hi > 32 ? hi - 32 : 0;
+                const int k = lo + lane;
+                unsigned part = 0u, dep = 0u;
+                if (k < hi) {
+                    const int p = prow[k];
+                    part = (saug[p >> 5] >> (p & 31)) & 1u;
+                    const int s = rflag[p];
+                    if (s == 0xffff) {
+                        for (int e = row_ptr[p]; e < row_ptr[p + 1]; ++e) {
+                            const int u = col_idx[e];
+                            const int kk = pivk[u];
+                            if (kk == 0xffff || kk == k) continue;
+                            if (kk >= hi) part ^= (X32[u >> 5] >> (u & 31)) & 1u;
+                            else if (kk > k) dep |= 1u << (kk - lo);
+                        }
+                    } else {
+                        const uint64_t *row = slots + static_cast<size_t>(s) * wn;
+                        for (int w = 0; w < wn; ++w) {
+                            uint64_t x = row[w];
+                            while (x) {
+                                const int bit = __ffsll(static_cast<long long>(x)) - 1;
+                                x &= x - 1;
+                                const int u = w * 64 + bit;
+                                const int kk = pivk[u];
+                                if (kk == 0xffff || kk == k) continue;
+                                if (kk >= hi) part ^= (X32[u >> 5] >> (u & 31)) & 1u;
+                                else if (kk > k) dep |= 1u << (kk - lo);
+                            }
+                        }
                     }
-                    par = warp_parity(bit);
-                } else {
-                    const uint64_t *row = slots + static_cast<size_t>(s) * wn;
-                    unsigned acc = 0u;
-                    for (int w = (j >> 6) + lane; w < wn; w += 32) acc += __popcll(row[w] & X[w]);
-                    par = warp_parity(acc);
                 }
-                par ^= (saug[p >> 5] >> (p & 31)) & 1u;
-                if (lane == 0 && par) X32[j >> 5] |= 1u << (j & 31);
+                unsigned E = 0u;
+                for (int L = hi - lo - 1; L >= 0; --L) {
+                    const unsigned mine = part ^ (__popc(dep & E) & 1u);
+                    const unsigned eL = __shfl_sync(0xffffffffu, mine, L);
+                    E |= eL << L;
+                }
+                if (k < hi && ((E >> lane) & 1u)) {
+                    const int u = pcol[k];
+                    atomicOr(&X32[u >> 5], 1u << (u & 31));
+                }
                 __syncwarp();
+                hi = lo;
             }
-            // ---- 6. e' = (e_S, 0) mapped back through pi -------------------------
-            for (int w = lane; w < 2 * wn; w += 32) ebits[w] = 0u;
-            __syncwarp();
-            for (int k = lane; k < rank; k += 32) {
-                const int j = pcol[k];
-                if ((X32[j >> 5] >> (j & 31)) & 1u) {
-                    const int v = perm[j];
-                    atomicOr(&ebits[v >> 5], 1u << (v & 31));
-                }
-            }
-            __syncwarp();
             uint32_t *dst = reinterpret_cast<uint32_t *>(a.err + static_cast<size_t>(b) * wn);
-            for (int w = lane; w < 2 * wn; w += 32) dst[w] = ebits[w];
+            for (int w = lane; w < 2 * wn; w += 32) dst[w] = X32[w];
         }
         if (lane == 0 && a.osd_out) a.osd_out[b] = nosol ? LBP_OSD_NO_SOLUTION : LBP_OSD_APPLIED;
         __syncwarp();
