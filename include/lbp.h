@@ -37,6 +37,7 @@ extern "C" {
 #define LBP_ENOMEM    (-12)   /* device allocation failed, or workspace too small */
 #define LBP_ENOSYS    (-38)   /* this code / precision combination is not supported */
 #define LBP_ECUDA     (-5)    /* a CUDA runtime call failed */
+#define LBP_E2BIG     (-7)    /* request needs more scratch than lbp_decode_noalloc's fixed area */
 
 /* Per-shot OSD status written to osd_out. */
 #define LBP_OSD_NOT_RUN     0  /* BP converged, or OSD disabled */
@@ -143,6 +144,32 @@ int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_
                     const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                     uint8_t *osd_out, int32_t *iters_out, float *llr_out,
                     void *workspace, size_t workspace_bytes, void *stream);
+
+/* Same decode as lbp_decode, for callers that cannot allocate device memory
+ * (no cudaMalloc, no allocator callback: e.g. a latency-bound request loop on
+ * a pre-sized device, a plugin whose host owns every allocation, a caller
+ * inside stream capture).  No workspace argument: scratch comes from a fixed
+ * device array of LBP_NOALLOC_SCRATCH_BYTES bytes inside this library, which
+ * every GPU that loads the library holds until the process exits.  The call
+ * allocates nothing; buffers and their meaning are those of lbp_decode.
+ *
+ * The paper has no counterpart to this call; it is a deployment variant.
+ *
+ * Limits and behaviour:
+ *  - Returns LBP_E2BIG, enqueuing nothing, when lbp_workspace_size(code,
+ *    params, num_shots) exceeds LBP_NOALLOC_SCRATCH_BYTES (OSD on a large
+ *    code, or very large OSD batches); use lbp_decode with a workspace then.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current) and keeps it: make that first call before any
+ *    stream capture that should contain a later call.
+ *  - All calls on a device share the array; the decode clears what must start
+ *    at zero on the call's stream, so calls in order on one stream are
+ *    independent, but calls that overlap on the GPU (other streams, other host
+ *    threads) race on it and must be serialised by the caller. */
+#define LBP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int lbp_decode_noalloc(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+                       const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                       uint8_t *osd_out, int32_t *iters_out, float *llr_out, void *stream);
 
 /* Kernel timing instrumentation, off by default.  While enabled, every
  * decode records a CUDA event pair on its stream around each kernel launch

@@ -39,6 +39,19 @@ struct EllImage {
 
 }  // namespace lbp
 
+struct lbp_code;
+
+namespace lbp {
+
+// The decode path behind lbp_decode: plan, workspace layout and launches of
+// K_bp and the OSD kernels on `stream`, using `ws_bytes` bytes at `ws`
+// (device, 256-byte aligned) as scratch.  Parameters are already validated.
+int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
+                  uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
+                  void *ws, size_t ws_bytes, cudaStream_t stream);
+
+}  // namespace lbp
+
 struct lbp_code {
     int device;
     int sm_count;

@@ -52,6 +52,7 @@ extern "C" const char *lbp_strerror(int code) {
         case LBP_ENOMEM: return "out of device memory or workspace too small";
         case LBP_ENOSYS: return "code / precision combination not supported";
         case LBP_ECUDA: return "CUDA runtime error";
+        case LBP_E2BIG: return "request needs more scratch than the fixed no-allocation area holds";
         default: return "unknown error";
     }
 }

@@ -238,6 +238,10 @@ int check_launch() {
     return e == cudaSuccess ? LBP_OK : LBP_ECUDA;
 }
 
+}  // namespace
+
+namespace lbp {
+
 int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                   uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                   void *ws, size_t ws_bytes, cudaStream_t stream) {
@@ -355,6 +359,10 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
     }
     return rc;
 }
+
+}  // namespace lbp
+
+namespace {
 
 int check_common(const lbp_code *c, const lbp_params *prm, int64_t B) {
     if (!c) return LBP_EINVAL;

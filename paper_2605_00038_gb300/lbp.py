@@ -16,14 +16,15 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 LIB_PATH = _HERE / "liblbp.so"
 
-LBP_OK, LBP_EINVAL, LBP_ENOMEM, LBP_ENOSYS, LBP_ECUDA = 0, -22, -12, -38, -5
+LBP_OK, LBP_EINVAL, LBP_ENOMEM, LBP_ENOSYS, LBP_ECUDA, LBP_E2BIG = 0, -22, -12, -38, -5, -7
+LBP_NOALLOC_SCRATCH_BYTES = 32 << 20
 LBP_OSD_NOT_RUN, LBP_OSD_APPLIED, LBP_OSD_NO_SOLUTION = 0, 1, 2
 LBP_MSG_F32, LBP_MSG_F16, LBP_MSG_I8 = 0, 1, 2
 LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info",
             "lbp_workspace_size", "lbp_decode", "lbp_host_workspace_size", "lbp_decode_host",
-            "lbp_timing_enable", "lbp_timing_read", "lbp_strerror"]
+            "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_strerror"]
 
 
 class lbp_params(ctypes.Structure):
@@ -70,6 +71,8 @@ def lib():
         L.lbp_decode.argtypes = dec
         L.lbp_decode_host.restype = ctypes.c_int
         L.lbp_decode_host.argtypes = dec
+        L.lbp_decode_noalloc.restype = ctypes.c_int
+        L.lbp_decode_noalloc.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, vp]
         L.lbp_timing_enable.restype = ctypes.c_int
         L.lbp_timing_enable.argtypes = [ctypes.c_int]
         L.lbp_timing_read.restype = ctypes.c_int
@@ -198,6 +201,16 @@ def lbp_decode_host(code: Code, params: lbp_params, num_shots: int, syndromes, e
                                  _hptr(iters_out), _hptr(llr_out), _dptr(workspace), ws_bytes,
                                  _stream_handle(stream)),
            "lbp_decode_host")
+
+
+def lbp_decode_noalloc(code: Code, params: lbp_params, num_shots: int, syndromes, err_out,
+                       converged, osd_out, iters_out, llr_out, stream=None):
+    """lbp_decode without a workspace: scratch is the library's fixed device
+    array (for callers that cannot allocate device memory)."""
+    _check(lib().lbp_decode_noalloc(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
+                                    _dptr(err_out), _dptr(converged), _dptr(osd_out),
+                                    _dptr(iters_out), _dptr(llr_out), _stream_handle(stream)),
+           "lbp_decode_noalloc")
 
 
 def lbp_timing_enable(on: bool):
