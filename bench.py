@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle shots for cpu_baseline")
+    ap.add_argument("--no-tune", action="store_true", help="skip lbp_tune (default launch shape)")
     return ap.parse_args()
 
 
@@ -232,6 +233,10 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # Launch-shape autotuning on the first batch (outside the timed region).
+    if not args.no_tune:
+        tb = min(B, 131072)
+        dec.tune(syn_d[0][:tb].contiguous(), prms[0], stream)
     for k in range(args.warmup):
         step(k)
     barrier()

@@ -19,8 +19,8 @@
  *  - Return value 0 on success, a negative LBP_E* code otherwise; nothing is
  *    enqueued when an argument check fails.  No C++ exception crosses the ABI.
  *  - A code object is bound to the device that was current at load time and
- *    may be used from several host threads at once (it is read-only after
- *    load); a workspace must not be shared by two calls in flight.
+ *    may be used from several host threads at once (only lbp_tune writes it);
+ *    a workspace must not be shared by two calls in flight.
  */
 #ifndef LBP_H
 #define LBP_H
@@ -128,6 +128,21 @@ int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots
                const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                uint8_t *osd_out, int32_t *iters_out, float *llr_out,
                void *workspace, size_t workspace_bytes, void *stream);
+
+/* Autotuner for the BP kernel's launch shape (groups of threads per CTA and
+ * threads per group, the "shot tile" and the threads working on one shot):
+ * decodes the given batch once per candidate shape, twice each, timing the
+ * BP kernel with CUDA events, and stores the fastest shape in `code` for its
+ * message type (params->msg); later decodes of that message type use it.
+ * Every shape computes identical results, so on return the outputs hold
+ * lbp_decode's results for the batch.  Arguments as for lbp_decode (llr_out
+ * omitted).  Synchronous: returns after the stream has drained.  It writes
+ * the code object: no other call may use `code` meanwhile.  Tune on a batch
+ * representative of the workload (its noise decides the iteration counts). */
+int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_shots,
+             const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+             uint8_t *osd_out, int32_t *iters_out, void *workspace, size_t workspace_bytes,
+             void *stream);
 
 /* Bytes of device workspace lbp_decode_host needs: lbp_workspace_size plus
  * device staging for the inputs and outputs.  When llr_out is requested the

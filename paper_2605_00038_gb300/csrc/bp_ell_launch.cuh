@@ -23,7 +23,9 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     switch (s.G) {
         case 32: return launch_ell_one<MsgT, 32, DC, DV>(s, a, st);
         case 64: return launch_ell_one<MsgT, 64, DC, DV>(s, a, st);
+        case 96: return launch_ell_one<MsgT, 96, DC, DV>(s, a, st);
         case 128: return launch_ell_one<MsgT, 128, DC, DV>(s, a, st);
+        case 192: return launch_ell_one<MsgT, 192, DC, DV>(s, a, st);
         case 256: return launch_ell_one<MsgT, 256, DC, DV>(s, a, st);
         default: return LBP_ENOSYS;
     }

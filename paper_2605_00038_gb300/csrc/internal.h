@@ -50,6 +50,14 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
                   uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                   void *ws, size_t ws_bytes, cudaStream_t stream);
 
+// Same, with an explicit BP launch shape (groups per CTA, threads per group;
+// 0, 0 = the code's tuned or default shape); when bp_ms is non-null the BP
+// kernel is timed with an event pair on `stream` (the call then waits).
+int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
+                         uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
+                         void *ws, size_t ws_bytes, cudaStream_t stream, int groups, int G,
+                         float *bp_ms);
+
 }  // namespace lbp
 
 struct lbp_code {
@@ -67,4 +75,7 @@ struct lbp_code {
     // 32-bit device copies, used by OSD.
     int32_t *d_row_ptr, *d_col_idx;
     float *d_mu;
+    // BP launch shape chosen by lbp_tune per message type (0 = not tuned):
+    // groups per CTA and threads per group.
+    int tuned_groups[3], tuned_G[3];
 };

@@ -17,6 +17,7 @@
 //   osd_mat    u64[grid][m][ceil(n/64)] K_osd dense matrices (when they do
 //                                                     not fit shared memory)
 //   slots      u64[warps][C][ceil(n/64)] K_osd_warp dense-row pools
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
@@ -79,7 +80,7 @@ int validate_params(const lbp_params *p) {
 
 // Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
 // group does not fit in shared memory.
-int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out) {
+int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_S = 0, int req_G = 0) {
     const int W32 = (c->m + 31) / 32;
     BpPlan p;
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
@@ -105,10 +106,31 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out) {
     }
     const size_t budget = static_cast<size_t>(c->smem_optin);
     if (image + static_cast<size_t>(p.state_bytes) > budget) return LBP_ENOSYS;
-    int S = static_cast<int>((budget - image) / p.state_bytes);
-    // Threads per group: enough to cover the checks, at most 256.
+    const int S_fit = static_cast<int>((budget - image) / p.state_bytes);
+    int S = S_fit;
+    // Default shape: threads per group scale with the code (at most 128; 96
+    // when the ELL kernel has room for at least 6 groups, which balances the
+    // d=11 space-time code best); lbp_tune replaces it by measurement.
     int G = 32;
-    while (G < 256 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
+    while (G < 128 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
+    if (p.ell && G == 128 && S_fit >= 6) G = 96;
+    const int mi = msg >= 0 && msg < 3 ? msg : 0;
+    if (c->tuned_G[mi] > 0) {
+        G = c->tuned_G[mi];
+        S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
+    }
+    // Explicit shape (lbp_tune candidates), then the LBP_BP_SHAPE override "S,G".
+    int s_req = req_S, g_req = req_G;
+    if (!g_req) {
+        if (const char *env = std::getenv("LBP_BP_SHAPE")) {
+            if (std::sscanf(env, "%d,%d", &s_req, &g_req) != 2) s_req = g_req = 0;
+        }
+    }
+    if (s_req > 0 && (g_req == 32 || g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 || g_req == 256)) {
+        G = g_req;
+        S = s_req < S_fit ? s_req : S_fit;
+    }
+    if (!p.ell && G != 32 && G != 64 && G != 128 && G != 256) G = 128;
     if (S * G > 1024) S = 1024 / G;
     if (G > 32 && S > 15) S = 15;     // named barriers 1..15
     if (S < 1) S = 1;
@@ -245,8 +267,16 @@ namespace lbp {
 int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                   uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                   void *ws, size_t ws_bytes, cudaStream_t stream) {
+    return decode_device_shaped(c, prm, B, syn, err, conv, osd_out, iters, llr, ws, ws_bytes, stream,
+                                0, 0, nullptr);
+}
+
+int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
+                         uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
+                         void *ws, size_t ws_bytes, cudaStream_t stream, int req_S, int req_G,
+                         float *bp_ms) {
     BpPlan bp;
-    int rc = plan_bp(c, prm->msg, B, &bp);
+    int rc = plan_bp(c, prm->msg, B, &bp, req_S, req_G);
     if (rc) return rc;
     OsdPlan op;
     OsdWarpPlan wp;
@@ -279,6 +309,14 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
     a.off_beta = bp.off_beta; a.off_lam = bp.off_lam; a.off_s = bp.off_s;
     a.off_shat = bp.off_shat; a.off_misc = bp.off_misc;
     void *tk = timing_begin(stream);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (bp_ms) {
+        if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+            cudaGetLastError();
+            return LBP_ECUDA;
+        }
+        cudaEventRecord(t0, stream);
+    }
     if (bp.ell) {
         BpEllArgs e;
         std::memset(&e, 0, sizeof(e));
@@ -305,6 +343,13 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
         }
     }
     timing_end(tk, stream, kTimeBp);
+    if (bp_ms) {
+        cudaEventRecord(t1, stream);
+        cudaEventSynchronize(t1);
+        if (cudaEventElapsedTime(bp_ms, t0, t1) != cudaSuccess) *bp_ms = -1.0f;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
     if (rc) return rc;
     rc = check_launch();
     if (rc) return rc;
@@ -465,5 +510,44 @@ extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, i
     if (osd_out) ok = ok && cudaMemcpyAsync(osd_out, d_osd, static_cast<size_t>(B), cudaMemcpyDeviceToHost, s) == cudaSuccess;
     if (llr_out) ok = ok && cudaMemcpyAsync(llr_out, d_llr, 4ull * code->n * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     if (!ok) { cudaGetLastError(); return LBP_ECUDA; }
+    return LBP_OK;
+}
+
+extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_shots,
+                        const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                        uint8_t *osd_out, int32_t *iters_out, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    int rc = check_common(code, params, num_shots);
+    if (rc) return rc;
+    if (num_shots == 0) return LBP_OK;
+    if (!syndromes || !err_out || !converged || !iters_out) return LBP_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != code->device) return LBP_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int mi = params->msg;
+    code->tuned_G[mi] = 0;
+    code->tuned_groups[mi] = 0;
+    const int Gs[] = {32, 64, 96, 128, 192, 256};
+    float best = -1.0f;
+    int best_S = 0, best_G = 0;
+    for (int G : Gs) {
+        BpPlan probe;
+        if (plan_bp(code, mi, num_shots, &probe, 1024, G) != LBP_OK) continue;
+        if (probe.G != G) continue;                    // shape not available for this code
+        const int S = probe.groups;
+        float ms = 0.0f, warm = 0.0f;
+        rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                       iters_out, nullptr, workspace, workspace_bytes, s, S, G, &warm);
+        if (rc) return rc;
+        rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                       iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms);
+        if (rc) return rc;
+        if (ms > 0.0f && (best < 0.0f || ms < best)) { best = ms; best_S = S; best_G = G; }
+    }
+    if (best_G > 0) {
+        code->tuned_G[mi] = best_G;
+        code->tuned_groups[mi] = best_S;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
     return LBP_OK;
 }

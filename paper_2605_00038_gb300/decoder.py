@@ -67,6 +67,14 @@ class Decoder:
                        out.llr, ws, stream)
         return out
 
+    def tune(self, syndromes: torch.Tensor, params, stream=None) -> DeviceResult:
+        """lbp_tune on this batch; returns its (valid) decode results."""
+        B = syndromes.shape[0]
+        out = self.alloc(B)
+        lbp.lbp_tune(self.code, params, B, syndromes, out.err, out.converged, out.osd, out.iters,
+                     self.workspace(params, B), stream)
+        return out
+
     def decode_host(self, syndromes, params, out: dict, stream=None):
         """syndromes and every array in `out` are pinned CPU tensors."""
         B = syndromes.shape[0]

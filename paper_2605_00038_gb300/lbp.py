@@ -23,7 +23,7 @@ LBP_MSG_F32, LBP_MSG_F16, LBP_MSG_I8 = 0, 1, 2
 LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info",
-            "lbp_workspace_size", "lbp_decode", "lbp_host_workspace_size", "lbp_decode_host",
+            "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_strerror"]
 
 
@@ -71,6 +71,8 @@ def lib():
         L.lbp_decode.argtypes = dec
         L.lbp_decode_host.restype = ctypes.c_int
         L.lbp_decode_host.argtypes = dec
+        L.lbp_tune.restype = ctypes.c_int
+        L.lbp_tune.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, sz, vp]
         L.lbp_decode_noalloc.restype = ctypes.c_int
         L.lbp_decode_noalloc.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, vp]
         L.lbp_timing_enable.restype = ctypes.c_int
@@ -201,6 +203,15 @@ def lbp_decode_host(code: Code, params: lbp_params, num_shots: int, syndromes, e
                                  _hptr(iters_out), _hptr(llr_out), _dptr(workspace), ws_bytes,
                                  _stream_handle(stream)),
            "lbp_decode_host")
+
+
+def lbp_tune(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
+             osd_out, iters_out, workspace, stream=None):
+    """Time each BP launch shape on this batch and keep the fastest in `code`."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().lbp_tune(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
+                          _dptr(err_out), _dptr(converged), _dptr(osd_out), _dptr(iters_out),
+                          _dptr(workspace), ws_bytes, _stream_handle(stream)), "lbp_tune")
 
 
 def lbp_decode_noalloc(code: Code, params: lbp_params, num_shots: int, syndromes, err_out,

@@ -173,6 +173,29 @@ def test_general_kernel_on_high_degree_code():
         assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
 
 
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16])
+def test_autotuner_keeps_results(msg):
+    """lbp_tune leaves lbp_decode's outputs and picks a shape later decodes use
+    without changing any result."""
+    w = workloads.c2_d11_spacetime(shots=3000, osd=1)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, msg=msg, seed=3)
+    ref = gpu_decode(w.h, w.priors, syn, want_llr=False, **kw)
+    dec = Decoder(w.h, w.priors)
+    prm = dec.params(**kw)
+    s = torch.from_numpy(syn.view(np.int64)).cuda()
+    out = dec.alloc(w.shots)
+    lbp.lbp_tune(dec.code, prm, w.shots, s, out.err, out.converged, out.osd, out.iters,
+                 dec.workspace(prm, w.shots))
+    assert np.array_equal(out.err.cpu().numpy().view(np.uint64), ref["err_words"])
+    assert np.array_equal(out.iters.cpu().numpy(), ref["iters"])
+    again = dec.decode(s, prm)
+    torch.cuda.synchronize()
+    assert np.array_equal(again.err.cpu().numpy().view(np.uint64), ref["err_words"])
+    assert np.array_equal(again.osd.cpu().numpy(), ref["osd"])
+    dec.close()
+
+
 # -------------------------------------------------------------- edge cases
 
 def test_ragged_sizes_and_tails():
