@@ -10,11 +10,18 @@
 //    minimum).  beta[k][c] (row length m + 1) is the message on that slot.
 //    Thread c reads slot k of consecutive checks from consecutive words: no
 //    bank conflicts, and loops over the DC slots unroll completely.
-//  * Column side in ELL form, slot-major: vent[k][v] packs (slot << 13 | check)
-//    of v's k-th check, ascending, padded with check m, slot 0, whose message
-//    beta[0][m] is +0 (x + 0 == x for every partial sum, which is never -0), so
-//    the LLR update sums exactly the oracle's sequence of binary32 additions.
+//  * Column side in ELL form, slot-major: vent[k][v] is the offset
+//    (slot * (m + 1) + check) of the message of v's k-th check, ascending,
+//    padded with offset m, the message beta[0][m] = +0 (x + 0 == x for every
+//    partial sum, which is never -0), so the LLR update sums exactly the
+//    oracle's sequence of binary32 additions.  The check of an offset, needed
+//    only by the syndrome scatter and the lottery, is offset mod (m + 1),
+//    computed with an exact multiply-high division.
 //  * The lottery reads V(c*) and C(v) from the same ELL arrays.
+//  * Placement: the graph image and each group's state sit in shared memory
+//    when they fit (kGraphSmem, kStateSmem); otherwise they are read from
+//    global memory (the image is L2-resident; the state goes to a per-group
+//    slice of the workspace), which is how the d=25 space-time code runs.
 // Everything else (groups of G threads per shot, named barriers, s_hat
 // scatter, early termination, lottery, outputs, OSD hand-off) is as in
 // bp_kernel.
@@ -48,13 +55,15 @@ struct BpEllArgs {
     float *osd_llr;
     uint32_t state_bytes;
     uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
+    uint8_t *gstate;          // per-group state slices when not in shared memory
+    uint32_t magic;           // floor(2^32 / (m + 1)) + 1: offset / (m + 1) by multiply-high
 };
 
-template <typename MsgT, int G, int DC, int DV>
+template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
-    static_assert(DC <= 8 && DV <= 8, "slot ids are packed in 3 bits");
+    static_assert(DC <= 8 && DV <= 8, "bounded degrees");
     extern __shared__ __align__(16) uint8_t smem[];
-    {
+    if (kGraphSmem) {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
         int4 *dst = reinterpret_cast<int4 *>(smem);
         const int words = static_cast<int>(a.img.bytes >> 4);
@@ -62,20 +71,28 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     }
     const int m = a.m, n = a.n, I = a.max_iter;
     const int m1s = m + 1;                     // beta row stride
-    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(smem + a.img.off_cidx);
-    const uint16_t *vent = reinterpret_cast<const uint16_t *>(smem + a.img.off_vent);
-    const float *mu = reinterpret_cast<const float *>(smem + a.img.off_mu);
+    const uint8_t *gbase = kGraphSmem ? smem : a.image;
+    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(gbase + a.img.off_cidx);
+    const uint16_t *vent = reinterpret_cast<const uint16_t *>(gbase + a.img.off_vent);
+    const float *mu = reinterpret_cast<const float *>(gbase + a.img.off_mu);
+    const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
 
     const int grp = threadIdx.x / G;
     const int t = threadIdx.x % G;
     const int lane = threadIdx.x & 31;
     const int bar = grp + 1;
-    uint8_t *st = smem + a.img.bytes + static_cast<size_t>(grp) * a.state_bytes;
+    const int groups = blockDim.x / G;
+    uint8_t *st = kStateSmem
+        ? smem + image_smem + static_cast<size_t>(grp) * a.state_bytes
+        : a.gstate + (static_cast<size_t>(blockIdx.x) * groups + grp) * a.state_bytes;
+    // The group's shot counter slot always lives in shared memory.
+    volatile uint32_t *misc = kStateSmem
+        ? reinterpret_cast<volatile uint32_t *>(st + a.off_misc)
+        : reinterpret_cast<volatile uint32_t *>(smem + image_smem + 16 * grp);
     MsgT *beta = reinterpret_cast<MsgT *>(st + a.off_beta);
     float *lam = reinterpret_cast<float *>(st + a.off_lam);
     uint32_t *s_w = reinterpret_cast<uint32_t *>(st + a.off_s);
     uint32_t *shat = reinterpret_cast<uint32_t *>(st + a.off_shat);
-    volatile uint32_t *misc = reinterpret_cast<volatile uint32_t *>(st + a.off_misc);
     if (t == 0) {
         beta[m] = Msg<MsgT>::store(0.0f);                 // column-side padding message
         lam[n] = __int_as_float(0x7f800000);              // check-side padding column
@@ -153,13 +170,13 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
                     ent[k] = vent[k * n + v];
-                    acc = __fadd_rn(acc, Msg<MsgT>::load(beta[(ent[k] >> 13) * m1s + (ent[k] & 0x1fffu)]));
+                    acc = __fadd_rn(acc, Msg<MsgT>::load(beta[ent[k]]));
                 }
                 lam[v] = acc;
                 if (acc <= 0.0f) {
                     #pragma unroll
                     for (int k = 0; k < DV; ++k) {
-                        const unsigned r = ent[k] & 0x1fffu;
+                        const unsigned r = ent[k] - __umulhi(ent[k], a.magic) * static_cast<unsigned>(m1s);
                         if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
                     }
                 }
@@ -228,7 +245,8 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                                 bc = 0;
                                 #pragma unroll
                                 for (int kk = 0; kk < DV; ++kk) {
-                                    const unsigned r = vent[kk * n + v] & 0x1fffu;
+                                    const unsigned o = vent[kk * n + v];
+                                    const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(m1s);
                                     if (r < static_cast<unsigned>(m))
                                         bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
                                 }

@@ -6,9 +6,9 @@
 
 namespace lbp {
 
-template <typename MsgT, int G, int DC, int DV>
+template <typename MsgT, int G, int DC, int DV, bool GS, bool SS>
 int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV>;
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -20,13 +20,30 @@ int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
 
 template <typename MsgT, int DC, int DV>
 int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    if (s.graph_smem) {
+        switch (s.G) {
+            case 32: return launch_ell_one<MsgT, 32, DC, DV, true, true>(s, a, st);
+            case 64: return launch_ell_one<MsgT, 64, DC, DV, true, true>(s, a, st);
+            case 96: return launch_ell_one<MsgT, 96, DC, DV, true, true>(s, a, st);
+            case 128: return launch_ell_one<MsgT, 128, DC, DV, true, true>(s, a, st);
+            case 192: return launch_ell_one<MsgT, 192, DC, DV, true, true>(s, a, st);
+            case 256: return launch_ell_one<MsgT, 256, DC, DV, true, true>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
+    }
+    // Large codes: graph in global memory; state in shared or global memory.
+    if (s.state_smem) {
+        switch (s.G) {
+            case 256: return launch_ell_one<MsgT, 256, DC, DV, false, true>(s, a, st);
+            case 512: return launch_ell_one<MsgT, 512, DC, DV, false, true>(s, a, st);
+            case 1024: return launch_ell_one<MsgT, 1024, DC, DV, false, true>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
+    }
     switch (s.G) {
-        case 32: return launch_ell_one<MsgT, 32, DC, DV>(s, a, st);
-        case 64: return launch_ell_one<MsgT, 64, DC, DV>(s, a, st);
-        case 96: return launch_ell_one<MsgT, 96, DC, DV>(s, a, st);
-        case 128: return launch_ell_one<MsgT, 128, DC, DV>(s, a, st);
-        case 192: return launch_ell_one<MsgT, 192, DC, DV>(s, a, st);
-        case 256: return launch_ell_one<MsgT, 256, DC, DV>(s, a, st);
+        case 256: return launch_ell_one<MsgT, 256, DC, DV, false, false>(s, a, st);
+        case 512: return launch_ell_one<MsgT, 512, DC, DV, false, false>(s, a, st);
+        case 1024: return launch_ell_one<MsgT, 1024, DC, DV, false, false>(s, a, st);
         default: return LBP_ENOSYS;
     }
 }

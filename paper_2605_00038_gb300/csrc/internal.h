@@ -27,10 +27,10 @@ struct GraphImage {
 };
 
 // ELL image for bounded-degree codes (bp_ell_kernel): check side cidx[DC][m]
-// (column ids, padding n) and column side vent[DV][n] (slot << 13 | check,
-// padding m), both slot-major uint16, then mu[n + 1] with mu[n] = +inf.
-// Exists when every check has <= 8 ones, every column <= 4, m < 8191 and
-// n < 65535.
+// (column ids, padding n) and column side vent[DV][n] (message offset
+// slot * (m + 1) + check, padding m), both slot-major uint16, then mu[n + 1]
+// with mu[n] = +inf.  Exists when every check has <= 8 ones, every column
+// <= 4, DC * (m + 1) < 65536 and n < 65535.
 struct EllImage {
     uint32_t bytes;
     uint32_t off_cidx, off_vent, off_mu;

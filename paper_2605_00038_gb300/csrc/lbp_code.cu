@@ -146,12 +146,15 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         rc = upload(reinterpret_cast<void **>(&c->d_image), img.data(), off);
     }
     // ELL image for the bounded-degree kernel.
-    if (rc == LBP_OK && maxdeg <= 8 && maxcol <= 4 && m < 8191 && n < 65535) {
+    int ell_dc = 8, ell_dv = 4;
+    if (maxdeg <= 6 && maxcol <= 2) { ell_dc = 6; ell_dv = 2; }
+    else if (maxdeg <= 6 && maxcol <= 3) { ell_dc = 6; ell_dv = 3; }
+    if (rc == LBP_OK && maxdeg <= 8 && maxcol <= 4 && static_cast<int64_t>(ell_dc) * (m + 1) < 65536 &&
+        n < 65535) {
         lbp::EllImage &e = c->ell;
         // Supported (DC, DV) shapes: (6, 2), (6, 3), (8, 4).
-        if (maxdeg <= 6 && maxcol <= 2) { e.DC = 6; e.DV = 2; }
-        else if (maxdeg <= 6 && maxcol <= 3) { e.DC = 6; e.DV = 3; }
-        else { e.DC = 8; e.DV = 4; }
+        e.DC = ell_dc;
+        e.DV = ell_dv;
         uint32_t off = 0;
         e.off_cidx = off; off = align16(off + 2u * e.DC * m);
         e.off_vent = off; off = align16(off + 2u * e.DV * n);
@@ -169,11 +172,11 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         for (int32_t v = 0; v < n; ++v) {
             const int32_t a = col_ptr[v], deg = col_ptr[v + 1] - a;
             for (int k = 0; k < e.DV; ++k) {
-                uint16_t ent = static_cast<uint16_t>(m);          // padding: check m, slot 0
+                uint16_t ent = static_cast<uint16_t>(m);          // padding: message beta[0][m] = +0
                 if (k < deg) {
                     const int32_t r = csc_row[a + k];
                     const int32_t slot = csc_edge[a + k] - row_ptr[r];
-                    ent = static_cast<uint16_t>((slot << 13) | r);
+                    ent = static_cast<uint16_t>(slot * (m + 1) + r);
                 }
                 ve[static_cast<size_t>(k) * n + v] = ent;
             }

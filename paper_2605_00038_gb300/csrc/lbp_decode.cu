@@ -40,7 +40,7 @@ uint32_t align16u(uint32_t x) { return (x + 15u) & ~15u; }
 int msg_bytes(int msg) { return msg == LBP_MSG_F32 ? 4 : (msg == LBP_MSG_F16 ? 2 : 1); }
 
 struct BpPlan {
-    bool ell = false;
+    bool ell = false, graph_smem = true, state_smem = true;
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -62,7 +62,8 @@ struct OsdWarpPlan {
 };
 
 struct WsLayout {
-    size_t counters = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, overflow = 0, slots = 0, total = 0;
+    size_t counters = 0, gstate = 0, osd_list = 0, osd_llr = 0, osd_mat = 0, overflow = 0, slots = 0,
+           total = 0;
 };
 
 int validate_params(const lbp_params *p) {
@@ -92,7 +93,39 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_
     p.off_misc = off; off = align16u(off + 16u);
     p.state_bytes = off;
     size_t image = c->ell.bytes;
-    p.ell = c->d_ell != nullptr && image + off <= static_cast<size_t>(c->smem_optin);
+    const size_t budget0 = static_cast<size_t>(c->smem_optin);
+    p.ell = c->d_ell != nullptr;
+    if (p.ell && image + off > budget0) {
+        // Large code: graph image from global memory (L2); state in shared
+        // memory when one group's fits, else in the workspace.
+        p.graph_smem = false;
+        p.state_smem = off <= budget0;
+        int G = 1024, S = 1;
+        if (p.state_smem) {
+            S = static_cast<int>(budget0 / off);
+            if (S < 1) S = 1;
+            G = 1024 / S >= 1024 ? 1024 : (1024 / S >= 512 ? 512 : 256);
+            if (S * G > 1024) S = 1024 / G;
+        } else {
+            G = 512;
+            S = 2;
+        }
+        if (req_G == 256 || req_G == 512 || req_G == 1024) {
+            G = req_G;
+            if (req_S > 0) S = req_S;
+            if (p.state_smem && static_cast<size_t>(S) * off > budget0) S = static_cast<int>(budget0 / off);
+            if (S * G > 1024) S = 1024 / G;
+            if (S < 1) S = 1;
+        }
+        p.groups = S;
+        p.G = G;
+        p.smem = p.state_smem ? static_cast<size_t>(S) * off : static_cast<size_t>(16) * S;
+        const int64_t need = (num_shots + S - 1) / S;
+        p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
+        if (p.grid < 1) p.grid = 1;
+        *out = p;
+        return LBP_OK;
+    }
     if (!p.ell) {
         if (!c->d_image) return LBP_ENOSYS;
         off = 0;
@@ -204,10 +237,14 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
 }
 
 WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, const OsdPlan *op,
-                const OsdWarpPlan *wp) {
+                const OsdWarpPlan *wp, const BpPlan *bp) {
     WsLayout w;
     size_t off = 0;
     w.counters = off; off = align256(off + 256);
+    if (bp && !bp->state_smem) {
+        w.gstate = off;
+        off = align256(off + static_cast<size_t>(bp->grid) * bp->groups * bp->state_bytes);
+    }
     if (prm->osd) {
         w.osd_list = off; off = align256(off + 4ull * num_shots);
         w.osd_llr = off;  off = align256(off + 4ull * num_shots * c->n);
@@ -285,7 +322,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         if (rc) return rc;
         plan_osd_warp(c, B, &wp);
     }
-    const WsLayout w = layout(c, prm, B, prm->osd ? &op : nullptr, prm->osd ? &wp : nullptr);
+    const WsLayout w = layout(c, prm, B, prm->osd ? &op : nullptr, prm->osd ? &wp : nullptr, &bp);
     if (!ws || ws_bytes < w.total) return LBP_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) & 255u) return LBP_EINVAL;
     uint8_t *base = static_cast<uint8_t *>(ws);
@@ -329,7 +366,9 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.llr = a.llr; e.counters = a.counters; e.osd_list = a.osd_list; e.osd_llr = a.osd_llr;
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
-        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem};
+        e.gstate = bp.state_smem ? nullptr : base + w.gstate;
+        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->m + 1) + 1);
+        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem};
         switch (prm->msg) {
             case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, e, c->ell.DC, c->ell.DV, stream); break;
             case LBP_MSG_F16: rc = launch_bp_ell_f16(shp, e, c->ell.DC, c->ell.DV, stream); break;
@@ -427,7 +466,9 @@ extern "C" size_t lbp_workspace_size(const lbp_code *code, const lbp_params *par
         if (plan_osd(code, num_shots, &op)) return 0;
         plan_osd_warp(code, num_shots, &wp);
     }
-    return layout(code, params, num_shots, params->osd ? &op : nullptr, params->osd ? &wp : nullptr).total;
+    BpPlan bp;
+    if (plan_bp(code, params->msg, num_shots, &bp)) return 0;
+    return layout(code, params, num_shots, params->osd ? &op : nullptr, params->osd ? &wp : nullptr, &bp).total;
 }
 
 extern "C" int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots,
@@ -527,7 +568,7 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     const int mi = params->msg;
     code->tuned_G[mi] = 0;
     code->tuned_groups[mi] = 0;
-    const int Gs[] = {32, 64, 96, 128, 192, 256};
+    const int Gs[] = {32, 64, 96, 128, 192, 256, 512, 1024};
     float best = -1.0f;
     int best_S = 0, best_G = 0;
     for (int G : Gs) {

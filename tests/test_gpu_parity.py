@@ -122,6 +122,17 @@ def test_precisions_on_d7_spacetime(msg):
     assert_parity(gpu_decode(st, pri, syn, **kw), oracle_decode(st, pri, syn, **kw))
 
 
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
+def test_c5_d25_spacetime_precisions(msg):
+    """d=25, 25 rounds (7,800 x 23,113): the graph image exceeds shared memory,
+    so the kernel reads it from global memory; FP32 state lives in the
+    workspace, FP16 / INT8 state in shared memory."""
+    w = workloads.c5_d25_spacetime(msg=msg, shots=300)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, seed=8)
+    assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
+
+
 def test_osd_bit_exact_on_gpu_llrs():
     """OSD fed with the GPU's exported LLRs gives the GPU's OSD output."""
     hx, _ = bb_code("bb72")
