@@ -13,13 +13,23 @@ namespace lbp {
 // ------------------------------------------------------------ message types
 
 template <typename T> struct Msg;
+// store_signed(mag, sgn): the stored message of value (sgn ? -mag : mag) for
+// mag >= 0 and sgn in {0, 0x80000000}; every storage rounding is symmetric
+// (round to nearest even, symmetric saturation), so rounding the magnitude
+// and then applying the sign equals rounding the signed value.
 template <> struct Msg<float> {
     static __device__ __forceinline__ float load(float x) { return x; }
     static __device__ __forceinline__ float store(float x) { return x; }
+    static __device__ __forceinline__ float store_signed(float mag, uint32_t sgn) {
+        return __uint_as_float(__float_as_uint(mag) ^ sgn);
+    }
 };
 template <> struct Msg<__half> {
     static __device__ __forceinline__ float load(__half x) { return __half2float(x); }
     static __device__ __forceinline__ __half store(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ __half store_signed(float mag, uint32_t sgn) {
+        return __ushort_as_half(static_cast<unsigned short>(__half_as_ushort(__float2half_rn(mag)) ^ (sgn >> 16)));
+    }
 };
 // Int3.4: q = clamp(rne(16 x), -127, 127), value q / 16.
 template <> struct Msg<int8_t> {
@@ -29,7 +39,30 @@ template <> struct Msg<int8_t> {
         q = q > 127 ? 127 : (q < -127 ? -127 : q);
         return static_cast<int8_t>(q);
     }
+    static __device__ __forceinline__ int8_t store_signed(float mag, uint32_t sgn) {
+        int q = __float2int_rn(__fmul_rn(16.0f, mag));
+        q = q > 127 ? 127 : q;
+        return static_cast<int8_t>(sgn ? -q : q);
+    }
 };
+
+// Two adjacent messages of one slot row, loaded / stored as one access.
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<__half> { using type = __half2; };
+template <> struct Pair<int8_t> { using type = char2; };
+
+template <typename T> __device__ __forceinline__ T pair_lo(typename Pair<T>::type p);
+template <typename T> __device__ __forceinline__ T pair_hi(typename Pair<T>::type p);
+template <> __device__ __forceinline__ float pair_lo<float>(float2 p) { return p.x; }
+template <> __device__ __forceinline__ float pair_hi<float>(float2 p) { return p.y; }
+template <> __device__ __forceinline__ __half pair_lo<__half>(__half2 p) { return __low2half(p); }
+template <> __device__ __forceinline__ __half pair_hi<__half>(__half2 p) { return __high2half(p); }
+template <> __device__ __forceinline__ int8_t pair_lo<int8_t>(char2 p) { return p.x; }
+template <> __device__ __forceinline__ int8_t pair_hi<int8_t>(char2 p) { return p.y; }
+__device__ __forceinline__ float2 make_pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ __half2 make_pair(__half a, __half b) { return __halves2half2(a, b); }
+__device__ __forceinline__ char2 make_pair(int8_t a, int8_t b) { return make_char2(a, b); }
 
 // -------------------------------------------------------------- group sync
 

@@ -1,27 +1,30 @@
-// K_bp (bounded degree): the same Alg. 1 + Alg. 3 iteration as bp_kernel,
+// K_bp (bounded degree): the Alg. 1 + Alg. 3 iteration of bp_kernel,
 // specialised for codes whose checks have at most DC ones and whose columns
 // at most DV ones (every surface-code space-time matrix: DC = 6, DV = 2; BB
 // codes: DC = 6, DV = 3).
 //
-// What changes against the general kernel is layout and instruction count:
-//  * Check side in ELL form, slot-major: cidx[k][c] is the k-th column of
-//    check c (ascending), padded with column n, whose prior and posterior are
-//    +inf (a neutral element of the check update: positive sign, never the
-//    minimum).  beta[k][c] (row length m + 1) is the message on that slot.
-//    Thread c reads slot k of consecutive checks from consecutive words: no
-//    bank conflicts, and loops over the DC slots unroll completely.
-//  * Column side in ELL form, slot-major: vent[k][v] is the offset
-//    (slot * (m + 1) + check) of the message of v's k-th check, ascending,
-//    padded with offset m, the message beta[0][m] = +0 (x + 0 == x for every
-//    partial sum, which is never -0), so the LLR update sums exactly the
-//    oracle's sequence of binary32 additions.  The check of an offset, needed
-//    only by the syndrome scatter and the lottery, is offset mod (m + 1),
-//    computed with an exact multiply-high division.
-//  * The lottery reads V(c*) and C(v) from the same ELL arrays.
-//  * Placement: the graph image and each group's state sit in shared memory
-//    when they fit (kGraphSmem, kStateSmem); otherwise they are read from
-//    global memory (the image is L2-resident; the state goes to a per-group
-//    slice of the workspace), which is how the d=25 space-time code runs.
+// Layout (all slot-major, uint16 indices):
+//  * Check side: cidx[k][c] is the k-th column of check c (ascending), padded
+//    with column n, whose prior and posterior are +inf: a neutral element of
+//    the check update (positive sign, never the minimum).  beta[k][c], row
+//    stride R = Mp + 2 (Mp = m rounded up to even), is the message on slot k.
+//  * Column side: vent[k][v] is the message offset k' * R + c of v's k-th
+//    check (ascending), padded with offset Mp, the message beta[0][Mp] = +0
+//    (x + 0 == x for every partial sum, which is never -0), so the LLR update
+//    sums exactly the oracle's sequence of binary32 additions.  The check of
+//    an offset, needed only by the syndrome scatter and the lottery, is
+//    offset mod R by an exact multiply-high division.
+//  * Each thread updates a pair of adjacent checks and a pair of adjacent
+//    columns, so index, message, prior and posterior accesses are paired
+//    32/64-bit accesses; an odd m or n gets one padding check / column.
+// Check update per check: sign bits r_k = [alpha_k < 0] << 31 and their XOR
+// t (with (-1)^{s_c}); exclusive minima of |alpha| from prefix and suffix
+// minima; beta_k = f * excl_k carrying sign bit t ^ r_k.  Same values as the
+// min1/min2/argmin form of bp_kernel, with fewer instructions.
+// Placement: the graph image and each group's state sit in shared memory when
+// they fit (kGraphSmem, kStateSmem); otherwise they are read from global
+// memory (the image is L2-resident; the state goes to a per-group slice of the
+// workspace), which is how the d=25 space-time code runs.
 // Everything else (groups of G threads per shot, named barriers, s_hat
 // scatter, early termination, lottery, outputs, OSD hand-off) is as in
 // bp_kernel.
@@ -36,7 +39,7 @@
 namespace lbp {
 
 struct BpEllArgs {
-    const uint8_t *image;     // ELL graph image (global), copied to shared memory
+    const uint8_t *image;     // ELL graph image (global)
     EllImage img;
     int32_t m, n;
     int32_t max_iter, scale_mode;
@@ -56,12 +59,38 @@ struct BpEllArgs {
     uint32_t state_bytes;
     uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
     uint8_t *gstate;          // per-group state slices when not in shared memory
-    uint32_t magic;           // floor(2^32 / (m + 1)) + 1: offset / (m + 1) by multiply-high
+    uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
 };
+
+// Exclusive minima and signed outputs of one check (DC slots).
+template <typename MsgT, int DC>
+__device__ __forceinline__ void check_update(const float (&al)[DC], uint32_t sbit, float f,
+                                             MsgT (&out)[DC]) {
+    uint32_t r[DC];
+    uint32_t tot = sbit << 31;
+    #pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        r[k] = al[k] < 0.0f ? 0x80000000u : 0u;
+        tot ^= r[k];
+    }
+    float pre[DC], suf[DC];
+    pre[0] = fabsf(al[0]);
+    #pragma unroll
+    for (int k = 1; k < DC; ++k) pre[k] = fminf(pre[k - 1], fabsf(al[k]));
+    suf[DC - 1] = fabsf(al[DC - 1]);
+    #pragma unroll
+    for (int k = DC - 2; k >= 0; --k) suf[k] = fminf(suf[k + 1], fabsf(al[k]));
+    #pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const float ex = k == 0 ? suf[1] : (k == DC - 1 ? pre[DC - 2] : fminf(pre[k - 1], suf[k + 1]));
+        out[k] = Msg<MsgT>::store_signed(__fmul_rn(f, ex), tot ^ r[k]);
+    }
+}
 
 template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
-    static_assert(DC <= 8 && DV <= 8, "bounded degrees");
+    static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
+    using PairT = typename Pair<MsgT>::type;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
@@ -70,11 +99,15 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     const int m = a.m, n = a.n, I = a.max_iter;
-    const int m1s = m + 1;                     // beta row stride
+    const int Mp = a.img.Mp, Np = a.img.Np, R = Mp + 2;
+    const int mpairs = Mp >> 1, npairs = Np >> 1;
     const uint8_t *gbase = kGraphSmem ? smem : a.image;
     const uint16_t *cidx = reinterpret_cast<const uint16_t *>(gbase + a.img.off_cidx);
+    const uint32_t *cidx2 = reinterpret_cast<const uint32_t *>(cidx);
     const uint16_t *vent = reinterpret_cast<const uint16_t *>(gbase + a.img.off_vent);
+    const uint32_t *vent2 = reinterpret_cast<const uint32_t *>(vent);
     const float *mu = reinterpret_cast<const float *>(gbase + a.img.off_mu);
+    const float2 *mu2 = reinterpret_cast<const float2 *>(mu);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
 
     const int grp = threadIdx.x / G;
@@ -90,11 +123,13 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         ? reinterpret_cast<volatile uint32_t *>(st + a.off_misc)
         : reinterpret_cast<volatile uint32_t *>(smem + image_smem + 16 * grp);
     MsgT *beta = reinterpret_cast<MsgT *>(st + a.off_beta);
+    PairT *beta2 = reinterpret_cast<PairT *>(beta);
     float *lam = reinterpret_cast<float *>(st + a.off_lam);
+    float2 *lam2 = reinterpret_cast<float2 *>(lam);
     uint32_t *s_w = reinterpret_cast<uint32_t *>(st + a.off_s);
     uint32_t *shat = reinterpret_cast<uint32_t *>(st + a.off_shat);
     if (t == 0) {
-        beta[m] = Msg<MsgT>::store(0.0f);                 // column-side padding message
+        beta[Mp] = Msg<MsgT>::store(0.0f);                // column-side padding message
         lam[n] = __int_as_float(0x7f800000);              // check-side padding column
     }
     __syncthreads();
@@ -126,58 +161,58 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         int it = 0;
         for (; it < I; ++it) {
             const float f = scale_at(a.scale_mode, a.scale_const, it);
-            // ---- C2V -------------------------------------------------------
-            for (int c = t; c < m; c += G) {
-                float al[DC];
+            // ---- C2V, two adjacent checks per thread ---------------------------
+            for (int pr = t; pr < mpairs; pr += G) {
+                const int c = 2 * pr;
+                float al0[DC], al1[DC];
                 if (it == 0) {
                     #pragma unroll
-                    for (int k = 0; k < DC; ++k) al[k] = mu[cidx[k * m + c]];
+                    for (int k = 0; k < DC; ++k) {
+                        const uint32_t cc = cidx2[k * mpairs + pr];
+                        al0[k] = mu[cc & 0xffffu];
+                        al1[k] = mu[cc >> 16];
+                    }
                 } else {
                     #pragma unroll
-                    for (int k = 0; k < DC; ++k)
-                        al[k] = __fsub_rn(lam[cidx[k * m + c]], Msg<MsgT>::load(beta[k * m1s + c]));
+                    for (int k = 0; k < DC; ++k) {
+                        const uint32_t cc = cidx2[k * mpairs + pr];
+                        const PairT bb = beta2[((k * R) >> 1) + pr];
+                        al0[k] = __fsub_rn(lam[cc & 0xffffu], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
+                        al1[k] = __fsub_rn(lam[cc >> 16], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
+                    }
                 }
-                unsigned parity = (s_w[c >> 5] >> (c & 31)) & 1u;
-                unsigned negmask = 0u;
-                float min1 = __int_as_float(0x7f800000), min2 = min1;
-                int pos = 0;
+                const uint32_t sw = s_w[c >> 5];               // c even: c and c + 1 share a word
+                MsgT o0[DC], o1[DC];
+                check_update<MsgT, DC>(al0, (sw >> (c & 31)) & 1u, f, o0);
+                check_update<MsgT, DC>(al1, (sw >> ((c & 31) + 1)) & 1u, f, o1);
                 #pragma unroll
-                for (int k = 0; k < DC; ++k) {
-                    const unsigned ng = al[k] < 0.0f ? 1u : 0u;
-                    negmask |= ng << k;
-                    parity ^= ng;
-                    const float aa = fabsf(al[k]);
-                    const bool lt = aa < min1;
-                    min2 = lt ? min1 : fminf(min2, aa);
-                    pos = lt ? k : pos;
-                    min1 = lt ? aa : min1;
-                }
-                const float m1 = __fmul_rn(f, min1);
-                const float m2 = __fmul_rn(f, min2);
-                #pragma unroll
-                for (int k = 0; k < DC; ++k) {
-                    const float mag = (k == pos) ? m2 : m1;
-                    const unsigned ng = (parity ^ (negmask >> k)) & 1u;
-                    beta[k * m1s + c] = Msg<MsgT>::store(ng ? -mag : mag);
-                }
+                for (int k = 0; k < DC; ++k) beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
             }
             group_sync<G>(bar);
-            // ---- LLR update, hard decision, syndrome scatter -------------------
+            // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
-            for (int v = t; v < n; v += G) {
-                unsigned ent[DV];
-                float acc = mu[v];
+            for (int q = t; q < npairs; q += G) {
+                uint32_t ent[DV];
+                const float2 mm = mu2[q];
+                float acc0 = mm.x, acc1 = mm.y;
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
-                    ent[k] = vent[k * n + v];
-                    acc = __fadd_rn(acc, Msg<MsgT>::load(beta[ent[k]]));
+                    ent[k] = vent2[k * npairs + q];
+                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[ent[k] & 0xffffu]));
+                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[ent[k] >> 16]));
                 }
-                lam[v] = acc;
-                if (acc <= 0.0f) {
+                lam2[q] = make_float2(acc0, acc1);
+                if (acc0 <= 0.0f || acc1 <= 0.0f) {
                     #pragma unroll
                     for (int k = 0; k < DV; ++k) {
-                        const unsigned r = ent[k] - __umulhi(ent[k], a.magic) * static_cast<unsigned>(m1s);
-                        if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
+                        #pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if ((h == 0 ? acc0 : acc1) <= 0.0f) {
+                                const unsigned o = h == 0 ? (ent[k] & 0xffffu) : (ent[k] >> 16);
+                                const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
+                                if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
+                            }
+                        }
                     }
                 }
             }
@@ -227,8 +262,8 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                             if (own) {
                                 int pick = 0;
                                 if (mine) {
-                                    uint32_t r = k - base - excl;
-                                    while (r--) word &= word - 1u;
+                                    uint32_t rr = k - base - excl;
+                                    while (rr--) word &= word - 1u;
                                     pick = w * 32 + (__ffs(word) - 1);
                                 }
                                 cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
@@ -239,14 +274,14 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                         int bc = -1, bv = 0x7fffffff;
                         float ba = 0.0f;
                         if (lane < DC) {
-                            const int v = cidx[lane * m + cstar];
+                            const int v = cidx[lane * Mp + cstar];
                             if (v < n) {
                                 bv = v;
                                 bc = 0;
                                 #pragma unroll
                                 for (int kk = 0; kk < DV; ++kk) {
-                                    const unsigned o = vent[kk * n + v];
-                                    const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(m1s);
+                                    const unsigned o = vent[kk * Np + v];
+                                    const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
                                     if (r < static_cast<unsigned>(m))
                                         bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
                                 }

@@ -26,15 +26,17 @@ struct GraphImage {
     uint32_t off_mu;         // f32[n]     prior LLR
 };
 
-// ELL image for bounded-degree codes (bp_ell_kernel): check side cidx[DC][m]
-// (column ids, padding n) and column side vent[DV][n] (message offset
-// slot * (m + 1) + check, padding m), both slot-major uint16, then mu[n + 1]
-// with mu[n] = +inf.  Exists when every check has <= 8 ones, every column
-// <= 4, DC * (m + 1) < 65536 and n < 65535.
+// ELL image for bounded-degree codes (bp_ell_kernel), with Mp, Np = m, n
+// rounded up to even and R = Mp + 2: check side cidx[DC][Mp] (column ids,
+// padding n) and column side vent[DV][Np] (message offset slot * R + check,
+// padding Mp), both slot-major uint16, then mu[Np + 2] with mu[n] = +inf.
+// Exists when every check has <= 8 ones, every column <= 4, DC * R < 65536 and
+// n < 65535.
 struct EllImage {
     uint32_t bytes;
     uint32_t off_cidx, off_vent, off_mu;
     int32_t DC, DV;
+    int32_t Mp, Np;          // m and n rounded up to even (paired accesses)
 };
 
 }  // namespace lbp

@@ -86,8 +86,8 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_
     BpPlan p;
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
     uint32_t off = 0;
-    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * (c->m + 1));
-    p.off_lam = off;  off = align16u(off + 4u * (c->n + 1));
+    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * (c->ell.Mp + 2));
+    p.off_lam = off;  off = align16u(off + 4u * (c->ell.Np + 2));
     p.off_s = off;    off = align16u(off + 4u * W32);
     p.off_shat = off; off = align16u(off + 12u * W32);
     p.off_misc = off; off = align16u(off + 16u);
@@ -367,7 +367,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
-        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->m + 1) + 1);
+        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
         const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem};
         switch (prm->msg) {
             case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, e, c->ell.DC, c->ell.DV, stream); break;
