@@ -160,6 +160,45 @@ int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_
                     uint8_t *osd_out, int32_t *iters_out, float *llr_out,
                     void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---- Serving: continuous batching on one device ---------------------------
+ *
+ * A server owns a device arena (one cudaMalloc of arena_bytes at creation),
+ * max_inflight CUDA streams and a scheduler thread.  Requests are decodes of
+ * loaded codes with HOST buffers (pinned memory makes the copies
+ * asynchronous).  The scheduler admits the oldest waiting request as soon as
+ * a stream is free and the arena has room for its device buffers and
+ * workspace (admission by memory); each admitted request runs H2D copy,
+ * decode and D2H copies on its own stream, so requests overlap on the device
+ * and a request that arrives while others run starts as soon as a slot and
+ * memory free up.  A request's results depend only on its code, parameters
+ * and syndromes, never on the other requests in flight.  The caller keeps the
+ * host buffers and the code alive until the request completes.
+ * The paper's decoder is a single-stream pipeline; this service is the GPU
+ * deployment around it. */
+typedef struct lbp_server lbp_server;
+
+/* Create a server on the current device.  Errors: LBP_EINVAL (arena_bytes <
+ * 4096 or max_inflight outside [1, 64]), LBP_ENOMEM, LBP_ECUDA. */
+int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_server **out);
+
+/* Queue a decode (buffers as for lbp_decode_host, osd_out may be NULL) and
+ * return its ticket.  LBP_E2BIG if the request can never fit the arena. */
+int lbp_server_submit(lbp_server *server, const lbp_code *code, const lbp_params *params,
+                      int64_t num_shots, const uint64_t *syndromes, uint64_t *err_out,
+                      uint8_t *converged, uint8_t *osd_out, int32_t *iters_out, int64_t *ticket);
+
+/* Non-blocking: *done = 1 once the request's outputs are in its host buffers,
+ * then *latency_s (nullable) is submission-to-completion time in seconds and
+ * the return value is the request's status; a completed ticket is forgotten
+ * after it has been reported once. */
+int lbp_server_poll(lbp_server *server, int64_t ticket, int *done, double *latency_s);
+
+/* Blocking version of lbp_server_poll. */
+int lbp_server_wait(lbp_server *server, int64_t ticket, double *latency_s);
+
+/* Drain every queued and in-flight request, then release the server. */
+int lbp_server_destroy(lbp_server *server);
+
 /* Same decode as lbp_decode, for callers that cannot allocate device memory
  * (no cudaMalloc, no allocator callback: e.g. a latency-bound request loop on
  * a pre-sized device, a plugin whose host owns every allocation, a caller

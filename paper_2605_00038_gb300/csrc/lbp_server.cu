@@ -1,0 +1,330 @@
+// lbp_server_*: a continuous-batching decode service on one device.
+//
+// Requests (host syndromes of any loaded code) enter a FIFO.  A scheduler
+// thread admits the oldest waiting request as soon as an in-flight slot is
+// free and the device arena has room for its buffers (syndromes, outputs and
+// decode workspace): admission by memory, not by a fixed batch.  An admitted
+// request gets its own stream: host-to-device copy, lbp_decode, device-to-host
+// copies, then an event.  Requests therefore overlap on the device: a small
+// request launches into the SMs a large one leaves idle, and work that
+// arrives while others run starts without waiting for them to finish.  The
+// scheduler frees a request's arena space when its event completes and
+// records its latency (submission to completion, host clock).
+//
+// Each request's results depend only on its code, parameters (seed and
+// shot_offset included) and syndromes, never on what else is in flight.
+//
+// The arena is one cudaMalloc made at creation; admission uses first-fit over
+// it, so no allocation happens while serving.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct Request {
+    int64_t ticket;
+    const lbp_code *code;
+    lbp_params params;
+    int64_t shots;
+    const uint64_t *syn;
+    uint64_t *err;
+    uint8_t *conv, *osd;
+    int32_t *iters;
+    Clock::time_point submitted;
+    // While in flight:
+    int slot = -1;
+    size_t arena_off = 0, arena_bytes = 0;
+    int status = LBP_OK;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    Request req;
+};
+
+// First-fit allocator over [0, size).
+struct Arena {
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> bytes
+    void init(size_t s) { size = s; free_.clear(); free_[0] = s; }
+    bool alloc(size_t bytes, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t noff = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[noff] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Layout {
+    size_t syn, err, conv, osd, iters, ws, ws_bytes, total;
+};
+
+bool request_layout(const lbp_code *c, const lbp_params *p, int64_t B, Layout *L) {
+    const size_t wsz = lbp_workspace_size(c, p, B);
+    if (wsz == 0) return false;
+    const size_t wm = (c->m + 63) / 64, wn = (c->n + 63) / 64;
+    size_t off = 0;
+    L->syn = off;   off = al256(off + 8 * wm * B);
+    L->err = off;   off = al256(off + 8 * wn * B);
+    L->conv = off;  off = al256(off + B);
+    L->osd = off;   off = al256(off + B);
+    L->iters = off; off = al256(off + 4 * B);
+    L->ws = off;    off = al256(off + wsz);
+    L->ws_bytes = wsz;
+    L->total = off;
+    return true;
+}
+
+}  // namespace
+
+struct lbp_server {
+    int device = 0;
+    uint8_t *arena_base = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::deque<Request> waiting;
+    std::map<int64_t, std::pair<int, double>> finished;   // ticket -> (status, latency s)
+    std::map<int64_t, bool> known;                         // tickets not yet collected
+    int64_t next_ticket = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread worker;
+    // statistics
+    int64_t completed = 0, shots_done = 0;
+};
+
+namespace {
+
+void launch(lbp_server *s, int si) {
+    Slot &sl = s->slots[si];
+    Request &r = sl.req;
+    Layout L;
+    request_layout(r.code, &r.params, r.shots, &L);
+    uint8_t *base = s->arena_base + r.arena_off;
+    const size_t wm = (r.code->m + 63) / 64, wn = (r.code->n + 63) / 64;
+    const int64_t B = r.shots;
+    cudaStream_t st = sl.stream;
+    int rc = LBP_OK;
+    if (cudaMemcpyAsync(base + L.syn, r.syn, 8 * wm * B, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = LBP_ECUDA;
+    if (rc == LBP_OK)
+        rc = lbp::decode_device(r.code, &r.params, B, reinterpret_cast<const uint64_t *>(base + L.syn),
+                                reinterpret_cast<uint64_t *>(base + L.err), base + L.conv, base + L.osd,
+                                reinterpret_cast<int32_t *>(base + L.iters), nullptr, base + L.ws,
+                                L.ws_bytes, st);
+    if (rc == LBP_OK) {
+        bool ok = cudaMemcpyAsync(r.err, base + L.err, 8 * wn * B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(r.conv, base + L.conv, B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(r.iters, base + L.iters, 4 * B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (r.osd) ok = ok && cudaMemcpyAsync(r.osd, base + L.osd, B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (!ok) rc = LBP_ECUDA;
+    }
+    if (rc != LBP_OK) cudaGetLastError();
+    r.status = rc;
+    cudaEventRecord(sl.done, st);
+}
+
+void run(lbp_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        // Retire finished requests.
+        bool progressed = false;
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            Slot &sl = s->slots[i];
+            if (!sl.busy) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                sl.req.status = LBP_ECUDA;
+            }
+            const double lat = std::chrono::duration<double>(Clock::now() - sl.req.submitted).count();
+            s->finished[sl.req.ticket] = {sl.req.status, lat};
+            s->arena.release(sl.req.arena_off, sl.req.arena_bytes);
+            s->completed += 1;
+            s->shots_done += sl.req.shots;
+            sl.busy = false;
+            progressed = true;
+        }
+        if (progressed) s->cv_done.notify_all();
+        // Admit waiting requests, oldest first, while a slot and memory allow.
+        while (!s->waiting.empty()) {
+            int free_slot = -1;
+            for (size_t i = 0; i < s->slots.size(); ++i)
+                if (!s->slots[i].busy) { free_slot = static_cast<int>(i); break; }
+            if (free_slot < 0) break;
+            Request &r = s->waiting.front();
+            Layout L;
+            request_layout(r.code, &r.params, r.shots, &L);
+            size_t off = 0;
+            if (!s->arena.alloc(L.total, &off)) break;           // wait for memory to free up
+            Slot &sl = s->slots[free_slot];
+            sl.req = r;
+            sl.req.arena_off = off;
+            sl.req.arena_bytes = L.total;
+            sl.req.slot = free_slot;
+            sl.busy = true;
+            s->waiting.pop_front();
+            launch(s, free_slot);
+            progressed = true;
+        }
+        bool any_busy = false;
+        for (auto &sl : s->slots) any_busy = any_busy || sl.busy;
+        if (s->stop && !any_busy && s->waiting.empty()) break;
+        if (!any_busy && s->waiting.empty()) {
+            s->cv_work.wait(lk, [&] { return s->stop || !s->waiting.empty(); });
+        } else if (!progressed) {
+            // Work is on the device: poll again shortly (bounded wait, no spin).
+            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_server **out) {
+    if (!out) return LBP_EINVAL;
+    *out = nullptr;
+    if (arena_bytes < 4096 || max_inflight < 1 || max_inflight > 64) return LBP_EINVAL;
+    lbp_server *s = new (std::nothrow) lbp_server();
+    if (!s) return LBP_ENOMEM;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBP_ECUDA; }
+    if (cudaMalloc(reinterpret_cast<void **>(&s->arena_base), arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return LBP_ENOMEM;
+    }
+    s->arena.init(arena_bytes);
+    s->slots.resize(max_inflight);
+    for (auto &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : s->slots) {
+                if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.done) cudaEventDestroy(x.done);
+            }
+            cudaFree(s->arena_base);
+            delete s;
+            return LBP_ECUDA;
+        }
+    }
+    s->worker = std::thread(run, s);
+    *out = s;
+    return LBP_OK;
+}
+
+extern "C" int lbp_server_submit(lbp_server *s, const lbp_code *code, const lbp_params *params,
+                                 int64_t num_shots, const uint64_t *syndromes, uint64_t *err_out,
+                                 uint8_t *converged, uint8_t *osd_out, int32_t *iters_out,
+                                 int64_t *ticket) {
+    if (!s || !code || !params || !ticket || num_shots < 1 || !syndromes || !err_out || !converged ||
+        !iters_out)
+        return LBP_EINVAL;
+    if (code->device != s->device) return LBP_EINVAL;
+    Layout L;
+    if (!request_layout(code, params, num_shots, &L)) return LBP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (L.total > s->arena.size) return LBP_E2BIG;            // can never be admitted
+    if (s->stop) return LBP_EINVAL;
+    Request r;
+    r.ticket = s->next_ticket++;
+    r.code = code;
+    r.params = *params;
+    r.shots = num_shots;
+    r.syn = syndromes;
+    r.err = err_out;
+    r.conv = converged;
+    r.osd = osd_out;
+    r.iters = iters_out;
+    r.submitted = Clock::now();
+    s->waiting.push_back(r);
+    s->known[r.ticket] = true;
+    *ticket = r.ticket;
+    s->cv_work.notify_one();
+    return LBP_OK;
+}
+
+extern "C" int lbp_server_poll(lbp_server *s, int64_t ticket, int *done, double *latency_s) {
+    if (!s || !done) return LBP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->known.count(ticket)) return LBP_EINVAL;
+    auto it = s->finished.find(ticket);
+    if (it == s->finished.end()) { *done = 0; return LBP_OK; }
+    *done = 1;
+    if (latency_s) *latency_s = it->second.second;
+    const int st = it->second.first;
+    s->finished.erase(it);
+    s->known.erase(ticket);
+    return st;
+}
+
+extern "C" int lbp_server_wait(lbp_server *s, int64_t ticket, double *latency_s) {
+    if (!s) return LBP_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (!s->known.count(ticket)) return LBP_EINVAL;
+    s->cv_done.wait(lk, [&] { return s->finished.count(ticket) > 0; });
+    auto it = s->finished.find(ticket);
+    if (latency_s) *latency_s = it->second.second;
+    const int st = it->second.first;
+    s->finished.erase(it);
+    s->known.erase(ticket);
+    return st;
+}
+
+extern "C" int lbp_server_destroy(lbp_server *s) {
+    if (!s) return LBP_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto &sl : s->slots) {
+        cudaStreamSynchronize(sl.stream);
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.done);
+    }
+    cudaFree(s->arena_base);
+    delete s;
+    return LBP_OK;
+}

@@ -24,7 +24,9 @@ LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
-            "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_strerror"]
+            "lbp_server_create", "lbp_server_submit", "lbp_server_poll", "lbp_server_wait",
+            "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
+            "lbp_strerror"]
 
 
 class lbp_params(ctypes.Structure):
@@ -73,6 +75,16 @@ def lib():
         L.lbp_decode_host.argtypes = dec
         L.lbp_tune.restype = ctypes.c_int
         L.lbp_tune.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.lbp_server_create.restype = ctypes.c_int
+        L.lbp_server_create.argtypes = [sz, ctypes.c_int, ctypes.POINTER(vp)]
+        L.lbp_server_submit.restype = ctypes.c_int
+        L.lbp_server_submit.argtypes = [vp, vp, P, i64, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+        L.lbp_server_poll.restype = ctypes.c_int
+        L.lbp_server_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.lbp_server_wait.restype = ctypes.c_int
+        L.lbp_server_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double)]
+        L.lbp_server_destroy.restype = ctypes.c_int
+        L.lbp_server_destroy.argtypes = [vp]
         L.lbp_decode_noalloc.restype = ctypes.c_int
         L.lbp_decode_noalloc.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, vp]
         L.lbp_timing_enable.restype = ctypes.c_int
@@ -234,3 +246,59 @@ def lbp_timing_read():
     _check(lib().lbp_timing_read(ctypes.byref(bm), ctypes.byref(bl), ctypes.byref(om),
                                  ctypes.byref(ol)), "lbp_timing_read")
     return bm.value, bl.value, om.value, ol.value
+
+
+class Server:
+    """Owning handle of an lbp_server."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ctypes.c_void_p(ptr)
+
+    def close(self):
+        if self.ptr:
+            lbp_server_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbp_server_create(arena_bytes: int, max_inflight: int) -> Server:
+    out = ctypes.c_void_p()
+    _check(lib().lbp_server_create(arena_bytes, max_inflight, ctypes.byref(out)), "lbp_server_create")
+    return Server(out.value)
+
+
+def lbp_server_submit(server: Server, code: Code, params: lbp_params, num_shots: int, syndromes,
+                      err_out, converged, osd_out, iters_out) -> int:
+    """Queue a decode with host buffers; returns the ticket.  The buffers must
+    stay alive (and unchanged) until the request completes."""
+    t = ctypes.c_int64()
+    _check(lib().lbp_server_submit(server.ptr, code.ptr, ctypes.byref(params), num_shots,
+                                   _hptr(syndromes), _hptr(err_out), _hptr(converged),
+                                   _hptr(osd_out), _hptr(iters_out), ctypes.byref(t)),
+           "lbp_server_submit")
+    return t.value
+
+
+def lbp_server_poll(server: Server, ticket: int):
+    """Returns (done, latency_s or None); raises if the request failed."""
+    done, lat = ctypes.c_int(), ctypes.c_double()
+    rc = lib().lbp_server_poll(server.ptr, ticket, ctypes.byref(done), ctypes.byref(lat))
+    _check(rc, "lbp_server_poll")
+    return bool(done.value), (lat.value if done.value else None)
+
+
+def lbp_server_wait(server: Server, ticket: int) -> float:
+    lat = ctypes.c_double()
+    _check(lib().lbp_server_wait(server.ptr, ticket, ctypes.byref(lat)), "lbp_server_wait")
+    return lat.value
+
+
+def lbp_server_destroy(server: Server):
+    if server.ptr:
+        rc = lib().lbp_server_destroy(server.ptr)
+        server.ptr = ctypes.c_void_p()
+        _check(rc, "lbp_server_destroy")

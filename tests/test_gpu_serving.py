@@ -1,0 +1,130 @@
+"""Serving: continuous batching through lbp_server_*.
+
+Requests of several codes and sizes are submitted from two host threads while
+others run; every request's result must equal the same request decoded alone
+with lbp_decode (bit-identical: the decode of a shot depends only on its
+syndrome, the code and the parameters)."""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2605_00038_gb300 import lbp
+from paper_2605_00038_gb300.decoder import Decoder
+from paper_2605_00038_gb300.inputs import sampler
+from paper_2605_00038_gb300.inputs.codes import bb_code, rotated_surface, spacetime, spacetime_priors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _codes():
+    out = []
+    for d in (5, 7):
+        hz, _ = rotated_surface(d)
+        out.append((spacetime(hz, d), spacetime_priors(hz, d, 0.004, 0.004)))
+    for name, p in (("bb72", 0.03), ("bb144", 0.02)):
+        hx, _ = bb_code(name)
+        out.append((hx, np.full(hx.n, p)))
+    return out
+
+
+def _requests(codes, count, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        ci = int(rng.integers(len(codes)))
+        h, pri = codes[ci]
+        B = int(np.exp(rng.uniform(0, np.log(700))))
+        off = int(rng.integers(0, 1 << 30))
+        _, syn = sampler.sample(h, pri, seed=10 + ci, num_shots=B, shot_offset=off)
+        reqs.append(dict(ci=ci, B=B, off=off, syn=syn, msg=int(rng.integers(0, 3))))
+    return reqs
+
+
+def _alone(decs, codes, r):
+    dec = decs[r["ci"]]
+    prm = dec.params(max_iter=60, lottery=1, osd=1, msg=r["msg"], seed=5, shot_offset=r["off"])
+    out = dec.decode(torch.from_numpy(r["syn"].view(np.int64)).cuda(), prm)
+    torch.cuda.synchronize()
+    return (out.err.cpu().numpy().view(np.uint64), out.converged.cpu().numpy(),
+            out.osd.cpu().numpy(), out.iters.cpu().numpy())
+
+
+def _device_bytes(dec, r):
+    h = dec.h
+    prm = dec.params(max_iter=60, lottery=1, osd=1, msg=r["msg"], seed=5, shot_offset=r["off"])
+    B = r["B"]
+    io = B * (8 * ((h.m + 63) // 64) + 8 * ((h.n + 63) // 64) + 6) + 6 * 256
+    return lbp.lbp_workspace_size(dec.code, prm, B) + io + 256
+
+
+@pytest.mark.parametrize("tight,inflight", [(False, 8), (True, 4)])
+def test_results_alone_equal_results_in_the_mix(tight, inflight):
+    """tight: the arena holds about 1.5 of the largest request, so admission
+    waits for memory, not for a free stream."""
+    codes = _codes()
+    decs = [Decoder(h, pri) for h, pri in codes]
+    reqs = _requests(codes, 40, seed=int(tight))
+    ref = [_alone(decs, codes, r) for r in reqs]
+    arena = (512 << 20) if not tight else int(1.5 * max(_device_bytes(decs[r["ci"]], r) for r in reqs))
+    srv = lbp.lbp_server_create(arena, inflight)
+    bufs = []
+    for r in reqs:
+        h = codes[r["ci"]][0]
+        bufs.append(dict(err=np.zeros((r["B"], (h.n + 63) // 64), np.uint64),
+                         conv=np.zeros(r["B"], np.uint8), osd=np.zeros(r["B"], np.uint8),
+                         iters=np.zeros(r["B"], np.int32)))
+    tickets = [None] * len(reqs)
+
+    def submit(idx):
+        rng = np.random.default_rng(idx[0])
+        for i in idx:
+            r = reqs[i]
+            prm = decs[r["ci"]].params(max_iter=60, lottery=1, osd=1, msg=r["msg"], seed=5,
+                                       shot_offset=r["off"])
+            b = bufs[i]
+            tickets[i] = lbp.lbp_server_submit(srv, decs[r["ci"]].code, prm, r["B"], r["syn"],
+                                               b["err"], b["conv"], b["osd"], b["iters"])
+            if rng.random() < 0.3:
+                threading.Event().wait(0.002)
+
+    th = [threading.Thread(target=submit, args=(list(range(k, len(reqs), 2)),)) for k in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    lats = [lbp.lbp_server_wait(srv, t) for t in tickets]
+    srv.close()
+    assert all(x > 0 for x in lats)
+    for i, r in enumerate(reqs):
+        e, c, o, it = ref[i]
+        b = bufs[i]
+        assert np.array_equal(b["err"], e) and np.array_equal(b["conv"], c)
+        assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it)
+    for d in decs:
+        d.close()
+
+
+def test_request_larger_than_the_arena_is_refused():
+    hx, _ = bb_code("bb144")
+    dec = Decoder(hx, np.full(hx.n, 0.02))
+    srv = lbp.lbp_server_create(1 << 16, 2)
+    B = 4096
+    syn = np.zeros((B, 2), np.uint64)
+    with pytest.raises(lbp.LbpError) as ei:
+        lbp.lbp_server_submit(srv, dec.code, dec.params(osd=1), B, syn, np.zeros((B, 3), np.uint64),
+                              np.zeros(B, np.uint8), None, np.zeros(B, np.int32))
+    assert ei.value.code == lbp.LBP_E2BIG
+    srv.close()
+    dec.close()
