@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle shots for cpu_baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip lbp_tune (default launch shape)")
+    ap.add_argument("--serving-only", action="store_true", help="print the serving and matched-LER results only")
     return ap.parse_args()
 
 
@@ -357,6 +358,9 @@ def run_gpu(args):
         line["quality"] = {"ler": fails / B, "shots": B, "logical_failures": fails}
 
     if not args.no_extras and rank == 0 and world == 1:
+        line["serving"] = run_serving()
+        line["matched_ler"] = run_matched()
+    if not args.no_extras and rank == 0 and world == 1:
         import oracle
         cores = os.cpu_count() or 1
         S = sampler.unpack(syn_h[0][: args.cpu_sample], w.h.m)
@@ -375,8 +379,185 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11):
+    """Serving mix: Poisson arrivals of 1-4096-shot requests over ten resident
+    codes (rotated surface space-time d = 5..17 with d rounds, BB 72/144/288
+    code capacity) and five noise levels 1e-3..5e-3; Lottery BP + OSD-0,
+    I = 100, FP16 messages.  Capacity first (all requests queued at once), then
+    open-loop arrivals at 50 / 80 / 95 % of it."""
+    import torch
+    from paper_2605_00038_gb300 import lbp
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+    from paper_2605_00038_gb300.inputs.codes import spacetime_priors
+
+    ps = (0.001, 0.002, 0.003, 0.004, 0.005)
+    codes = workloads.serving_codes()
+    decs = {}
+    rounds = {}
+    for ci, (name, h, st_info) in enumerate(codes):
+        for pi, p in enumerate(ps):
+            if st_info is not None:
+                hz, d = st_info
+                pri = spacetime_priors(hz, d, p, p)
+                rounds[ci] = d
+            else:
+                pri = np.full(h.n, p)
+                rounds[ci] = 1
+            decs[(ci, pi)] = Decoder(h, pri)
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n_requests):
+        ci, pi = int(rng.integers(len(codes))), int(rng.integers(len(ps)))
+        B = int(round(np.exp(rng.uniform(0, np.log(4096)))))
+        dec = decs[(ci, pi)]
+        h = dec.h
+        _, syn = sampler.sample(h, dec_priors(dec), seed=seed + ci, num_shots=B, shot_offset=i << 16)
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+        s = pin(syn.shape, torch.int64)
+        s.numpy()[:] = syn.view(np.int64)
+        reqs.append(dict(ci=ci, pi=pi, B=B, syn=s, err=pin((B, (h.n + 63) // 64), torch.int64),
+                         conv=pin(B, torch.uint8), osd=pin(B, torch.uint8), iters=pin(B, torch.int32),
+                         prm=dec.params(max_iter=100, lottery=1, osd=1, msg=1, seed=seed,
+                                        shot_offset=i << 16)))
+    srv = lbp.lbp_server_create(8 << 30, 16)
+
+    def submit(r):
+        return lbp.lbp_server_submit(srv, decs[(r["ci"], r["pi"])].code, r["prm"], r["B"], r["syn"],
+                                     r["err"], r["conv"], r["osd"], r["iters"])
+
+    # warm-up: one request per code / noise pair
+    for k in range(min(len(reqs), 50)):
+        lbp.lbp_server_wait(srv, submit(reqs[k]))
+    t0 = time.perf_counter()
+    tickets = [submit(r) for r in reqs]
+    for t in tickets:
+        lbp.lbp_server_wait(srv, t)
+    dt = time.perf_counter() - t0
+    total_shots = sum(r["B"] for r in reqs)
+    cap_req = len(reqs) / dt
+    out = {"codes": len(codes), "noise_levels": len(ps), "requests": len(reqs),
+           "mean_request_shots": total_shots / len(reqs), "capacity_shots_per_s": total_shots / dt,
+           "capacity_requests_per_s": cap_req, "rates": []}
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap_req
+        n = max(20, min(len(reqs), int(rate * seconds_per_rate)))
+        gaps = rng.exponential(1.0 / rate, size=n)
+        order = rng.permutation(len(reqs))[:n]
+        sent = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for j, i in enumerate(order):
+            t_next += gaps[j]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                time.sleep(min(0.0005, t_next - now))
+            sent.append((i, submit(reqs[i])))
+        lats, per_round = [], []
+        for i, t in sent:
+            lat = lbp.lbp_server_wait(srv, t)
+            lats.append(lat)
+            per_round.append(lat / rounds[reqs[i]["ci"]])
+        span = time.perf_counter() - t_start
+        q = lambda a, x: float(np.quantile(np.asarray(a), x) * 1e3)
+        out["rates"].append({"load": load, "offered_requests_per_s": rate, "requests": n,
+                             "shots_per_s": sum(reqs[i]["B"] for i, _ in sent) / span,
+                             "p50_ms": q(lats, 0.5), "p99_ms": q(lats, 0.99),
+                             "p50_ms_per_round": q(per_round, 0.5), "p99_ms_per_round": q(per_round, 0.99)})
+    srv.close()
+    for d in decs.values():
+        d.close()
+    return out
+
+
+def dec_priors(dec):
+    return dec.priors
+
+
+def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
+    """Matched-LER head-to-head on identical shots of the rotated d=7 surface
+    code, 7 noisy rounds, p = 0.012: (A) plain NMS BP + OSD-0, FP32 messages,
+    one batched lbp_decode; (B) Lottery BP + OSD-0, FP16 messages, served in
+    4096-shot requests through lbp_server.  Logical error rates with Wilson
+    95% intervals and the paired McNemar test, throughput and p99 latency."""
+    import torch
+    from paper_2605_00038_gb300 import evaluate, lbp
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler
+    from paper_2605_00038_gb300.inputs.codes import rotated_surface, spacetime, spacetime_priors
+
+    d, p = 7, 0.012
+    hz, _ = rotated_surface(d)
+    h = spacetime(hz, d)
+    pri = spacetime_priors(hz, d, p, p)
+    e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
+    spec = evaluate.surface_spec(d, d, h.n)
+    true_d = torch.from_numpy(e.view(np.int64)).cuda()
+    dec = Decoder(h, pri)
+    # Arm A: plain BP + OSD-0, FP32, batched.
+    pa = dec.params(max_iter=100, lottery=0, osd=1, msg=0, seed=seed)
+    sd = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec.decode(sd, pa)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    ra = dec.decode(sd, pa)
+    ev1.record()
+    torch.cuda.synchronize()
+    ta = ev0.elapsed_time(ev1) / 1e3
+    fa = evaluate.logical_failures(spec, true_d, ra.err, ra.converged, ra.osd)
+    # Arm B: Lottery BP + OSD-0, FP16, served.
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+    hs = pin(syn.shape, torch.int64)
+    hs.numpy()[:] = syn.view(np.int64)
+    wn = (h.n + 63) // 64
+    herr, hconv, hosd, hit = pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8), pin(shots, torch.int32)
+    srv = lbp.lbp_server_create(8 << 30, 16)
+    reqs = []
+    for lo in range(0, shots, request):
+        B = min(request, shots - lo)
+        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=1, seed=seed, shot_offset=lo)
+        reqs.append((lo, B, prm))
+    lbp.lbp_server_wait(srv, lbp.lbp_server_submit(srv, dec.code, reqs[0][2], reqs[0][1], hs[:reqs[0][1]],
+                                                   herr[:reqs[0][1]], hconv[:reqs[0][1]], hosd[:reqs[0][1]],
+                                                   hit[:reqs[0][1]]))
+    t0 = time.perf_counter()
+    tks = [lbp.lbp_server_submit(srv, dec.code, prm, B, hs[lo:lo + B], herr[lo:lo + B], hconv[lo:lo + B],
+                                 hosd[lo:lo + B], hit[lo:lo + B]) for lo, B, prm in reqs]
+    lats = [lbp.lbp_server_wait(srv, t) for t in tks]
+    tb = time.perf_counter() - t0
+    srv.close()
+    fb = evaluate.logical_failures(spec, true_d, herr.cuda(), hconv.cuda(), hosd.cuda())
+    ka, kb = int(fa.sum().item()), int(fb.sum().item())
+    only_a = int((fa & ~fb).sum().item())
+    only_b = int((fb & ~fa).sum().item())
+    dec.close()
+    return {
+        "workload": "rotated_d7_st7_p0.012", "shots": shots,
+        "plain_bp_osd_fp32_batched": {
+            "ler": ka / shots, "ler_ci95": evaluate.wilson(ka, shots), "shots_per_s": shots / ta,
+            "latency_ms": ta * 1e3, "osd_invoke_rate": float((ra.osd != 0).float().mean().item()),
+            "mean_iters": float(ra.iters.float().mean().item())},
+        "lottery_bp_osd_fp16_served": {
+            "ler": kb / shots, "ler_ci95": evaluate.wilson(kb, shots), "shots_per_s": shots / tb,
+            "request_shots": request, "p50_ms": float(np.quantile(lats, 0.5) * 1e3),
+            "p99_ms": float(np.quantile(lats, 0.99) * 1e3),
+            "osd_invoke_rate": float((hosd != 0).float().mean().item()),
+            "mean_iters": float(hit.float().mean().item())},
+        "ler_relative_difference": (kb - ka) / max(ka, 1), "mcnemar_discordant": [only_a, only_b],
+        "mcnemar_p": evaluate.mcnemar_p(only_a, only_b),
+    }
+
+
 def main():
     args = parse()
+    if args.serving_only:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"serving": run_serving(), "matched_ler": run_matched()}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

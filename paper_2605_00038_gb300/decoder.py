@@ -28,6 +28,7 @@ class DeviceResult:
 class Decoder:
     def __init__(self, h, priors, device: str | int = "cuda"):
         self.h = h
+        self.priors = priors
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
             self.code = lbp.lbp_load_code(h.m, h.n, h.row_ptr, h.col_idx, priors)
