@@ -360,6 +360,7 @@ def run_gpu(args):
     if not args.no_extras and rank == 0 and world == 1:
         line["serving"] = run_serving()
         line["matched_ler"] = run_matched()
+        line["precision"] = run_precision()
     if not args.no_extras and rank == 0 and world == 1:
         import oracle
         cores = os.cpu_count() or 1
@@ -383,8 +384,10 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     """Serving mix: Poisson arrivals of 1-4096-shot requests over ten resident
     codes (rotated surface space-time d = 5..17 with d rounds, BB 72/144/288
     code capacity) and five noise levels 1e-3..5e-3; Lottery BP + OSD-0,
-    I = 100, FP16 messages.  Capacity first (all requests queued at once), then
-    open-loop arrivals at 50 / 80 / 95 % of it."""
+    I = 100, INT8 messages.  Capacity first (all requests queued at once), then
+    open-loop arrivals at 50 / 80 / 95 % of it.  Messages are Int3.4 (INT8),
+    the format the paper's hardware uses; FP16 messages roughly double the
+    lottery's OSD invoke rate on these surface codes."""
     import torch
     from paper_2605_00038_gb300 import lbp
     from paper_2605_00038_gb300.decoder import Decoder
@@ -418,7 +421,7 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
         s.numpy()[:] = syn.view(np.int64)
         reqs.append(dict(ci=ci, pi=pi, B=B, syn=s, err=pin((B, (h.n + 63) // 64), torch.int64),
                          conv=pin(B, torch.uint8), osd=pin(B, torch.uint8), iters=pin(B, torch.int32),
-                         prm=dec.params(max_iter=100, lottery=1, osd=1, msg=1, seed=seed,
+                         prm=dec.params(max_iter=100, lottery=1, osd=1, msg=2, seed=seed,
                                         shot_offset=i << 16)))
     srv = lbp.lbp_server_create(8 << 30, 16)
 
@@ -479,7 +482,7 @@ def dec_priors(dec):
 def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     """Matched-LER head-to-head on identical shots of the rotated d=7 surface
     code, 7 noisy rounds, p = 0.012: (A) plain NMS BP + OSD-0, FP32 messages,
-    one batched lbp_decode; (B) Lottery BP + OSD-0, FP16 messages, served in
+    one batched lbp_decode; (B) Lottery BP + OSD-0, INT8 (Int3.4) messages, served in
     4096-shot requests through lbp_server.  Logical error rates with Wilson
     95% intervals and the paired McNemar test, throughput and p99 latency."""
     import torch
@@ -508,7 +511,7 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     torch.cuda.synchronize()
     ta = ev0.elapsed_time(ev1) / 1e3
     fa = evaluate.logical_failures(spec, true_d, ra.err, ra.converged, ra.osd)
-    # Arm B: Lottery BP + OSD-0, FP16, served.
+    # Arm B: Lottery BP + OSD-0, INT8, served.
     pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
     hs = pin(syn.shape, torch.int64)
     hs.numpy()[:] = syn.view(np.int64)
@@ -518,7 +521,7 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     reqs = []
     for lo in range(0, shots, request):
         B = min(request, shots - lo)
-        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=1, seed=seed, shot_offset=lo)
+        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=2, seed=seed, shot_offset=lo)
         reqs.append((lo, B, prm))
     lbp.lbp_server_wait(srv, lbp.lbp_server_submit(srv, dec.code, reqs[0][2], reqs[0][1], hs[:reqs[0][1]],
                                                    herr[:reqs[0][1]], hconv[:reqs[0][1]], hosd[:reqs[0][1]],
@@ -540,7 +543,7 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
             "ler": ka / shots, "ler_ci95": evaluate.wilson(ka, shots), "shots_per_s": shots / ta,
             "latency_ms": ta * 1e3, "osd_invoke_rate": float((ra.osd != 0).float().mean().item()),
             "mean_iters": float(ra.iters.float().mean().item())},
-        "lottery_bp_osd_fp16_served": {
+        "lottery_bp_osd_int8_served": {
             "ler": kb / shots, "ler_ci95": evaluate.wilson(kb, shots), "shots_per_s": shots / tb,
             "request_shots": request, "p50_ms": float(np.quantile(lats, 0.5) * 1e3),
             "p99_ms": float(np.quantile(lats, 0.99) * 1e3),
@@ -551,12 +554,84 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     }
 
 
+def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int = 31):
+    """Precision gap: Lottery BP + OSD-0 on the rotated d=7 surface code, 7
+    noisy rounds, p = 0.012, with FP32 / FP16 / INT8 messages (2^20 shots
+    each, identical shots), against the FP64 oracle on the first 2^15 shots.
+    Then throughput of the d=25, 25-round code (7,800 x 23,113) per precision."""
+    import torch
+    import oracle
+    from paper_2605_00038_gb300 import evaluate
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+    from paper_2605_00038_gb300.inputs.codes import rotated_surface, spacetime, spacetime_priors
+
+    d, p = 7, 0.012
+    hz, _ = rotated_surface(d)
+    h = spacetime(hz, d)
+    pri = spacetime_priors(hz, d, p, p)
+    e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
+    spec = evaluate.surface_spec(d, d, h.n)
+    true_d = torch.from_numpy(e.view(np.int64)).cuda()
+    sd = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec = Decoder(h, pri)
+    cores = os.cpu_count() or 1
+    r = oracle.decode(h, pri, sampler.unpack(syn[:oracle_shots], h.m),
+                      oracle.OracleParams(max_iter=100, lottery=True, osd=True, prec=oracle.PREC_F64,
+                                          seed=seed), nthreads=cores)
+    fo = evaluate.logical_failures(spec, true_d[:oracle_shots].cpu(),
+                                   torch.from_numpy(sampler.pack(r.err).view(np.int64)),
+                                   torch.from_numpy(r.converged), torch.from_numpy(r.osd_used)).numpy()
+    out = {"workload": "rotated_d7_st7_p0.012", "shots": shots, "oracle_shots": oracle_shots,
+           "fp64_oracle": {"ler_subset": float(fo.mean()), "osd_invoke_rate_subset": float(r.osd_used.mean())}}
+    for msg, name in ((0, "fp32"), (1, "fp16"), (2, "int8")):
+        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=msg, seed=seed)
+        res = dec.decode(sd, prm)
+        torch.cuda.synchronize()
+        f = evaluate.logical_failures(spec, true_d, res.err, res.converged, res.osd).cpu().numpy()
+        fs = f[:oracle_shots]
+        k = int(f.sum())
+        out[name] = {"ler": k / shots, "ler_ci95": evaluate.wilson(k, shots),
+                     "ler_subset": float(fs.mean()),
+                     "gap_vs_fp64_subset": float(fs.mean() - fo.mean()),
+                     "mcnemar_p_vs_fp64": evaluate.mcnemar_p(int((fs & ~fo).sum()), int((fo & ~fs).sum())),
+                     "osd_invoke_rate": float((res.osd != 0).float().mean().item()),
+                     "mean_iters": float(res.iters.float().mean().item())}
+    dec.close()
+    # d=25 throughput per precision (no OSD, as configured).
+    c5 = {}
+    for msg, name in ((0, "fp32"), (1, "fp16"), (2, "int8")):
+        w = workloads.c5_d25_spacetime(msg=msg, shots=1 << 17)
+        _, s5 = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+        d5 = Decoder(w.h, w.priors)
+        prm = d5.params(**w.decoder)
+        s5d = torch.from_numpy(s5.view(np.int64)).cuda()
+        d5.tune(s5d[:16384].contiguous(), prm)
+        d5.decode(s5d, prm)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        res = d5.decode(s5d, prm)
+        a1.record()
+        torch.cuda.synchronize()
+        t = a0.elapsed_time(a1) / 1e3
+        it = float(res.iters.float().mean().item())
+        bpm = {0: 4, 1: 2, 2: 1}[msg]
+        c5[name] = {"shots_per_s": w.shots / t, "mean_iters": it,
+                    "unconverged": float((res.converged == 0).float().mean().item()),
+                    "state_gbs": w.shots * it * 2 * (w.h.nnz * bpm + 4 * w.h.n) / t / 1e9}
+        d5.close()
+    out["d25_throughput"] = c5
+    return out
+
+
 def main():
     args = parse()
     if args.serving_only:
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps({"serving": run_serving(), "matched_ler": run_matched()}), flush=True)
+        print(json.dumps({"serving": run_serving(), "matched_ler": run_matched(),
+                          "precision": run_precision()}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
