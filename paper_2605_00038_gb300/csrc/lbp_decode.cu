@@ -242,8 +242,10 @@ WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, con
     size_t off = 0;
     w.counters = off; off = align256(off + 256);
     if (bp && !bp->state_smem) {
+        // Sized for every launch shape (at most 1024 / 256 groups per CTA, one
+        // CTA per SM), so lbp_tune's candidates and any tuned shape fit.
         w.gstate = off;
-        off = align256(off + static_cast<size_t>(bp->grid) * bp->groups * bp->state_bytes);
+        off = align256(off + static_cast<size_t>(c->sm_count) * 4 * bp->state_bytes);
     }
     if (prm->osd) {
         w.osd_list = off; off = align256(off + 4ull * num_shots);
@@ -579,6 +581,7 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
         float ms = 0.0f, warm = 0.0f;
         rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
                                        iters_out, nullptr, workspace, workspace_bytes, s, S, G, &warm);
+        if (rc == LBP_ENOMEM || rc == LBP_ENOSYS) continue;   // candidate does not fit: skip it
         if (rc) return rc;
         rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
                                        iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms);
@@ -588,6 +591,12 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     if (best_G > 0) {
         code->tuned_G[mi] = best_G;
         code->tuned_groups[mi] = best_S;
+    } else {
+        // No candidate ran: decode once with the default shape so the outputs
+        // are lbp_decode's (or report why it cannot run).
+        rc = lbp::decode_device(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                iters_out, nullptr, workspace, workspace_bytes, s);
+        if (rc) return rc;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
     return LBP_OK;
