@@ -112,6 +112,24 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_offsets(rank: int, shots: int, n_batches: int = N_BATCHES):
+    """Global index of shot 0 of each input batch of `rank`: ranks decode
+    disjoint shot ranges, keyed by global index (weak scaling)."""
+    return [(rank * n_batches + k) * shots for k in range(n_batches)]
+
+
+def job_value(world: int, shots: int, steps: int, elapsed_ms_per_rank, dist=None):
+    """(max elapsed ms over ranks, whole-job shots/s).  `elapsed_ms_per_rank`
+    is this rank's time; with a process group the max is all-reduced."""
+    import torch
+    t = torch.tensor([float(elapsed_ms_per_rank)],
+                     device="cuda" if (dist is not None and dist.get_backend() == "nccl") else "cpu")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, world * shots * steps / (max_ms / 1e3)
+
+
 def workload(shots):
     from paper_2605_00038_gb300.inputs import workloads
     return workloads.c2_d11_spacetime(shots=shots, osd=1)
@@ -227,8 +245,7 @@ def run_gpu(args):
 
     # Inputs: N_BATCHES distinct batches per rank, resident on the device.
     syn_h, err_h, syn_d, prms = [], [], [], []
-    for k in range(N_BATCHES):
-        off = (rank * N_BATCHES + k) * B
+    for k, off in enumerate(rank_offsets(rank, B)):
         e, s = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=B, shot_offset=off)
         err_h.append(e)
         syn_h.append(s)
@@ -269,11 +286,7 @@ def run_gpu(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     bp_ms, bp_n, osd_ms, osd_n = lbp.lbp_timing_read()
     lbp.lbp_timing_enable(False)
-    t = torch.tensor([elapsed_ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * B * args.steps / (max_ms / 1e3)
+    max_ms, value = job_value(world, B, args.steps, elapsed_ms, dist)
 
     # Work actually done in the timed steps (iterations, OSD invocations).
     iters_total = 0
@@ -348,10 +361,8 @@ def run_gpu(args):
             hstep(k)
         e1.record(stream)
         barrier()
-        t = torch.tensor([e0.elapsed_time(e1)], device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * B * args.steps / (float(t.item()) / 1e3), "unit": UNIT,
+        _, e2e_value = job_value(world, B, args.steps, e0.elapsed_time(e1), dist)
+        line["e2e"] = {"value": e2e_value, "unit": UNIT,
                        "h2d_bytes_per_step": B * wm * 8,
                        "d2h_bytes_per_step": B * (wn * 8 + 1 + 1 + 4)}
 
