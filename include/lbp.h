@@ -51,6 +51,19 @@ extern "C" {
 #define LBP_MSG_F16 1          /* IEEE binary16, round to nearest even */
 #define LBP_MSG_I8  2          /* Int3.4 fixed point: q = clamp(rne(16 x), -127, 127), value q/16 */
 
+/* Lottery policy (Sec. III-B and Table I): the proposed rule of Alg. 3 and
+ * the four baselines it is compared with.  "Worst CN": the unsatisfied check
+ * with the most columns currently estimated in error (lowest row on ties);
+ * "random CN": the k-th unsatisfied check, k = floor(u N / 2^32) (Alg. 3);
+ * "unreliable VN": least |lambda| among the check's columns (lowest column on
+ * ties); "random VN": column floor(u2 deg / 2^32) of the check, u2 the high 32
+ * bits of the same 64-bit draw whose low 32 bits are u. */
+#define LBP_LOTTERY_PROPOSED          0  /* random CN, most unsatisfied checks, then least |lambda| */
+#define LBP_LOTTERY_WORST_UNRELIABLE  1
+#define LBP_LOTTERY_WORST_RANDOM      2
+#define LBP_LOTTERY_RANDOM_UNRELIABLE 3
+#define LBP_LOTTERY_RANDOM_RANDOM     4
+
 /* Normalisation factor of the min-sum CN update. */
 #define LBP_SCALE_CONST    0   /* scale_const at every iteration */
 #define LBP_SCALE_ADAPTIVE 1   /* 1 - 2^-(i+1) at iteration i (Alg. 1) */
@@ -65,7 +78,7 @@ typedef struct {
     int32_t  lottery_skip;  /* first iteration index (0-based) at which it may run; 6 in Sec. III-B */
     int32_t  osd;           /* 1: OSD-0 (Alg. 2) on shots BP did not converge on */
     int32_t  msg;           /* LBP_MSG_* */
-    int32_t  reserved;      /* must be 0 */
+    int32_t  lottery_policy;/* LBP_LOTTERY_*: which check and column the lottery picks */
     uint64_t seed;          /* key of the lottery's random draws */
     uint64_t shot_offset;   /* global index of shot 0 of this call: the draws of shot b
                                depend only on (seed, shot_offset + b), never on batching */

@@ -35,7 +35,8 @@
  *   s_hat(-1) = 0; it runs for lottery_skip <= i < I-1;
  *   RandomSelect: u = low 32 bits of SplitMix64 at counter (g << 24) + i for
  *   global shot index g, k = floor(u * N / 2^32), c* = k-th unsatisfied
- *   check in ascending row order;
+ *   check in ascending row order (a random column, for the baseline policies,
+ *   uses the high 32 bits of the same output);
  *   ties: most unsatisfied checks, then least |lambda|, then lowest column;
  *   OSD sorts signed lambda ascending, ties by column index; if s is not in
  *   the column space, the BP estimate is kept and a flag is raised;
@@ -63,7 +64,9 @@ typedef struct {
     int32_t prec;
     int32_t early_exit;   /* 1: Alg. 1 early termination; 0: exactly max_iter iterations */
     int32_t rule;         /* 0: normalised min-sum (Alg. 1); 1: sum-product tanh rule */
-    int32_t pad_;
+    int32_t policy;       /* lottery policy, Sec. III-B: 0 proposed (Alg. 3), 1 worst CN +
+                             unreliable VN, 2 worst CN + random VN, 3 random CN + unreliable VN,
+                             4 random CN + random VN */
     uint64_t seed;
     uint64_t shot_offset;
 } oracle_params;
@@ -161,26 +164,48 @@ static void graph_free(graph_t *g) {
 
 /* ------------------------------------------------- Alg. 3: lottery --- */
 
-/* Given the unsatisfied set U (bytes per check) and lambda, pick c* as the
- * k-th member of U with k = floor(u * |U| / 2^32), then v* in V(c*): most
- * members of C(v) in U, then least |lambda_v|, then lowest index.
+/* Lottery selection.  U: unsatisfied set (bytes per check); lam: current
+ * posteriors; r: one 64-bit draw, whose low 32 bits pick the random check and
+ * whose high 32 bits pick the random column (policies 2 and 4).
+ * Policy 0 (Alg. 3): c* = the k-th member of U, k = floor(u |U| / 2^32); v* in
+ * V(c*) with the most members of C(v) in U, then least |lambda_v|, then lowest
+ * column.  Baselines of Sec. III-B: "worst CN" = the member of U with the most
+ * columns estimated in error (lambda <= 0 now), lowest row on ties; "random
+ * CN" = as in policy 0; "unreliable VN" = least |lambda| in V(c*), lowest
+ * column on ties; "random VN" = column number floor(u2 deg(c*) / 2^32) of c*.
  * Returns v*, or -1 when U is empty. */
 static int lottery_select(const graph_t *g, const uint8_t *U, const double *lam,
-                          uint32_t u, int *cstar_out) {
+                          uint64_t r, int policy, int *cstar_out) {
     int N = 0;
     for (int c = 0; c < g->m; ++c) N += U[c] ? 1 : 0;
     if (N == 0) return -1;
-    int k = (int)(((uint64_t)u * (uint64_t)N) >> 32);      /* floor(r N), r = u / 2^32 */
+    const uint32_t u = (uint32_t)r, u2 = (uint32_t)(r >> 32);
+    const int worst_cn = policy == 1 || policy == 2;
+    const int random_vn = policy == 2 || policy == 4;
     int cstar = -1;
-    for (int c = 0, seen = 0; c < g->m; ++c)
-        if (U[c]) { if (seen == k) { cstar = c; break; } seen++; }
+    if (worst_cn) {
+        int best_err = -1;
+        for (int c = 0; c < g->m; ++c) {
+            if (!U[c]) continue;
+            int ne = 0;                                  /* columns of c estimated in error */
+            for (int e = g->row_ptr[c]; e < g->row_ptr[c + 1]; ++e) ne += lam[g->col_idx[e]] <= 0.0 ? 1 : 0;
+            if (ne > best_err) { best_err = ne; cstar = c; }
+        }
+    } else {
+        int k = (int)(((uint64_t)u * (uint64_t)N) >> 32);  /* floor(r N), r = u / 2^32 */
+        for (int c = 0, seen = 0; c < g->m; ++c)
+            if (U[c]) { if (seen == k) { cstar = c; break; } seen++; }
+    }
     if (cstar_out) *cstar_out = cstar;
+    const int e0 = g->row_ptr[cstar], deg = g->row_ptr[cstar + 1] - e0;
+    if (random_vn) return g->col_idx[e0 + (int)(((uint64_t)u2 * (uint64_t)deg) >> 32)];
     int best = -1, best_cnt = -1;
     double best_abs = 0.0;
-    for (int e = g->row_ptr[cstar]; e < g->row_ptr[cstar + 1]; ++e) {
+    for (int e = e0; e < e0 + deg; ++e) {
         int v = g->col_idx[e];
-        int cnt = 0;                                     /* |C(v) ∩ U| */
-        for (int k2 = g->col_ptr[v]; k2 < g->col_ptr[v + 1]; ++k2) cnt += U[g->csc_row[k2]] ? 1 : 0;
+        int cnt = 0;                                     /* |C(v) ∩ U|, policy 0 only */
+        if (policy == 0)
+            for (int k2 = g->col_ptr[v]; k2 < g->col_ptr[v + 1]; ++k2) cnt += U[g->csc_row[k2]] ? 1 : 0;
         double a = fabs(lam[v]);
         if (cnt > best_cnt || (cnt == best_cnt && (a < best_abs || (a == best_abs && v < best)))) {
             best = v; best_cnt = cnt; best_abs = a;
@@ -190,13 +215,14 @@ static int lottery_select(const graph_t *g, const uint8_t *U, const double *lam,
 }
 
 int oracle_lottery_select(int m, int n, const int32_t *row_ptr, const int32_t *col_idx,
-                          const uint8_t *U, const double *lam, uint32_t u,
+                          const uint8_t *U, const double *lam, uint64_t r, int policy,
                           int32_t *cstar, int32_t *vstar) {
+    if (policy < 0 || policy > 4) return -1;
     graph_t g;
     int rc = graph_init(&g, m, n, row_ptr, col_idx);
     if (rc) return rc;
     int cs = -1;
-    int v = lottery_select(&g, U, lam, u, &cs);
+    int v = lottery_select(&g, U, lam, r, policy, &cs);
     if (cstar) *cstar = cs;
     if (vstar) *vstar = v;
     graph_free(&g);
@@ -423,8 +449,8 @@ static void decode_one(shot_ws *w, uint64_t gshot, const uint8_t *s, uint8_t *e_
             if (prm->lottery && i >= prm->lottery_skip && i < I - 1) {
                 for (int c = 0; c < m; ++c) w->U[c] = (uint8_t)(w->shat_prev[c] ^ (s[c] & 1));
                 uint64_t ctr = (gshot << 24) + (uint64_t)i;
-                uint32_t u = (uint32_t)oracle_splitmix64_at(prm->seed, ctr);
-                int vstar = lottery_select(g, w->U, w->lam, u, NULL);
+                uint64_t r = oracle_splitmix64_at(prm->seed, ctr);
+                int vstar = lottery_select(g, w->U, w->lam, r, prm->policy, NULL);
                 if (vstar >= 0) w->lam[vstar] = -w->lam[vstar];
             }
         }
@@ -499,6 +525,7 @@ int oracle_decode(int m, int n, const int32_t *row_ptr, const int32_t *col_idx,
     if (prm->prec < PREC_F64 || prm->prec > PREC_I8) return -1;
     if (prm->rule == RULE_SUM_PRODUCT && prm->prec != PREC_F64) return -1;
     if (prm->lottery_skip < 0 || prm->max_iter >= (1 << 24)) return -1;
+    if (prm->policy < 0 || prm->policy > 4) return -1;
     graph_t g;
     int rc = graph_init(&g, m, n, row_ptr, col_idx);
     if (rc) return rc;

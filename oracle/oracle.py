@@ -39,7 +39,7 @@ class _Params(ctypes.Structure):
                 ("scale_const", ctypes.c_double), ("lottery", ctypes.c_int32),
                 ("lottery_skip", ctypes.c_int32), ("osd", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("early_exit", ctypes.c_int32),
-                ("rule", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("rule", ctypes.c_int32), ("policy", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("shot_offset", ctypes.c_uint64)]
 
 
@@ -54,13 +54,14 @@ class OracleParams:
     prec: int = PREC_F64
     early_exit: bool = True
     rule: int = RULE_MIN_SUM
+    policy: int = 0              # lottery policy: 0 proposed, 1..4 baselines (Sec. III-B)
     seed: int = 0
     shot_offset: int = 0
 
     def _c(self) -> _Params:
         return _Params(self.max_iter, self.scale_mode, self.scale_const, int(self.lottery),
                        self.lottery_skip, int(self.osd), self.prec, int(self.early_exit),
-                       self.rule, 0, self.seed, self.shot_offset)
+                       self.rule, self.policy, self.seed, self.shot_offset)
 
 
 _L = None
@@ -81,7 +82,7 @@ def _lib():
         lib.oracle_osd0.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.oracle_lottery_select.restype = ctypes.c_int
         lib.oracle_lottery_select.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
-                                              ctypes.c_uint32, vp, vp]
+                                              ctypes.c_uint64, ctypes.c_int, vp, vp]
         lib.oracle_splitmix64_at.restype = ctypes.c_uint64
         lib.oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.oracle_round_f16.restype = ctypes.c_double
@@ -152,14 +153,15 @@ def osd0(h, llr, s):
     return (e if rc == 0 else None), rank.value, basis[:rank.value].copy()
 
 
-def lottery_select(h, U, llr, u: int):
-    """Alg. 3 selection for one shot: returns (c*, v*)."""
+def lottery_select(h, U, llr, u: int, policy: int = 0):
+    """Lottery selection for one shot: returns (c*, v*).  u is the 64-bit draw
+    (low 32 bits: random check; high 32 bits: random column)."""
     rp, ci = _csr(h)
     Ub = np.ascontiguousarray(U, dtype=np.uint8)
     lam = np.ascontiguousarray(llr, dtype=np.float64)
     cs = ctypes.c_int32(-1)
     vs = ctypes.c_int32(-1)
-    rc = _lib().oracle_lottery_select(h.m, h.n, _ptr(rp), _ptr(ci), _ptr(Ub), _ptr(lam), u,
+    rc = _lib().oracle_lottery_select(h.m, h.n, _ptr(rp), _ptr(ci), _ptr(Ub), _ptr(lam), u, policy,
                                       ctypes.addressof(cs), ctypes.addressof(vs))
     if rc != 0:
         raise ValueError("oracle_lottery_select rejected its input (code %d)" % rc)

@@ -44,7 +44,7 @@ struct BpEllArgs {
     int32_t m, n;
     int32_t max_iter, scale_mode;
     float scale_const;
-    int32_t lottery, lottery_skip, osd;
+    int32_t lottery, lottery_skip, osd, policy;
     uint64_t seed, shot_offset;
     int64_t num_shots;
     const uint64_t *syn;
@@ -225,13 +225,10 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 sh_nxt[w] = 0u;
             }
             if (!group_sync_or<G>(bar, mism)) { converged = true; break; }
-            // ---- lottery (Alg. 3) ---------------------------------------------
+            // ---- lottery (Alg. 3, or a baseline policy of Sec. III-B) ---------
             if (a.lottery && it >= a.lottery_skip && it < I - 1) {
                 if (t < 32) {
                     const uint32_t *sp = shat + prev * W32;
-                    // N = |U| and c* = member k of U, from per-word prefix counts.
-                    uint32_t base = 0;
-                    int cstar = -1;
                     uint32_t N = 0;
                     for (int w0 = 0; w0 < W32; w0 += 32) {
                         const int w = w0 + lane;
@@ -243,58 +240,99 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                     }
                     if (N > 0) {
                         const uint64_t g = a.shot_offset + b;
-                        const uint32_t u = static_cast<uint32_t>(
-                            splitmix64_at(a.seed, (g << 24) + static_cast<uint64_t>(it)));
-                        const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(u) * N) >> 32);
-                        for (int w0 = 0; w0 < W32 && cstar < 0; w0 += 32) {
-                            const int w = w0 + lane;
-                            uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
-                            const uint32_t pc = __popc(word);
-                            uint32_t incl = pc;
-                            #pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                                if (lane >= o) incl += y;
-                            }
-                            const uint32_t excl = incl - pc;
-                            const bool mine = (k >= base + excl) && (k < base + incl);
-                            const unsigned own = __ballot_sync(0xffffffffu, mine);
-                            if (own) {
-                                int pick = 0;
-                                if (mine) {
-                                    uint32_t rr = k - base - excl;
-                                    while (rr--) word &= word - 1u;
-                                    pick = w * 32 + (__ffs(word) - 1);
+                        const uint64_t r64 = splitmix64_at(a.seed, (g << 24) + static_cast<uint64_t>(it));
+                        const uint32_t u = static_cast<uint32_t>(r64), u2 = static_cast<uint32_t>(r64 >> 32);
+                        int cstar = -1;
+                        if (a.policy == LBP_LOTTERY_WORST_UNRELIABLE || a.policy == LBP_LOTTERY_WORST_RANDOM) {
+                            // Worst CN: most columns estimated in error, lowest row on ties.
+                            int bn = -1, bcr = 0x7fffffff;
+                            for (int w = lane; w < W32; w += 32) {
+                                uint32_t word = sp[w] ^ s_w[w];
+                                while (word) {
+                                    const int c = w * 32 + __ffs(word) - 1;
+                                    word &= word - 1u;
+                                    int ne = 0;
+                                    #pragma unroll
+                                    for (int k = 0; k < DC; ++k) {
+                                        const int v = cidx[k * Mp + c];
+                                        ne += (v < n && lam[v] <= 0.0f) ? 1 : 0;
+                                    }
+                                    if (ne > bn || (ne == bn && c < bcr)) { bn = ne; bcr = c; }
                                 }
-                                cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
                             }
-                            base += __shfl_sync(0xffffffffu, incl, 31);
+                            #pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                const int on = __shfl_xor_sync(0xffffffffu, bn, o);
+                                const int oc = __shfl_xor_sync(0xffffffffu, bcr, o);
+                                if (on > bn || (on == bn && oc < bcr)) { bn = on; bcr = oc; }
+                            }
+                            cstar = bcr;
+                        } else {
+                            // Random CN: member k = floor(u N / 2^32) of U, ascending rows.
+                            const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(u) * N) >> 32);
+                            uint32_t base = 0;
+                            for (int w0 = 0; w0 < W32 && cstar < 0; w0 += 32) {
+                                const int w = w0 + lane;
+                                uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
+                                const uint32_t pc = __popc(word);
+                                uint32_t incl = pc;
+                                #pragma unroll
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                                    if (lane >= o) incl += y;
+                                }
+                                const uint32_t excl = incl - pc;
+                                const bool mine = (k >= base + excl) && (k < base + incl);
+                                const unsigned own = __ballot_sync(0xffffffffu, mine);
+                                if (own) {
+                                    int pick = 0;
+                                    if (mine) {
+                                        uint32_t rr = k - base - excl;
+                                        while (rr--) word &= word - 1u;
+                                        pick = w * 32 + (__ffs(word) - 1);
+                                    }
+                                    cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
+                                }
+                                base += __shfl_sync(0xffffffffu, incl, 31);
+                            }
                         }
-                        // v*: most unsatisfied checks, least |lambda|, lowest column.
                         int bc = -1, bv = 0x7fffffff;
                         float ba = 0.0f;
-                        if (lane < DC) {
-                            const int v = cidx[lane * Mp + cstar];
-                            if (v < n) {
-                                bv = v;
-                                bc = 0;
-                                #pragma unroll
-                                for (int kk = 0; kk < DV; ++kk) {
-                                    const unsigned o = vent[kk * Np + v];
-                                    const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
-                                    if (r < static_cast<unsigned>(m))
-                                        bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
+                        if (a.policy == LBP_LOTTERY_WORST_RANDOM || a.policy == LBP_LOTTERY_RANDOM_RANDOM) {
+                            // Random VN: column floor(u2 deg / 2^32) of c*.
+                            const int vl = lane < DC ? cidx[lane * Mp + cstar] : n;
+                            const int deg = __popc(__ballot_sync(0xffffffffu, lane < DC && vl < n));
+                            const int kk = static_cast<int>((static_cast<uint64_t>(u2) * static_cast<uint32_t>(deg)) >> 32);
+                            bv = cidx[kk * Mp + cstar];
+                            bc = 0;
+                        } else {
+                            // Unreliable VN (the proposed rule first prefers the column
+                            // with the most unsatisfied checks), then lowest column.
+                            if (lane < DC) {
+                                const int v = cidx[lane * Mp + cstar];
+                                if (v < n) {
+                                    bv = v;
+                                    bc = 0;
+                                    if (a.policy == LBP_LOTTERY_PROPOSED) {
+                                        #pragma unroll
+                                        for (int kk = 0; kk < DV; ++kk) {
+                                            const unsigned o = vent[kk * Np + v];
+                                            const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
+                                            if (r < static_cast<unsigned>(m))
+                                                bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
+                                        }
+                                    }
+                                    ba = fabsf(lam[v]);
                                 }
-                                ba = fabsf(lam[v]);
                             }
-                        }
-                        #pragma unroll
-                        for (int o = 4; o > 0; o >>= 1) {
-                            const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-                            const float oa = __shfl_xor_sync(0xffffffffu, ba, o);
-                            const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                            const bool better = oc > bc || (oc == bc && (oa < ba || (oa == ba && ov < bv)));
-                            if (better) { bc = oc; ba = oa; bv = ov; }
+                            #pragma unroll
+                            for (int o = 4; o > 0; o >>= 1) {
+                                const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                                const float oa = __shfl_xor_sync(0xffffffffu, ba, o);
+                                const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                                const bool better = oc > bc || (oc == bc && (oa < ba || (oa == ba && ov < bv)));
+                                if (better) { bc = oc; ba = oa; bv = ov; }
+                            }
                         }
                         if (lane == 0 && bc >= 0) lam[bv] = -lam[bv];
                     }

@@ -75,7 +75,7 @@ int validate_params(const lbp_params *p) {
     if (p->lottery_skip < 0) return LBP_EINVAL;
     if (p->osd != 0 && p->osd != 1) return LBP_EINVAL;
     if (p->msg != LBP_MSG_F32 && p->msg != LBP_MSG_F16 && p->msg != LBP_MSG_I8) return LBP_EINVAL;
-    if (p->reserved != 0) return LBP_EINVAL;
+    if (p->lottery_policy < LBP_LOTTERY_PROPOSED || p->lottery_policy > LBP_LOTTERY_RANDOM_RANDOM) return LBP_EINVAL;
     return LBP_OK;
 }
 
@@ -338,6 +338,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     a.m = c->m; a.n = c->n;
     a.max_iter = prm->max_iter; a.scale_mode = prm->scale_mode; a.scale_const = prm->scale_const;
     a.lottery = prm->lottery; a.lottery_skip = prm->lottery_skip; a.osd = prm->osd;
+    a.policy = prm->lottery_policy;
     a.seed = prm->seed; a.shot_offset = prm->shot_offset;
     a.num_shots = B;
     a.syn = syn; a.err = err; a.conv = conv; a.osd_out = osd_out; a.iters = iters; a.llr = llr;
@@ -364,6 +365,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.m = a.m; e.n = a.n; e.max_iter = a.max_iter; e.scale_mode = a.scale_mode;
         e.scale_const = a.scale_const; e.lottery = a.lottery; e.lottery_skip = a.lottery_skip;
         e.osd = a.osd; e.seed = a.seed; e.shot_offset = a.shot_offset; e.num_shots = a.num_shots;
+        e.policy = a.policy;
         e.syn = a.syn; e.err = a.err; e.conv = a.conv; e.osd_out = a.osd_out; e.iters = a.iters;
         e.llr = a.llr; e.counters = a.counters; e.osd_list = a.osd_list; e.osd_llr = a.osd_llr;
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;

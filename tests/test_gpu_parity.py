@@ -57,6 +57,7 @@ def oracle_decode(h, pri, syn, prec=None, **kw):
                             scale_const=kw.get("scale_const", 0.625),
                             lottery=bool(kw.get("lottery", 1)), lottery_skip=kw.get("lottery_skip", 6),
                             osd=bool(kw.get("osd", 0)), prec=PREC[msg] if prec is None else prec,
+                            policy=kw.get("lottery_policy", 0),
                             seed=kw.get("seed", 0), shot_offset=kw.get("shot_offset", 0))
     return oracle.decode(h, pri, sampler.unpack(syn, h.m), p, want_llr=True)
 
@@ -131,6 +132,26 @@ def test_c5_d25_spacetime_precisions(msg):
     _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
     kw = dict(w.decoder, seed=8)
     assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
+
+
+@pytest.mark.parametrize("policy", [1, 2, 3, 4])
+def test_lottery_baseline_policies(policy):
+    """The four baseline sign-flip policies of Sec. III-B, on the bounded-degree
+    kernel (d=7 space-time code, BB72) and the general kernel (high degree)."""
+    hz, _ = rotated_surface(7)
+    st = spacetime(hz, 7)
+    cases = [(st, spacetime_priors(hz, 7, 0.008, 0.008))]
+    hx, _ = bb_code("bb72")
+    cases.append((hx, np.full(hx.n, 0.05)))
+    rng = np.random.default_rng(9)
+    rows = [sorted(rng.choice(150, size=int(rng.integers(2, 13)), replace=False).tolist())
+            for _ in range(60)]
+    hh = SparseH.from_rows(rows, 150)
+    cases.append((hh, np.full(150, 0.03)))
+    for h, pri in cases:
+        _, syn = sampler.sample(h, pri, seed=41, num_shots=1500)
+        kw = dict(max_iter=60, lottery=1, lottery_skip=3, lottery_policy=policy, osd=1, seed=2)
+        assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
 
 
 def test_osd_bit_exact_on_gpu_llrs():

@@ -186,6 +186,30 @@ def test_lottery_prefers_most_unsatisfied_then_least_reliable_then_lowest():
     assert oracle.lottery_select(h, np.zeros(4, np.uint8), lam, 0) == (-1, -1)
 
 
+def test_lottery_baseline_policies():
+    """Sec. III-B baselines.  c0 = {0, 1, 2}, c1 = {2, 3, 4}, c2 = {4, 5}."""
+    h = _H([[0, 1, 2], [2, 3, 4], [4, 5]], 6)
+    U = np.array([1, 1, 1], dtype=np.uint8)
+    lam = np.array([0.5, -0.1, 0.3, -0.2, -0.4, 2.0])   # in error: 1, 3, 4
+    # worst CN: c1 has 2 columns in error (3, 4), c0 and c2 one each
+    assert oracle.lottery_select(h, U, lam, 0, policy=1) == (1, 3)   # then least |lambda| in c1: |-0.2|
+    # worst CN, ties -> lowest row: make c0 also have 2 errors
+    lam2 = lam.copy()
+    lam2[0] = -0.05
+    assert oracle.lottery_select(h, U, lam2, 0, policy=1) == (0, 0)
+    # random VN: column floor(u2 deg / 2^32) of c*, u2 = high 32 bits
+    for u2, want in [(0, 2), (2 ** 32 - 1, 4), ((2 ** 32 + 2) // 3, 3)]:
+        assert oracle.lottery_select(h, U, lam, u2 << 32, policy=2) == (1, want)
+    # random CN (k-th member) with unreliable VN: no unsatisfied-count criterion
+    hh = _H([[0, 1, 2], [1, 2], [1, 3], [3, 4]], 5)
+    UU = np.array([1, 1, 1, 0], dtype=np.uint8)
+    ll = np.array([0.1, 5.0, 0.2, 1.0, 1.0])
+    assert oracle.lottery_select(hh, UU, ll, 0, policy=0) == (0, 1)  # proposed: count first
+    assert oracle.lottery_select(hh, UU, ll, 0, policy=3) == (0, 0)  # least |lambda| only
+    # random CN + random VN: member k of U, column floor(u2 deg / 2^32)
+    assert oracle.lottery_select(hh, UU, ll, (2 ** 31) << 32 | (2 ** 32 - 1), policy=4) == (2, 3)
+
+
 def test_fig4_plain_bp_deadlock():
     """Fig. 4b: on the [[13,1,3]] code with error {q2, q8, q9}, plain BP with
     a uniform prior settles on the ambiguous mix {q1, q9} (plus the easy q8),
