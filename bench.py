@@ -400,6 +400,7 @@ def run_gpu(args):
         line["serving"] = run_serving()
         line["matched_ler"] = run_matched()
         line["precision"] = run_precision()
+        line["lottery_design_space"] = run_policies()
     if not args.no_extras and rank == 0 and world == 1:
         import oracle
         cores = os.cpu_count() or 1
@@ -664,13 +665,56 @@ def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int =
     return out
 
 
+def run_policies(shots: int = 1 << 18, seed: int = 41):
+    """Lottery design space (Sec. III-B, Table I, Fig. 5) on the rotated d=9
+    surface code with 9 noisy rounds, p = 0.005, FP32, I = 100: logical error
+    rate of BP alone (unconverged shots count as failures) and OSD invoke
+    rate, for plain BP, the proposed policy and the four baselines (skip 6),
+    then the proposed policy's skip-iteration sweep."""
+    import torch
+    from paper_2605_00038_gb300 import evaluate
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler
+    from paper_2605_00038_gb300.inputs.codes import rotated_surface, spacetime, spacetime_priors
+
+    d, p = 9, 0.005
+    hz, _ = rotated_surface(d)
+    h = spacetime(hz, d)
+    pri = spacetime_priors(hz, d, p, p)
+    e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
+    spec = evaluate.surface_spec(d, d, h.n)
+    true_d = torch.from_numpy(e.view(np.int64)).cuda()
+    sd = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec = Decoder(h, pri)
+    names = {0: "proposed", 1: "worst_cn_unreliable_vn", 2: "worst_cn_random_vn",
+             3: "random_cn_unreliable_vn", 4: "random_cn_random_vn"}
+
+    def one(**kw):
+        r = dec.decode(sd, dec.params(max_iter=100, osd=0, msg=0, seed=seed, **kw))
+        torch.cuda.synchronize()
+        f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+        k = int(f.sum().item())
+        return {"ler_bp_only": k / shots, "ler_ci95": evaluate.wilson(k, shots),
+                "osd_invoke_rate": float((r.converged == 0).float().mean().item()),
+                "mean_iters": float(r.iters.float().mean().item())}
+
+    out = {"workload": "rotated_d9_st9_p0.005", "shots": shots, "plain_bp": one(lottery=0), "policies": {}}
+    for pol, name in names.items():
+        out["policies"][name] = one(lottery=1, lottery_skip=6, lottery_policy=pol)
+    out["skip_sweep_proposed"] = {str(s): one(lottery=1, lottery_skip=s, lottery_policy=0)
+                                  for s in (0, 2, 4, 6, 8, 12)}
+    dec.close()
+    return out
+
+
 def main():
     args = parse()
     if args.serving_only:
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"serving": run_serving(), "matched_ler": run_matched(),
-                          "precision": run_precision()}), flush=True)
+                          "precision": run_precision(), "lottery_design_space": run_policies()}),
+              flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
