@@ -662,6 +662,29 @@ def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int =
                     "state_gbs": w.shots * it * 2 * (w.h.nnz * bpm + 4 * w.h.n) / t / 1e9}
         d5.close()
     out["d25_throughput"] = c5
+    # d=27 in the form of Table II (unrotated code, cyclic boundary, 18,954 x
+    # 56,889): the paper's simulator ran out of GPU memory here.
+    from paper_2605_00038_gb300.inputs.codes import unrotated_surface
+    _, hz27 = unrotated_surface(27)
+    st27 = spacetime(hz27, 27, "cyclic")
+    pri27 = np.full(st27.n, 0.004)
+    d27 = Decoder(st27, pri27)
+    n27 = 1 << 13
+    _, s27 = sampler.sample(st27, pri27, seed=27, num_shots=n27)
+    s27d = torch.from_numpy(s27.view(np.int64)).cuda()
+    prm = d27.params(max_iter=100, lottery=1, osd=0, msg=0, seed=27)
+    d27.decode(s27d[:512].contiguous(), prm)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    res = d27.decode(s27d, prm)
+    a1.record()
+    torch.cuda.synchronize()
+    t = a0.elapsed_time(a1) / 1e3
+    out["d27_table2_fp32"] = {"shape": [st27.m, st27.n, st27.nnz], "shots": n27, "shots_per_s": n27 / t,
+                              "mean_iters": float(res.iters.float().mean().item()),
+                              "device_state_mb_per_shot": (6 * (st27.m + 3) * 4 + 4 * (st27.n + 3)) / 2 ** 20}
+    d27.close()
     return out
 
 

@@ -3,7 +3,8 @@
 // at most DV ones (every surface-code space-time matrix: DC = 6, DV = 2; BB
 // codes: DC = 6, DV = 3).
 //
-// Layout (all slot-major, uint16 indices):
+// Layout (all slot-major; uint16 indices, or uint32 for codes too large for
+// 16-bit message offsets, whose image is then read from global memory):
 //  * Check side: cidx[k][c] is the k-th column of check c (ascending), padded
 //    with column n, whose prior and posterior are +inf: a neutral element of
 //    the check update (positive sign, never the minimum).  beta[k][c], row
@@ -62,6 +63,20 @@ struct BpEllArgs {
     uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
 };
 
+// Index width of the ELL image: 16-bit (the image fits shared memory) or
+// 32-bit (large codes, read from global memory); P holds two indices.
+template <typename IdxT> struct Idx;
+template <> struct Idx<uint16_t> {
+    using P = uint32_t;
+    static __device__ __forceinline__ uint32_t lo(uint32_t p) { return p & 0xffffu; }
+    static __device__ __forceinline__ uint32_t hi(uint32_t p) { return p >> 16; }
+};
+template <> struct Idx<uint32_t> {
+    using P = uint2;
+    static __device__ __forceinline__ uint32_t lo(uint2 p) { return p.x; }
+    static __device__ __forceinline__ uint32_t hi(uint2 p) { return p.y; }
+};
+
 // Exclusive minima and signed outputs of one check (DC slots).
 template <typename MsgT, int DC>
 __device__ __forceinline__ void check_update(const float (&al)[DC], uint32_t sbit, float f,
@@ -87,10 +102,12 @@ __device__ __forceinline__ void check_update(const float (&al)[DC], uint32_t sbi
     }
 }
 
-template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem>
+template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename IdxT = uint16_t>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
+    static_assert(kGraphSmem == false || sizeof(IdxT) == 2, "32-bit images are read from global memory");
     using PairT = typename Pair<MsgT>::type;
+    using IP = typename Idx<IdxT>::P;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
@@ -102,10 +119,10 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     const int Mp = a.img.Mp, Np = a.img.Np, R = Mp + 2;
     const int mpairs = Mp >> 1, npairs = Np >> 1;
     const uint8_t *gbase = kGraphSmem ? smem : a.image;
-    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(gbase + a.img.off_cidx);
-    const uint32_t *cidx2 = reinterpret_cast<const uint32_t *>(cidx);
-    const uint16_t *vent = reinterpret_cast<const uint16_t *>(gbase + a.img.off_vent);
-    const uint32_t *vent2 = reinterpret_cast<const uint32_t *>(vent);
+    const IdxT *cidx = reinterpret_cast<const IdxT *>(gbase + a.img.off_cidx);
+    const IP *cidx2 = reinterpret_cast<const IP *>(cidx);
+    const IdxT *vent = reinterpret_cast<const IdxT *>(gbase + a.img.off_vent);
+    const IP *vent2 = reinterpret_cast<const IP *>(vent);
     const float *mu = reinterpret_cast<const float *>(gbase + a.img.off_mu);
     const float2 *mu2 = reinterpret_cast<const float2 *>(mu);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
@@ -168,17 +185,17 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 if (it == 0) {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
-                        const uint32_t cc = cidx2[k * mpairs + pr];
-                        al0[k] = mu[cc & 0xffffu];
-                        al1[k] = mu[cc >> 16];
+                        const IP cc = cidx2[k * mpairs + pr];
+                        al0[k] = mu[Idx<IdxT>::lo(cc)];
+                        al1[k] = mu[Idx<IdxT>::hi(cc)];
                     }
                 } else {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
-                        const uint32_t cc = cidx2[k * mpairs + pr];
+                        const IP cc = cidx2[k * mpairs + pr];
                         const PairT bb = beta2[((k * R) >> 1) + pr];
-                        al0[k] = __fsub_rn(lam[cc & 0xffffu], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
-                        al1[k] = __fsub_rn(lam[cc >> 16], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
+                        al0[k] = __fsub_rn(lam[Idx<IdxT>::lo(cc)], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
+                        al1[k] = __fsub_rn(lam[Idx<IdxT>::hi(cc)], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
                     }
                 }
                 const uint32_t sw = s_w[c >> 5];               // c even: c and c + 1 share a word
@@ -192,14 +209,14 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
             for (int q = t; q < npairs; q += G) {
-                uint32_t ent[DV];
+                IP ent[DV];
                 const float2 mm = mu2[q];
                 float acc0 = mm.x, acc1 = mm.y;
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
                     ent[k] = vent2[k * npairs + q];
-                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[ent[k] & 0xffffu]));
-                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[ent[k] >> 16]));
+                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[Idx<IdxT>::lo(ent[k])]));
+                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[Idx<IdxT>::hi(ent[k])]));
                 }
                 lam2[q] = make_float2(acc0, acc1);
                 if (acc0 <= 0.0f || acc1 <= 0.0f) {
@@ -208,7 +225,7 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                         #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             if ((h == 0 ? acc0 : acc1) <= 0.0f) {
-                                const unsigned o = h == 0 ? (ent[k] & 0xffffu) : (ent[k] >> 16);
+                                const unsigned o = h == 0 ? Idx<IdxT>::lo(ent[k]) : Idx<IdxT>::hi(ent[k]);
                                 const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
                                 if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
                             }

@@ -6,9 +6,9 @@
 
 namespace lbp {
 
-template <typename MsgT, int G, int DC, int DV, bool GS, bool SS>
+template <typename MsgT, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
 int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS>;
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, IdxT>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -32,6 +32,14 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
         }
     }
     // Large codes: graph in global memory; state in shared or global memory.
+    if (s.idx32) {
+        if (s.state_smem) {
+            if (s.G == 1024) return launch_ell_one<MsgT, 1024, DC, DV, false, true, uint32_t>(s, a, st);
+            return LBP_ENOSYS;
+        }
+        if (s.G == 512) return launch_ell_one<MsgT, 512, DC, DV, false, false, uint32_t>(s, a, st);
+        return LBP_ENOSYS;
+    }
     if (s.state_smem) {
         switch (s.G) {
             case 256: return launch_ell_one<MsgT, 256, DC, DV, false, true>(s, a, st);

@@ -37,6 +37,7 @@ struct EllImage {
     uint32_t off_cidx, off_vent, off_mu;
     int32_t DC, DV;
     int32_t Mp, Np;          // m and n rounded up to even (paired accesses)
+    int32_t idx_bytes;       // 2 (uint16 indices) or 4 (uint32, image read from global memory)
 };
 
 }  // namespace lbp

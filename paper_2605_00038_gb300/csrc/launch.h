@@ -11,7 +11,7 @@ namespace lbp {
 struct LaunchShape {
     int grid, groups, G;
     size_t smem;
-    bool graph_smem, state_smem;
+    bool graph_smem, state_smem, idx32;
 };
 
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);

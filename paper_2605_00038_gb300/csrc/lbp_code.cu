@@ -150,38 +150,46 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
     if (maxdeg <= 6 && maxcol <= 2) { ell_dc = 6; ell_dv = 2; }
     else if (maxdeg <= 6 && maxcol <= 3) { ell_dc = 6; ell_dv = 3; }
     const int32_t Mp = (m + 1) & ~1, Np = (n + 1) & ~1, R = Mp + 2;
-    if (rc == LBP_OK && maxdeg <= 8 && maxcol <= 4 && static_cast<int64_t>(ell_dc) * R < 65536 &&
-        n < 65535) {
+    // 16-bit indices when every message offset and column fits; otherwise
+    // 32-bit (the kernel recovers an offset's check by a multiply-high
+    // division, exact while DC * R^2 < 2^32).
+    const bool fits16 = static_cast<int64_t>(ell_dc) * R < 65536 && n < 65535;
+    const bool fits32 = static_cast<uint64_t>(ell_dc) * R * R < (1ull << 32);
+    if (rc == LBP_OK && maxdeg <= 8 && maxcol <= 4 && (fits16 || fits32)) {
         lbp::EllImage &e = c->ell;
         // Supported (DC, DV) shapes: (6, 2), (6, 3), (8, 4).
         e.DC = ell_dc;
         e.DV = ell_dv;
         e.Mp = Mp;
         e.Np = Np;
+        e.idx_bytes = fits16 ? 2 : 4;
+        const uint32_t ib = static_cast<uint32_t>(e.idx_bytes);
         uint32_t off = 0;
-        e.off_cidx = off; off = align16(off + 2u * e.DC * Mp);
-        e.off_vent = off; off = align16(off + 2u * e.DV * Np);
+        e.off_cidx = off; off = align16(off + ib * e.DC * Mp);
+        e.off_vent = off; off = align16(off + ib * e.DV * Np);
         e.off_mu = off;   off = align16(off + 4u * (Np + 2));
         e.bytes = off;
         std::vector<uint8_t> img(off, 0);
-        uint16_t *ci = reinterpret_cast<uint16_t *>(img.data() + e.off_cidx);
-        uint16_t *ve = reinterpret_cast<uint16_t *>(img.data() + e.off_vent);
+        auto put = [&](uint32_t base, size_t i, uint32_t v) {
+            if (ib == 2) reinterpret_cast<uint16_t *>(img.data() + base)[i] = static_cast<uint16_t>(v);
+            else reinterpret_cast<uint32_t *>(img.data() + base)[i] = v;
+        };
         float *mu_e = reinterpret_cast<float *>(img.data() + e.off_mu);
         for (int32_t r = 0; r < Mp; ++r) {
             const int32_t a = r < m ? row_ptr[r] : 0, deg = r < m ? row_ptr[r + 1] - a : 0;
             for (int k = 0; k < e.DC; ++k)
-                ci[static_cast<size_t>(k) * Mp + r] = static_cast<uint16_t>(k < deg ? col_idx[a + k] : n);
+                put(e.off_cidx, static_cast<size_t>(k) * Mp + r, static_cast<uint32_t>(k < deg ? col_idx[a + k] : n));
         }
         for (int32_t v = 0; v < Np; ++v) {
             const int32_t a = v < n ? col_ptr[v] : 0, deg = v < n ? col_ptr[v + 1] - a : 0;
             for (int k = 0; k < e.DV; ++k) {
-                uint16_t ent = static_cast<uint16_t>(Mp);         // padding: message beta[0][Mp] = +0
+                uint32_t ent = static_cast<uint32_t>(Mp);         // padding: message beta[0][Mp] = +0
                 if (k < deg) {
                     const int32_t r = csc_row[a + k];
                     const int32_t slot = csc_edge[a + k] - row_ptr[r];
-                    ent = static_cast<uint16_t>(slot * R + r);
+                    ent = static_cast<uint32_t>(slot * R + r);
                 }
-                ve[static_cast<size_t>(k) * Np + v] = ent;
+                put(e.off_vent, static_cast<size_t>(k) * Np + v, ent);
             }
         }
         for (int32_t v = 0; v < Np + 2; ++v) mu_e[v] = v < n ? mu[v] : INFINITY;

@@ -40,7 +40,7 @@ uint32_t align16u(uint32_t x) { return (x + 15u) & ~15u; }
 int msg_bytes(int msg) { return msg == LBP_MSG_F32 ? 4 : (msg == LBP_MSG_F16 ? 2 : 1); }
 
 struct BpPlan {
-    bool ell = false, graph_smem = true, state_smem = true;
+    bool ell = false, graph_smem = true, state_smem = true, idx32 = false;
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -95,7 +95,8 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_
     size_t image = c->ell.bytes;
     const size_t budget0 = static_cast<size_t>(c->smem_optin);
     p.ell = c->d_ell != nullptr;
-    if (p.ell && image + off > budget0) {
+    p.idx32 = p.ell && c->ell.idx_bytes == 4;
+    if (p.ell && (p.idx32 || image + off > budget0)) {
         // Large code: graph image from global memory (L2); state in shared
         // memory when one group's fits, else in the workspace.
         p.graph_smem = false;
@@ -110,7 +111,10 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_
             G = 512;
             S = 2;
         }
-        if (req_G == 256 || req_G == 512 || req_G == 1024) {
+        if (p.idx32) {
+            // 32-bit images have one shape per placement.
+            if (p.state_smem) { G = 1024; S = 1; } else { G = 512; S = 2; }
+        } else if (req_G == 256 || req_G == 512 || req_G == 1024) {
             G = req_G;
             if (req_S > 0) S = req_S;
             if (p.state_smem && static_cast<size_t>(S) * off > budget0) S = static_cast<int>(budget0 / off);
@@ -372,7 +376,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
-        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem};
+        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32};
         switch (prm->msg) {
             case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, e, c->ell.DC, c->ell.DV, stream); break;
             case LBP_MSG_F16: rc = launch_bp_ell_f16(shp, e, c->ell.DC, c->ell.DV, stream); break;

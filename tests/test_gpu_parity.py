@@ -154,6 +154,22 @@ def test_lottery_baseline_policies(policy):
         assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
 
 
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
+def test_d27_table2_spacetime_32bit_image(msg):
+    """The d=27 space-time matrix in the exact form whose size Table II prints
+    (unrotated code, cyclic time boundary: 18,954 x 56,889, nnz 112,320): its
+    message offsets exceed 16 bits, so the kernel uses the 32-bit image from
+    global memory."""
+    from paper_2605_00038_gb300.inputs.codes import unrotated_surface
+    _, hz = unrotated_surface(27)
+    st = spacetime(hz, 27, "cyclic")
+    assert (st.n, st.nnz) == (56889, 112320)
+    pri = np.full(st.n, 0.004)
+    _, syn = sampler.sample(st, pri, seed=27, num_shots=40)
+    kw = dict(max_iter=40, lottery=1, msg=msg, seed=5)
+    assert_parity(gpu_decode(st, pri, syn, **kw), oracle_decode(st, pri, syn, **kw))
+
+
 def test_osd_bit_exact_on_gpu_llrs():
     """OSD fed with the GPU's exported LLRs gives the GPU's OSD output."""
     hx, _ = bb_code("bb72")
