@@ -405,10 +405,13 @@ static void cn_update(shot_ws *w, int c, int i, uint8_t s_c) {
             double mag = arith(prec, f * mn);
             out = neg ? -mag : mag;
         } else {
-            /* tanh rule: beta = (-1)^{s_c} 2 atanh(prod tanh(alpha/2)) (F64 only). */
+            /* tanh rule: beta = (-1)^{s_c} 2 atanh(prod tanh(alpha/2)) (F64 only),
+             * magnitude saturated at 25 (atanh(+-1) would be infinite). */
             double prod = s_c ? -1.0 : 1.0;
             for (int k2 = 0; k2 < deg; ++k2) if (k2 != k) prod *= tanh(w->alpha[k2] / 2.0);
-            out = 2.0 * atanh(prod);
+            double mag = 2.0 * atanh(fabs(prod));
+            if (!(mag <= 25.0)) mag = 25.0;
+            out = prod < 0.0 ? -mag : mag;
         }
         w->beta[e0 + k] = store_msg(prec, out);
     }

@@ -98,6 +98,22 @@ def test_sum_product_on_trees_is_exact_marginal(seed):
     assert np.allclose(res.llr[0], want, rtol=1e-9, atol=1e-9)
 
 
+@pytest.mark.parametrize("s_c", [0, 1])
+def test_sum_product_degree_two_check_passes_message_and_saturates(s_c):
+    """A weight-2 check forwards its other input unchanged, 2 atanh(tanh(a / 2))
+    = a, with the sign (-1)^{s_c}; above 25 the magnitude saturates at 25."""
+    h = SparseH(1, 2, np.array([0, 2]), np.array([0, 1]))
+    for p0, p1 in ((0.05, 0.2), (1e-15, 0.2), (1e-15, 1e-14)):
+        p = np.array([p0, p1])
+        mu = mu_of(p)
+        prm = OracleParams(max_iter=1, lottery=False, early_exit=False, prec=PREC_F64,
+                           rule=oracle.oracle.RULE_SUM_PRODUCT)
+        res = oracle.decode(h, p, np.array([[s_c]], dtype=np.uint8), prm, want_llr=True, nthreads=1)
+        sign = -1.0 if s_c else 1.0
+        want = mu + sign * np.minimum(mu[::-1], 25.0)
+        assert np.allclose(res.llr[0], want, rtol=1e-9, atol=1e-9), (p0, p1)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_f32_mode_is_single_precision(seed):
     """F32 mode: every posterior is a binary32 value, close to the F64 one."""
