@@ -401,6 +401,7 @@ def run_gpu(args):
         line["matched_ler"] = run_matched()
         line["precision"] = run_precision()
         line["lottery_design_space"] = run_policies()
+        line["check_rule"] = run_sum_product()
     if not args.no_extras and rank == 0 and world == 1:
         import oracle
         cores = os.cpu_count() or 1
@@ -730,13 +731,82 @@ def run_policies(shots: int = 1 << 18, seed: int = 41):
     return out
 
 
+def run_sum_product(shots: int = 1 << 17, seed: int = 43):
+    """Check-node rule comparison: normalised min-sum (Alg. 1) against the
+    sum-product tanh rule, with and without the lottery, on the rotated d=9
+    surface code with 9 noisy rounds at p = 0.005 (BP alone: unconverged
+    shots count as failures), then Lottery BP + OSD-0 throughput of each rule
+    on the d=11 space-time workload (2^18 shots, tuned launch shape)."""
+    import torch
+    from paper_2605_00038_gb300 import evaluate, lbp
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+    from paper_2605_00038_gb300.inputs.codes import rotated_surface, spacetime, spacetime_priors
+
+    d, p = 9, 0.005
+    hz, _ = rotated_surface(d)
+    h = spacetime(hz, d)
+    pri = spacetime_priors(hz, d, p, p)
+    e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
+    spec = evaluate.surface_spec(d, d, h.n)
+    true_d = torch.from_numpy(e.view(np.int64)).cuda()
+    sd = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec = Decoder(h, pri)
+
+    def one(**kw):
+        r = dec.decode(sd, dec.params(max_iter=100, osd=0, seed=seed, **kw))
+        torch.cuda.synchronize()
+        f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+        k = int(f.sum().item())
+        return {"ler_bp_only": k / shots, "ler_ci95": evaluate.wilson(k, shots),
+                "osd_invoke_rate": float((r.converged == 0).float().mean().item()),
+                "mean_iters": float(r.iters.float().mean().item())}
+
+    MS, SPR = lbp.LBP_RULE_MIN_SUM, lbp.LBP_RULE_SUM_PRODUCT
+    out = {"workload": "rotated_d9_st9_p0.005", "shots": shots, "quality": {
+        "min_sum_plain_f32": one(rule=MS, lottery=0, msg=0),
+        "min_sum_lottery_f32": one(rule=MS, lottery=1, msg=0),
+        "sum_product_plain_f32": one(rule=SPR, lottery=0, msg=0),
+        "sum_product_lottery_f32": one(rule=SPR, lottery=1, msg=0),
+        "sum_product_lottery_f16": one(rule=SPR, lottery=1, msg=1)}}
+    dec.close()
+
+    w = workloads.c2_d11_spacetime(shots=1 << 18)
+    _, syn2 = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    x = torch.from_numpy(syn2.view(np.int64)).cuda()
+    dec = Decoder(w.h, w.priors)
+    thr = {}
+    for name, rule, msg in (("min_sum_f32", MS, 0), ("sum_product_f32", SPR, 0),
+                            ("sum_product_f16", SPR, 1)):
+        prm = dec.params(**dict(w.decoder, rule=rule, msg=msg))
+        dec.tune(x, prm)
+        o = dec.alloc(w.shots)
+        ws = dec.workspace(prm, w.shots)
+        ms = []
+        for r in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lbp.lbp_decode(dec.code, prm, w.shots, x, o.err, o.converged, o.osd, o.iters, None, ws,
+                           torch.cuda.current_stream().cuda_stream)
+            b.record()
+            b.synchronize()
+            if r:
+                ms.append(a.elapsed_time(b))
+        thr[name] = {"shots_per_s": w.shots / (min(ms) / 1e3),
+                     "osd_invoke_rate": float((o.converged == 0).float().mean().item())}
+    dec.close()
+    out["throughput_d11_st11_lottery_osd"] = thr
+    return out
+
+
 def main():
     args = parse()
     if args.serving_only:
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"serving": run_serving(), "matched_ler": run_matched(),
-                          "precision": run_precision(), "lottery_design_space": run_policies()}),
+                          "precision": run_precision(), "lottery_design_space": run_policies(),
+                          "check_rule": run_sum_product()}),
               flush=True)
         return
     if args.impl == "reference":

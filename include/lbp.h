@@ -64,6 +64,18 @@ extern "C" {
 #define LBP_LOTTERY_RANDOM_UNRELIABLE 3
 #define LBP_LOTTERY_RANDOM_RANDOM     4
 
+/* Check-node rule.  LBP_RULE_MIN_SUM is the normalised min-sum update of
+ * Alg. 1.  LBP_RULE_SUM_PRODUCT is the tanh rule
+ *   beta_{v<-c} = (-1)^{s_c} 2 atanh( prod_{v' != v} tanh(alpha_{v'->c} / 2) ),
+ * evaluated in binary32 in the equivalent log-domain form
+ *   |beta| = phi( sum_{v' != v} phi(|alpha_{v'->c}|) ),  phi(x) = ln((e^x + 1) / (e^x - 1)),
+ * with the sign of the product, the magnitude saturated at 25 (phi(0) is
+ * infinite), and no normalisation factor (scale_mode and scale_const are
+ * ignored).  Its results are not bit-identical across toolkits: they depend on
+ * the device's expm1f and log1pf. */
+#define LBP_RULE_MIN_SUM     0
+#define LBP_RULE_SUM_PRODUCT 1
+
 /* Normalisation factor of the min-sum CN update. */
 #define LBP_SCALE_CONST    0   /* scale_const at every iteration */
 #define LBP_SCALE_ADAPTIVE 1   /* 1 - 2^-(i+1) at iteration i (Alg. 1) */
@@ -82,10 +94,12 @@ typedef struct {
     uint64_t seed;          /* key of the lottery's random draws */
     uint64_t shot_offset;   /* global index of shot 0 of this call: the draws of shot b
                                depend only on (seed, shot_offset + b), never on batching */
+    int32_t  rule;          /* LBP_RULE_*: check-node update */
+    int32_t  reserved;      /* must be 0 */
 } lbp_params;
 
 /* Fill *p with the paper's Lottery BP defaults: I = 100, adaptive scale,
- * lottery on with skip 6, OSD off, binary32 messages, seed 0. */
+ * lottery on with skip 6, OSD off, binary32 messages, min-sum rule, seed 0. */
 void lbp_params_default(lbp_params *p);
 
 /* Load the check matrix H and the per-column error probabilities p_v.
@@ -146,7 +160,8 @@ int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots
  * threads per group, the "shot tile" and the threads working on one shot):
  * decodes the given batch once per candidate shape, twice each, timing the
  * BP kernel with CUDA events, and stores the fastest shape in `code` for its
- * message type (params->msg); later decodes of that message type use it.
+ * message type and check-node rule (params->msg, params->rule); later decodes
+ * with that pair use it.
  * Every shape computes identical results, so on return the outputs hold
  * lbp_decode's results for the batch.  Arguments as for lbp_decode (llr_out
  * omitted).  Synchronous: returns after the stream has drained.  It writes

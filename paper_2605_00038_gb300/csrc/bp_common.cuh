@@ -103,6 +103,20 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t counte
     return z ^ (z >> 31);
 }
 
+// Gallager's function phi(x) = ln((e^x + 1) / (e^x - 1)) = -ln tanh(x / 2)
+// for x >= 0, written as log1p(2 / expm1(x)) so that it keeps full relative
+// accuracy at both ends: phi(0) = +inf, phi(+inf) = 0, and phi(phi(x)) = x.
+// The sum-product magnitude 2 atanh(prod tanh(|alpha_k| / 2)) equals
+// phi(sum_k phi(|alpha_k|)); the product form loses everything above
+// |beta| ~ 17 in binary32 (tanh rounds to 1), this form does not.
+__device__ __forceinline__ float gallager_phi(float x) {
+    return log1pf(__fdiv_rn(2.0f, expm1f(x)));
+}
+
+// Saturation of sum-product message magnitudes (phi of an empty or
+// vanishing sum is infinite).
+constexpr float kSpMaxMag = 25.0f;
+
 // Normalisation factor at iteration i, binary32: the constant, or
 // 1 - 2^-(i+1) rounded to nearest (exact for i + 1 <= 24, 1.0 beyond).
 __device__ __forceinline__ float scale_at(int mode, float c, int i) {

@@ -21,7 +21,12 @@
 // Check update per check: sign bits r_k = [alpha_k < 0] << 31 and their XOR
 // t (with (-1)^{s_c}); exclusive minima of |alpha| from prefix and suffix
 // minima; beta_k = f * excl_k carrying sign bit t ^ r_k.  Same values as the
-// min1/min2/argmin form of bp_kernel, with fewer instructions.
+// min1/min2/argmin form of bp_kernel, with fewer instructions.  The
+// sum-product instantiation (kRule = LBP_RULE_SUM_PRODUCT) keeps the signs
+// and replaces the minima by exclusive sums of phi(|alpha|) (prefix plus
+// suffix, so no term is ever subtracted back out), beta_k = min(phi(excl_k),
+// 25) with the same sign; the padding column (+inf) has phi = 0, still a
+// neutral element.
 // Placement: the graph image and each group's state sit in shared memory when
 // they fit (kGraphSmem, kStateSmem); otherwise they are read from global
 // memory (the image is L2-resident; the state goes to a per-group slice of the
@@ -45,7 +50,7 @@ struct BpEllArgs {
     int32_t m, n;
     int32_t max_iter, scale_mode;
     float scale_const;
-    int32_t lottery, lottery_skip, osd, policy;
+    int32_t lottery, lottery_skip, osd, policy, rule;
     uint64_t seed, shot_offset;
     int64_t num_shots;
     const uint64_t *syn;
@@ -102,7 +107,36 @@ __device__ __forceinline__ void check_update(const float (&al)[DC], uint32_t sbi
     }
 }
 
-template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename IdxT = uint16_t>
+// Sum-product form: exclusive sums of phi(|alpha|), beta_k = phi(excl_k)
+// saturated at 25, sign as in the min-sum update.
+template <typename MsgT, int DC>
+__device__ __forceinline__ void check_update_sp(const float (&al)[DC], uint32_t sbit,
+                                                MsgT (&out)[DC]) {
+    uint32_t r[DC];
+    uint32_t tot = sbit << 31;
+    float ph[DC];
+    #pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        r[k] = al[k] < 0.0f ? 0x80000000u : 0u;
+        tot ^= r[k];
+        ph[k] = gallager_phi(fabsf(al[k]));
+    }
+    float pre[DC], suf[DC];
+    pre[0] = ph[0];
+    #pragma unroll
+    for (int k = 1; k < DC; ++k) pre[k] = __fadd_rn(pre[k - 1], ph[k]);
+    suf[DC - 1] = ph[DC - 1];
+    #pragma unroll
+    for (int k = DC - 2; k >= 0; --k) suf[k] = __fadd_rn(suf[k + 1], ph[k]);
+    #pragma unroll
+    for (int k = 0; k < DC; ++k) {
+        const float ex = k == 0 ? suf[1] : (k == DC - 1 ? pre[DC - 2] : __fadd_rn(pre[k - 1], suf[k + 1]));
+        out[k] = Msg<MsgT>::store_signed(fminf(gallager_phi(ex), kSpMaxMag), tot ^ r[k]);
+    }
+}
+
+template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename IdxT = uint16_t,
+          int kRule = LBP_RULE_MIN_SUM>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
     static_assert(kGraphSmem == false || sizeof(IdxT) == 2, "32-bit images are read from global memory");
@@ -200,8 +234,13 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 }
                 const uint32_t sw = s_w[c >> 5];               // c even: c and c + 1 share a word
                 MsgT o0[DC], o1[DC];
-                check_update<MsgT, DC>(al0, (sw >> (c & 31)) & 1u, f, o0);
-                check_update<MsgT, DC>(al1, (sw >> ((c & 31) + 1)) & 1u, f, o1);
+                if (kRule == LBP_RULE_SUM_PRODUCT) {
+                    check_update_sp<MsgT, DC>(al0, (sw >> (c & 31)) & 1u, o0);
+                    check_update_sp<MsgT, DC>(al1, (sw >> ((c & 31) + 1)) & 1u, o1);
+                } else {
+                    check_update<MsgT, DC>(al0, (sw >> (c & 31)) & 1u, f, o0);
+                    check_update<MsgT, DC>(al1, (sw >> ((c & 31) + 1)) & 1u, f, o1);
+                }
                 #pragma unroll
                 for (int k = 0; k < DC; ++k) beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
             }

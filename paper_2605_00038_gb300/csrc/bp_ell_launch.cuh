@@ -1,14 +1,14 @@
 // Dispatch of bp_ell_kernel over the group width G and the degree bounds
-// (DC, DV) for one message type.
+// (DC, DV) for one message type and check-node rule (kRule).
 #pragma once
 
 #include "launch.h"
 
 namespace lbp {
 
-template <typename MsgT, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
 int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, IdxT>;
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, IdxT, kRule>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -18,49 +18,49 @@ int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     return LBP_OK;
 }
 
-template <typename MsgT, int DC, int DV>
+template <typename MsgT, int kRule, int DC, int DV>
 int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     if (s.graph_smem) {
         switch (s.G) {
-            case 32: return launch_ell_one<MsgT, 32, DC, DV, true, true>(s, a, st);
-            case 64: return launch_ell_one<MsgT, 64, DC, DV, true, true>(s, a, st);
-            case 96: return launch_ell_one<MsgT, 96, DC, DV, true, true>(s, a, st);
-            case 128: return launch_ell_one<MsgT, 128, DC, DV, true, true>(s, a, st);
-            case 192: return launch_ell_one<MsgT, 192, DC, DV, true, true>(s, a, st);
-            case 256: return launch_ell_one<MsgT, 256, DC, DV, true, true>(s, a, st);
+            case 32: return launch_ell_one<MsgT, kRule, 32, DC, DV, true, true>(s, a, st);
+            case 64: return launch_ell_one<MsgT, kRule, 64, DC, DV, true, true>(s, a, st);
+            case 96: return launch_ell_one<MsgT, kRule, 96, DC, DV, true, true>(s, a, st);
+            case 128: return launch_ell_one<MsgT, kRule, 128, DC, DV, true, true>(s, a, st);
+            case 192: return launch_ell_one<MsgT, kRule, 192, DC, DV, true, true>(s, a, st);
+            case 256: return launch_ell_one<MsgT, kRule, 256, DC, DV, true, true>(s, a, st);
             default: return LBP_ENOSYS;
         }
     }
     // Large codes: graph in global memory; state in shared or global memory.
     if (s.idx32) {
         if (s.state_smem) {
-            if (s.G == 1024) return launch_ell_one<MsgT, 1024, DC, DV, false, true, uint32_t>(s, a, st);
+            if (s.G == 1024) return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, true, uint32_t>(s, a, st);
             return LBP_ENOSYS;
         }
-        if (s.G == 512) return launch_ell_one<MsgT, 512, DC, DV, false, false, uint32_t>(s, a, st);
+        if (s.G == 512) return launch_ell_one<MsgT, kRule, 512, DC, DV, false, false, uint32_t>(s, a, st);
         return LBP_ENOSYS;
     }
     if (s.state_smem) {
         switch (s.G) {
-            case 256: return launch_ell_one<MsgT, 256, DC, DV, false, true>(s, a, st);
-            case 512: return launch_ell_one<MsgT, 512, DC, DV, false, true>(s, a, st);
-            case 1024: return launch_ell_one<MsgT, 1024, DC, DV, false, true>(s, a, st);
+            case 256: return launch_ell_one<MsgT, kRule, 256, DC, DV, false, true>(s, a, st);
+            case 512: return launch_ell_one<MsgT, kRule, 512, DC, DV, false, true>(s, a, st);
+            case 1024: return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, true>(s, a, st);
             default: return LBP_ENOSYS;
         }
     }
     switch (s.G) {
-        case 256: return launch_ell_one<MsgT, 256, DC, DV, false, false>(s, a, st);
-        case 512: return launch_ell_one<MsgT, 512, DC, DV, false, false>(s, a, st);
-        case 1024: return launch_ell_one<MsgT, 1024, DC, DV, false, false>(s, a, st);
+        case 256: return launch_ell_one<MsgT, kRule, 256, DC, DV, false, false>(s, a, st);
+        case 512: return launch_ell_one<MsgT, kRule, 512, DC, DV, false, false>(s, a, st);
+        case 1024: return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, false>(s, a, st);
         default: return LBP_ENOSYS;
     }
 }
 
-template <typename MsgT>
+template <typename MsgT, int kRule>
 int launch_ell(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
-    if (DC == 6 && DV == 2) return launch_ell_g<MsgT, 6, 2>(s, a, st);
-    if (DC == 6 && DV == 3) return launch_ell_g<MsgT, 6, 3>(s, a, st);
-    if (DC == 8 && DV == 4) return launch_ell_g<MsgT, 8, 4>(s, a, st);
+    if (DC == 6 && DV == 2) return launch_ell_g<MsgT, kRule, 6, 2>(s, a, st);
+    if (DC == 6 && DV == 3) return launch_ell_g<MsgT, kRule, 6, 3>(s, a, st);
+    if (DC == 8 && DV == 4) return launch_ell_g<MsgT, kRule, 8, 4>(s, a, st);
     return LBP_ENOSYS;
 }
 

@@ -34,6 +34,8 @@
 //    (bar.red.or.pred).  The lottery runs in the group's first warp:
 //    ballot/popc prefix sums pick c*, one lane per neighbour counts
 //    |C(v) ∩ U| and a shuffle reduction picks v*.
+//  * The sum-product rule (a.rule) replaces the minima by exclusive sums of
+//    Gallager's phi(|alpha|) and beta = phi(sum), saturated at 25.
 //  * All arithmetic is explicit round-to-nearest binary32 (__fadd_rn,
 //    __fsub_rn, __fmul_rn; the library builds with -fmad=false), so results
 //    are bit-reproducible.
@@ -53,7 +55,7 @@ struct BpArgs {
     int32_t m, n;
     int32_t max_iter, scale_mode;
     float scale_const;
-    int32_t lottery, lottery_skip, osd, policy;
+    int32_t lottery, lottery_skip, osd, policy, rule;
     uint64_t seed, shot_offset;
     int64_t num_shots;
     const uint64_t *syn;      // [B][wm64]
@@ -130,7 +132,31 @@ __global__ void __launch_bounds__(1024, 1) bp_kernel(const BpArgs a) {
         for (; it < I; ++it) {
             const float f = scale_at(a.scale_mode, a.scale_const, it);
             // ---- C2V (check-node update) --------------------------------
-            for (int c = t; c < m; c += G) {
+            for (int c = t; c < m && a.rule == LBP_RULE_SUM_PRODUCT; c += G) {
+                // Sum-product: exclusive sums of phi(|alpha|) from prefix sums
+                // and a running suffix sum (deg <= 32), in the same order of
+                // binary32 additions as the bounded-degree kernel.
+                const int e0 = row_ptr[c];
+                const int deg = row_ptr[c + 1] - e0;
+                unsigned parity = (s_w[c >> 5] >> (c & 31)) & 1u;
+                unsigned negmask = 0u;
+                float ph[32], pre[32];
+                for (int k = 0; k < deg; ++k) {
+                    const int v = col_idx[e0 + k];
+                    const float al = (it == 0) ? mu[v] : __fsub_rn(lam[v], Msg<MsgT>::load(beta[e0 + k]));
+                    if (al < 0.0f) { negmask |= 1u << k; parity ^= 1u; }
+                    ph[k] = gallager_phi(fabsf(al));
+                    pre[k] = k == 0 ? ph[0] : __fadd_rn(pre[k - 1], ph[k]);
+                }
+                float suf = 0.0f;
+                for (int k = deg - 1; k >= 0; --k) {
+                    const float ex = k == deg - 1 ? pre[deg - 2] : (k == 0 ? suf : __fadd_rn(pre[k - 1], suf));
+                    suf = k == deg - 1 ? ph[k] : __fadd_rn(suf, ph[k]);
+                    const uint32_t sg = ((parity ^ (negmask >> k)) & 1u) << 31;
+                    beta[e0 + k] = Msg<MsgT>::store_signed(fminf(gallager_phi(ex), kSpMaxMag), sg);
+                }
+            }
+            for (int c = t; c < m && a.rule != LBP_RULE_SUM_PRODUCT; c += G) {
                 const int e0 = row_ptr[c];
                 const int deg = row_ptr[c + 1] - e0;
                 unsigned parity = (s_w[c >> 5] >> (c & 31)) & 1u;   // (-1)^{s_c}

@@ -80,5 +80,5 @@ struct lbp_code {
     float *d_mu;
     // BP launch shape chosen by lbp_tune per message type (0 = not tuned):
     // groups per CTA and threads per group.
-    int tuned_groups[3], tuned_G[3];
+    int tuned_groups[6], tuned_G[6];   // per (rule, message type), lbp_tune
 };

@@ -17,5 +17,8 @@ struct LaunchShape {
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
 int launch_bp_ell_f16(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
 int launch_bp_ell_i8(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+int launch_bp_ell_sp_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+int launch_bp_ell_sp_f16(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
+int launch_bp_ell_sp_i8(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);
 
 }  // namespace lbp

@@ -43,6 +43,7 @@ extern "C" void lbp_params_default(lbp_params *p) {
     p->lottery_skip = 6;
     p->osd = 0;
     p->msg = LBP_MSG_F32;
+    p->rule = LBP_RULE_MIN_SUM;
 }
 
 extern "C" const char *lbp_strerror(int code) {

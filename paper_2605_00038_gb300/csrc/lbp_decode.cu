@@ -39,6 +39,12 @@ uint32_t align16u(uint32_t x) { return (x + 15u) & ~15u; }
 
 int msg_bytes(int msg) { return msg == LBP_MSG_F32 ? 4 : (msg == LBP_MSG_F16 ? 2 : 1); }
 
+// Index of the tuned launch shape kept per (check-node rule, message type).
+int tuned_slot(int msg, int rule) {
+    const int mi = msg >= 0 && msg < 3 ? msg : 0;
+    return (rule == LBP_RULE_SUM_PRODUCT ? 3 : 0) + mi;
+}
+
 struct BpPlan {
     bool ell = false, graph_smem = true, state_smem = true, idx32 = false;
     int groups = 0, G = 0, grid = 0;
@@ -76,12 +82,15 @@ int validate_params(const lbp_params *p) {
     if (p->osd != 0 && p->osd != 1) return LBP_EINVAL;
     if (p->msg != LBP_MSG_F32 && p->msg != LBP_MSG_F16 && p->msg != LBP_MSG_I8) return LBP_EINVAL;
     if (p->lottery_policy < LBP_LOTTERY_PROPOSED || p->lottery_policy > LBP_LOTTERY_RANDOM_RANDOM) return LBP_EINVAL;
+    if (p->rule != LBP_RULE_MIN_SUM && p->rule != LBP_RULE_SUM_PRODUCT) return LBP_EINVAL;
+    if (p->reserved != 0) return LBP_EINVAL;
     return LBP_OK;
 }
 
 // Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
 // group does not fit in shared memory.
-int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_S = 0, int req_G = 0) {
+int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out, int req_S = 0,
+            int req_G = 0) {
     const int W32 = (c->m + 31) / 32;
     BpPlan p;
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
@@ -151,7 +160,7 @@ int plan_bp(const lbp_code *c, int msg, int64_t num_shots, BpPlan *out, int req_
     int G = 32;
     while (G < 128 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
     if (p.ell && G == 128 && S_fit >= 6) G = 96;
-    const int mi = msg >= 0 && msg < 3 ? msg : 0;
+    const int mi = tuned_slot(msg, rule);
     if (c->tuned_G[mi] > 0) {
         G = c->tuned_G[mi];
         S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
@@ -319,7 +328,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
                          void *ws, size_t ws_bytes, cudaStream_t stream, int req_S, int req_G,
                          float *bp_ms) {
     BpPlan bp;
-    int rc = plan_bp(c, prm->msg, B, &bp, req_S, req_G);
+    int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G);
     if (rc) return rc;
     OsdPlan op;
     OsdWarpPlan wp;
@@ -343,6 +352,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     a.max_iter = prm->max_iter; a.scale_mode = prm->scale_mode; a.scale_const = prm->scale_const;
     a.lottery = prm->lottery; a.lottery_skip = prm->lottery_skip; a.osd = prm->osd;
     a.policy = prm->lottery_policy;
+    a.rule = prm->rule;
     a.seed = prm->seed; a.shot_offset = prm->shot_offset;
     a.num_shots = B;
     a.syn = syn; a.err = err; a.conv = conv; a.osd_out = osd_out; a.iters = iters; a.llr = llr;
@@ -370,6 +380,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.scale_const = a.scale_const; e.lottery = a.lottery; e.lottery_skip = a.lottery_skip;
         e.osd = a.osd; e.seed = a.seed; e.shot_offset = a.shot_offset; e.num_shots = a.num_shots;
         e.policy = a.policy;
+        e.rule = a.rule;
         e.syn = a.syn; e.err = a.err; e.conv = a.conv; e.osd_out = a.osd_out; e.iters = a.iters;
         e.llr = a.llr; e.counters = a.counters; e.osd_list = a.osd_list; e.osd_llr = a.osd_llr;
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
@@ -377,10 +388,17 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
         const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32};
+        const bool sp = prm->rule == LBP_RULE_SUM_PRODUCT;
         switch (prm->msg) {
-            case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, e, c->ell.DC, c->ell.DV, stream); break;
-            case LBP_MSG_F16: rc = launch_bp_ell_f16(shp, e, c->ell.DC, c->ell.DV, stream); break;
-            default: rc = launch_bp_ell_i8(shp, e, c->ell.DC, c->ell.DV, stream); break;
+            case LBP_MSG_F32:
+                rc = (sp ? launch_bp_ell_sp_f32 : launch_bp_ell_f32)(shp, e, c->ell.DC, c->ell.DV, stream);
+                break;
+            case LBP_MSG_F16:
+                rc = (sp ? launch_bp_ell_sp_f16 : launch_bp_ell_f16)(shp, e, c->ell.DC, c->ell.DV, stream);
+                break;
+            default:
+                rc = (sp ? launch_bp_ell_sp_i8 : launch_bp_ell_i8)(shp, e, c->ell.DC, c->ell.DV, stream);
+                break;
         }
     } else {
         switch (prm->msg) {
@@ -475,7 +493,7 @@ extern "C" size_t lbp_workspace_size(const lbp_code *code, const lbp_params *par
         plan_osd_warp(code, num_shots, &wp);
     }
     BpPlan bp;
-    if (plan_bp(code, params->msg, num_shots, &bp)) return 0;
+    if (plan_bp(code, params->msg, params->rule, num_shots, &bp)) return 0;
     return layout(code, params, num_shots, params->osd ? &op : nullptr, params->osd ? &wp : nullptr, &bp).total;
 }
 
@@ -573,7 +591,7 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != code->device) return LBP_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int mi = params->msg;
+    const int mi = tuned_slot(params->msg, params->rule);
     code->tuned_G[mi] = 0;
     code->tuned_groups[mi] = 0;
     const int Gs[] = {32, 64, 96, 128, 192, 256, 512, 1024};
@@ -581,7 +599,7 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     int best_S = 0, best_G = 0;
     for (int G : Gs) {
         BpPlan probe;
-        if (plan_bp(code, mi, num_shots, &probe, 1024, G) != LBP_OK) continue;
+        if (plan_bp(code, params->msg, params->rule, num_shots, &probe, 1024, G) != LBP_OK) continue;
         if (probe.G != G) continue;                    // shape not available for this code
         const int S = probe.groups;
         float ms = 0.0f, warm = 0.0f;

@@ -21,6 +21,7 @@ LBP_NOALLOC_SCRATCH_BYTES = 32 << 20
 LBP_OSD_NOT_RUN, LBP_OSD_APPLIED, LBP_OSD_NO_SOLUTION = 0, 1, 2
 LBP_MSG_F32, LBP_MSG_F16, LBP_MSG_I8 = 0, 1, 2
 LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
+LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
 (LBP_LOTTERY_PROPOSED, LBP_LOTTERY_WORST_UNRELIABLE, LBP_LOTTERY_WORST_RANDOM,
  LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM) = range(5)
 
@@ -36,7 +37,8 @@ class lbp_params(ctypes.Structure):
                 ("scale_const", ctypes.c_float), ("lottery", ctypes.c_int32),
                 ("lottery_skip", ctypes.c_int32), ("osd", ctypes.c_int32),
                 ("msg", ctypes.c_int32), ("lottery_policy", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("shot_offset", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("shot_offset", ctypes.c_uint64),
+                ("rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class LbpError(RuntimeError):

@@ -34,9 +34,9 @@ def test_exports_every_declared_symbol(L):
 
 def test_params_default_matches_paper(L):
     p = lbp.lbp_params_default()
-    assert (p.max_iter, p.scale_mode, p.lottery, p.lottery_skip, p.osd, p.msg) == (
-        100, lbp.LBP_SCALE_ADAPTIVE, 1, 6, 0, lbp.LBP_MSG_F32)
-    assert ctypes.sizeof(lbp.lbp_params) == 48
+    assert (p.max_iter, p.scale_mode, p.lottery, p.lottery_skip, p.osd, p.msg, p.rule) == (
+        100, lbp.LBP_SCALE_ADAPTIVE, 1, 6, 0, lbp.LBP_MSG_F32, lbp.LBP_RULE_MIN_SUM)
+    assert ctypes.sizeof(lbp.lbp_params) == 56
 
 
 def test_strerror(L):
@@ -72,7 +72,7 @@ def test_decode_rejects_bad_params_without_gpu(L):
     rc = L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(bad), 1, None, None, None, None, None,
                       None, None, 0, None)
     assert rc == lbp.LBP_EINVAL
-    for kw in (dict(msg=7), dict(scale_mode=5), dict(lottery=2), dict(lottery_policy=5),
+    for kw in (dict(msg=7), dict(scale_mode=5), dict(lottery=2), dict(lottery_policy=5), dict(rule=2), dict(reserved=1),
                dict(scale_mode=0, scale_const=0.0), dict(lottery_skip=-1)):
         p = lbp.lbp_params_default(**kw)
         assert L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(p), 1, None, None, None, None, None,
