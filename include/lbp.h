@@ -125,6 +125,19 @@ int lbp_free_code(lbp_code *code);
 /* Sizes of a loaded code (any pointer may be NULL). */
 int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
 
+/* Whether lbp_load_code recognised H as the space-time matrix (Eq. 1) of the
+ * unrotated distance-d surface code whose per-round rows are those of
+ * Table III: T rounds of d(d-1) checks of one type (*type 0: X, 1: Z), then
+ * T - 1 (open time boundary, *cyclic 0) or T (cyclic, 1) measurement blocks,
+ * d >= 3, columns and rows in Table III's order.  Such a code can run K_bp on
+ * the implicit graph: every neighbour index is evaluated from the formulas,
+ * no index image is read (LBP_GRAPH=table|implicit selects the form, else
+ * lbp_tune's choice, else the image when it fits shared memory beside one
+ * shot's state and the implicit graph when it does not).  Both forms give
+ * identical results.  *d = 0 when not recognised; any output pointer may be
+ * NULL. */
+int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type, int32_t *cyclic);
+
 /* Bytes of device workspace lbp_decode needs for num_shots shots with these
  * parameters (0 on invalid input).  The size grows linearly with num_shots
  * only when params->osd is set (the LLRs of shots handed to OSD).

@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "bp_common.cuh"
+#include "bp_graph.cuh"
 #include "internal.h"
 
 namespace lbp {
@@ -66,20 +67,8 @@ struct BpEllArgs {
     uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
     uint8_t *gstate;          // per-group state slices when not in shared memory
     uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
-};
-
-// Index width of the ELL image: 16-bit (the image fits shared memory) or
-// 32-bit (large codes, read from global memory); P holds two indices.
-template <typename IdxT> struct Idx;
-template <> struct Idx<uint16_t> {
-    using P = uint32_t;
-    static __device__ __forceinline__ uint32_t lo(uint32_t p) { return p & 0xffffu; }
-    static __device__ __forceinline__ uint32_t hi(uint32_t p) { return p >> 16; }
-};
-template <> struct Idx<uint32_t> {
-    using P = uint2;
-    static __device__ __forceinline__ uint32_t lo(uint2 p) { return p.x; }
-    static __device__ __forceinline__ uint32_t hi(uint2 p) { return p.y; }
+    SurfaceDesc surf;         // implicit graph (SurfaceGraph)
+    const float *mu_tab;      // its mu[Np + 2] when not uniform per block
 };
 
 // Exclusive minima and signed outputs of one check (DC slots).
@@ -135,13 +124,12 @@ __device__ __forceinline__ void check_update_sp(const float (&al)[DC], uint32_t 
     }
 }
 
-template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename IdxT = uint16_t,
+template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename GraphT,
           int kRule = LBP_RULE_MIN_SUM>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
-    static_assert(kGraphSmem == false || sizeof(IdxT) == 2, "32-bit images are read from global memory");
+    static_assert(GraphT::kImage || !kGraphSmem, "an implicit graph has no image to stage");
     using PairT = typename Pair<MsgT>::type;
-    using IP = typename Idx<IdxT>::P;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
@@ -152,13 +140,7 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     const int m = a.m, n = a.n, I = a.max_iter;
     const int Mp = a.img.Mp, Np = a.img.Np, R = Mp + 2;
     const int mpairs = Mp >> 1, npairs = Np >> 1;
-    const uint8_t *gbase = kGraphSmem ? smem : a.image;
-    const IdxT *cidx = reinterpret_cast<const IdxT *>(gbase + a.img.off_cidx);
-    const IP *cidx2 = reinterpret_cast<const IP *>(cidx);
-    const IdxT *vent = reinterpret_cast<const IdxT *>(gbase + a.img.off_vent);
-    const IP *vent2 = reinterpret_cast<const IP *>(vent);
-    const float *mu = reinterpret_cast<const float *>(gbase + a.img.off_mu);
-    const float2 *mu2 = reinterpret_cast<const float2 *>(mu);
+    const GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.mu_tab, m, n);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
 
     const int grp = threadIdx.x / G;
@@ -216,20 +198,20 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             for (int pr = t; pr < mpairs; pr += G) {
                 const int c = 2 * pr;
                 float al0[DC], al1[DC];
+                uint32_t v0[DC], v1[DC];
+                gr.cols2(pr, v0, v1);
                 if (it == 0) {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
-                        const IP cc = cidx2[k * mpairs + pr];
-                        al0[k] = mu[Idx<IdxT>::lo(cc)];
-                        al1[k] = mu[Idx<IdxT>::hi(cc)];
+                        al0[k] = gr.mu(v0[k]);
+                        al1[k] = gr.mu(v1[k]);
                     }
                 } else {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
-                        const IP cc = cidx2[k * mpairs + pr];
                         const PairT bb = beta2[((k * R) >> 1) + pr];
-                        al0[k] = __fsub_rn(lam[Idx<IdxT>::lo(cc)], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
-                        al1[k] = __fsub_rn(lam[Idx<IdxT>::hi(cc)], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
+                        al0[k] = __fsub_rn(lam[v0[k]], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
+                        al1[k] = __fsub_rn(lam[v1[k]], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
                     }
                 }
                 const uint32_t sw = s_w[c >> 5];               // c even: c and c + 1 share a word
@@ -248,14 +230,14 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
             for (int q = t; q < npairs; q += G) {
-                IP ent[DV];
-                const float2 mm = mu2[q];
+                uint32_t e0[DV], e1[DV];
+                gr.ents2(q, e0, e1);
+                const float2 mm = gr.mu2(q);
                 float acc0 = mm.x, acc1 = mm.y;
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
-                    ent[k] = vent2[k * npairs + q];
-                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[Idx<IdxT>::lo(ent[k])]));
-                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[Idx<IdxT>::hi(ent[k])]));
+                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[e0[k]]));
+                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[e1[k]]));
                 }
                 lam2[q] = make_float2(acc0, acc1);
                 if (acc0 <= 0.0f || acc1 <= 0.0f) {
@@ -264,7 +246,7 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                         #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             if ((h == 0 ? acc0 : acc1) <= 0.0f) {
-                                const unsigned o = h == 0 ? Idx<IdxT>::lo(ent[k]) : Idx<IdxT>::hi(ent[k]);
+                                const unsigned o = h == 0 ? e0[k] : e1[k];
                                 const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
                                 if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
                             }
@@ -309,9 +291,16 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                                     word &= word - 1u;
                                     int ne = 0;
                                     #pragma unroll
+                                    uint32_t vv[DC], unused[DC];
+                                    gr.cols2(c >> 1, vv, unused);
+                                    if (c & 1) {
+                                        #pragma unroll
+                                        for (int k = 0; k < DC; ++k) vv[k] = unused[k];
+                                    }
+                                    #pragma unroll
                                     for (int k = 0; k < DC; ++k) {
-                                        const int v = cidx[k * Mp + c];
-                                        ne += (v < n && lam[v] <= 0.0f) ? 1 : 0;
+                                        const uint32_t v = vv[k];
+                                        ne += (v < static_cast<uint32_t>(n) && lam[v] <= 0.0f) ? 1 : 0;
                                     }
                                     if (ne > bn || (ne == bn && c < bcr)) { bn = ne; bcr = c; }
                                 }
@@ -354,25 +343,35 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                         }
                         int bc = -1, bv = 0x7fffffff;
                         float ba = 0.0f;
+                        // Lane k < DC holds slot k of c* (n when absent).
+                        const int vl = lane < DC ? static_cast<int>(gr.col(lane, cstar)) : n;
                         if (a.policy == LBP_LOTTERY_WORST_RANDOM || a.policy == LBP_LOTTERY_RANDOM_RANDOM) {
-                            // Random VN: column floor(u2 deg / 2^32) of c*.
-                            const int vl = lane < DC ? cidx[lane * Mp + cstar] : n;
-                            const int deg = __popc(__ballot_sync(0xffffffffu, lane < DC && vl < n));
+                            // Random VN: column floor(u2 deg / 2^32) of c* in ascending
+                            // order (rank of each present column among the slots).
+                            const bool present = lane < DC && vl < n;
+                            const int deg = __popc(__ballot_sync(0xffffffffu, present));
                             const int kk = static_cast<int>((static_cast<uint64_t>(u2) * static_cast<uint32_t>(deg)) >> 32);
-                            bv = cidx[kk * Mp + cstar];
+                            int rank = 0;
+                            #pragma unroll
+                            for (int o = 0; o < DC; ++o) {
+                                const int w = __shfl_sync(0xffffffffu, vl, o);
+                                rank += (w < vl) ? 1 : 0;
+                            }
+                            const unsigned pick = __ballot_sync(0xffffffffu, present && rank == kk);
+                            bv = __shfl_sync(0xffffffffu, vl, __ffs(pick) - 1);
                             bc = 0;
                         } else {
                             // Unreliable VN (the proposed rule first prefers the column
                             // with the most unsatisfied checks), then lowest column.
                             if (lane < DC) {
-                                const int v = cidx[lane * Mp + cstar];
+                                const int v = vl;
                                 if (v < n) {
                                     bv = v;
                                     bc = 0;
                                     if (a.policy == LBP_LOTTERY_PROPOSED) {
                                         #pragma unroll
                                         for (int kk = 0; kk < DV; ++kk) {
-                                            const unsigned o = vent[kk * Np + v];
+                                            const unsigned o = gr.ent(kk, v);
                                             const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
                                             if (r < static_cast<unsigned>(m))
                                                 bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;

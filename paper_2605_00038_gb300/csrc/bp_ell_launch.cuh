@@ -6,9 +6,9 @@
 
 namespace lbp {
 
-template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
-int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, IdxT, kRule>;
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename GraphT>
+int launch_graph_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, GraphT, kRule>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -16,6 +16,33 @@ int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     }
     k<<<s.grid, s.groups * G, s.smem, st>>>(a);
     return LBP_OK;
+}
+
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
+int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    return launch_graph_one<MsgT, kRule, G, DC, DV, GS, SS, EllGraph<IdxT, DC, DV>>(s, a, st);
+}
+
+// Implicit surface-code graph (Table III): no image; state in shared memory
+// (any G) or in the workspace (G = 512, 1024).
+template <typename MsgT, int kRule>
+int launch_surface(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    using GR = SurfaceGraph<6, 2>;
+    if (s.state_smem) {
+        switch (s.G) {
+            case 64: return launch_graph_one<MsgT, kRule, 64, 6, 2, false, true, GR>(s, a, st);
+            case 96: return launch_graph_one<MsgT, kRule, 96, 6, 2, false, true, GR>(s, a, st);
+            case 128: return launch_graph_one<MsgT, kRule, 128, 6, 2, false, true, GR>(s, a, st);
+            case 192: return launch_graph_one<MsgT, kRule, 192, 6, 2, false, true, GR>(s, a, st);
+            case 256: return launch_graph_one<MsgT, kRule, 256, 6, 2, false, true, GR>(s, a, st);
+            case 512: return launch_graph_one<MsgT, kRule, 512, 6, 2, false, true, GR>(s, a, st);
+            case 1024: return launch_graph_one<MsgT, kRule, 1024, 6, 2, false, true, GR>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
+    }
+    if (s.G == 512) return launch_graph_one<MsgT, kRule, 512, 6, 2, false, false, GR>(s, a, st);
+    if (s.G == 1024) return launch_graph_one<MsgT, kRule, 1024, 6, 2, false, false, GR>(s, a, st);
+    return LBP_ENOSYS;
 }
 
 template <typename MsgT, int kRule, int DC, int DV>
@@ -58,6 +85,7 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
 
 template <typename MsgT, int kRule>
 int launch_ell(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
+    if (s.surface) return launch_surface<MsgT, kRule>(s, a, st);
     if (DC == 6 && DV == 2) return launch_ell_g<MsgT, kRule, 6, 2>(s, a, st);
     if (DC == 6 && DV == 3) return launch_ell_g<MsgT, kRule, 6, 3>(s, a, st);
     if (DC == 8 && DV == 4) return launch_ell_g<MsgT, kRule, 8, 4>(s, a, st);

@@ -40,6 +40,22 @@ struct EllImage {
     int32_t idx_bytes;       // 2 (uint16 indices) or 4 (uint32, image read from global memory)
 };
 
+// Space-time matrix of the unrotated surface code (Eq. 1 with one check type
+// per round), recognised by lbp_load_code: T rounds of m_r = d(d-1) checks
+// over n_r = d^2 + (d-1)^2 data columns, then nb measurement blocks of m_r
+// columns (nb = T - 1 with an open time boundary, T when cyclic).  Table III
+// gives each check's columns by closed formulas; the BP kernel evaluates them
+// (and their inverses for the column side) instead of loading an index image.
+struct SurfaceDesc {
+    int32_t d, T, nb;
+    int32_t type;            // 0: X checks (H_X rows), 1: Z checks (H_Z rows)
+    int32_t cyclic;
+    uint32_t nr, mr, d2;     // n_r, m_r, d^2
+    uint32_t mg_d, mg_d1, mg_nr, mg_mr;   // floor(2^32 / x) + 1 for exact x / divisor
+    int32_t mu_uniform;      // 1: mu is one value on data columns and one on measurement columns
+    float mu_data, mu_meas;
+};
+
 }  // namespace lbp
 
 struct lbp_code;
@@ -54,12 +70,14 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
                   void *ws, size_t ws_bytes, cudaStream_t stream);
 
 // Same, with an explicit BP launch shape (groups per CTA, threads per group;
-// 0, 0 = the code's tuned or default shape); when bp_ms is non-null the BP
-// kernel is timed with an event pair on `stream` (the call then waits).
+// 0, 0 = the code's tuned or default shape) and graph form (1 index image,
+// 2 implicit surface-code graph, 0 = tuned or default); when bp_ms is
+// non-null the BP kernel is timed with an event pair on `stream` (the call
+// then waits).
 int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                          uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                          void *ws, size_t ws_bytes, cudaStream_t stream, int groups, int G,
-                         float *bp_ms);
+                         float *bp_ms, int graph = 0);
 
 }  // namespace lbp
 
@@ -78,7 +96,13 @@ struct lbp_code {
     // 32-bit device copies, used by OSD.
     int32_t *d_row_ptr, *d_col_idx;
     float *d_mu;
+    // Implicit graph (Table III) when H is a recognised surface-code
+    // space-time matrix; d_mu_pad is mu[Np + 2] with +inf past n.
+    int surface;
+    lbp::SurfaceDesc surf;
+    float *d_mu_pad;
     // BP launch shape chosen by lbp_tune per message type (0 = not tuned):
     // groups per CTA and threads per group.
     int tuned_groups[6], tuned_G[6];   // per (rule, message type), lbp_tune
+    int tuned_graph[6];                // graph form chosen by lbp_tune (0 none, 1 image, 2 implicit)
 };

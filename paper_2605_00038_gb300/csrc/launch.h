@@ -12,6 +12,7 @@ struct LaunchShape {
     int grid, groups, G;
     size_t smem;
     bool graph_smem, state_smem, idx32;
+    bool surface;            // implicit surface-code graph (no index image)
 };
 
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);

@@ -5,6 +5,7 @@
 // Alg. 1 in binary64 and rounds it to binary32, and uploads a compact 16-bit
 // image of the whole Tanner graph that the decode kernels stage into shared
 // memory once per CTA.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -24,11 +25,96 @@ void release(lbp_code *c) {
     cudaSetDevice(c->device);
     cudaFree(c->d_image);
     cudaFree(c->d_ell);
+    cudaFree(c->d_mu_pad);
     cudaFree(c->d_row_ptr);
     cudaFree(c->d_col_idx);
     cudaFree(c->d_mu);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
+}
+
+uint32_t magic(uint32_t x) { return static_cast<uint32_t>((1ull << 32) / x + 1); }
+
+// Columns of check j of round t of the unrotated surface-code space-time
+// matrix, by the formulas of Table III (VN0..VN3 data, VN4 / VN5 measurement
+// blocks t-1 and t); absent neighbours are skipped.  Returns the count.
+int surface_row(const lbp::SurfaceDesc &s, uint32_t t, uint32_t j, uint32_t out[6]) {
+    int k = 0;
+    const uint32_t d = static_cast<uint32_t>(s.d), bd = t * s.nr;
+    if (s.type == 0) {
+        const uint32_t r = j / d, cc = j % d;
+        out[k++] = bd + j;
+        out[k++] = bd + j + d;
+        const uint32_t h = bd + s.d2 + r * (d - 1) + cc;
+        if (cc != 0) out[k++] = h - 1;
+        if (cc != d - 1) out[k++] = h;
+    } else {
+        const uint32_t r = j / (d - 1), cc = j % (d - 1);
+        out[k++] = bd + r * d + cc;
+        out[k++] = bd + r * d + cc + 1;
+        const uint32_t h = bd + s.d2 + r * (d - 1) + cc;
+        if (r != 0) out[k++] = h - (d - 1);
+        if (r != d - 1) out[k++] = h;
+    }
+    const uint32_t M0 = static_cast<uint32_t>(s.T) * s.nr;
+    int b4 = static_cast<int>(t) - 1;
+    if (b4 < 0 && s.cyclic) b4 = s.T - 1;
+    if (b4 >= 0 && b4 < s.nb) out[k++] = M0 + static_cast<uint32_t>(b4) * s.mr + j;
+    if (static_cast<int>(t) < s.nb) out[k++] = M0 + t * s.mr + j;
+    return k;
+}
+
+// Recognise H as the space-time matrix of Eq. 1 built from the H_X or H_Z
+// rows of Table III (open or cyclic time boundary, d >= 3) by regenerating
+// every row and comparing.  Fills *out and returns true on a match.
+bool detect_surface(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                    const std::vector<float> &mu, lbp::SurfaceDesc *out) {
+    for (int64_t d = 3; d * (d - 1) <= m; ++d) {
+        const int64_t mr = d * (d - 1), nr = d * d + (d - 1) * (d - 1);
+        if (m % mr) continue;
+        const int64_t T = m / mr;
+        for (int cyclic = 0; cyclic < 2; ++cyclic) {
+            if (cyclic && T < 2) continue;
+            const int64_t nb = cyclic ? T : T - 1;
+            if (T * nr + nb * mr != n) continue;
+            // Exact multiply-high division for every dividend the kernel divides.
+            if (static_cast<uint64_t>(n) * nr >= (1ull << 32) || static_cast<uint64_t>(m) * mr >= (1ull << 32))
+                continue;
+            for (int type = 0; type < 2; ++type) {
+                lbp::SurfaceDesc s;
+                std::memset(&s, 0, sizeof(s));
+                s.d = static_cast<int32_t>(d); s.T = static_cast<int32_t>(T); s.nb = static_cast<int32_t>(nb);
+                s.type = type; s.cyclic = cyclic;
+                s.nr = static_cast<uint32_t>(nr); s.mr = static_cast<uint32_t>(mr);
+                s.d2 = static_cast<uint32_t>(d * d);
+                bool ok = true;
+                uint32_t cols[6];
+                for (int32_t c = 0; c < m && ok; ++c) {
+                    const uint32_t t = static_cast<uint32_t>(c / mr), j = static_cast<uint32_t>(c % mr);
+                    const int k = surface_row(s, t, j, cols);
+                    std::sort(cols, cols + k);
+                    const int32_t a = row_ptr[c];
+                    if (row_ptr[c + 1] - a != k) { ok = false; break; }
+                    for (int i = 0; i < k; ++i)
+                        if (static_cast<uint32_t>(col_idx[a + i]) != cols[i]) { ok = false; break; }
+                }
+                if (!ok) continue;
+                s.mg_d = magic(static_cast<uint32_t>(d));
+                s.mg_d1 = magic(static_cast<uint32_t>(d - 1));
+                s.mg_nr = magic(s.nr);
+                s.mg_mr = magic(s.mr);
+                const int64_t M0 = T * nr;
+                s.mu_uniform = 1;
+                s.mu_data = n > 0 ? mu[0] : 0.0f;
+                s.mu_meas = nb > 0 ? mu[M0] : 0.0f;
+                for (int64_t v = 0; v < n && s.mu_uniform; ++v)
+                    if (mu[v] != (v < M0 ? s.mu_data : s.mu_meas)) s.mu_uniform = 0;
+                *out = s;
+                return true;
+            }
+        }
+    }
+    return false;
 }
 
 }  // namespace
@@ -195,6 +281,14 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         }
         for (int32_t v = 0; v < Np + 2; ++v) mu_e[v] = v < n ? mu[v] : INFINITY;
         rc = upload(reinterpret_cast<void **>(&c->d_ell), img.data(), off);
+        // Implicit graph: the same shape (DC = 6, DV = 2, Mp, Np, R = Mp + 2)
+        // with indices from Table III's formulas; priors that are not uniform
+        // per block are read from d_mu_pad.
+        if (rc == LBP_OK && ell_dc == 6 && ell_dv == 2 && detect_surface(m, n, row_ptr, col_idx, mu, &c->surf)) {
+            c->surface = 1;
+            if (!c->surf.mu_uniform)
+                rc = upload(reinterpret_cast<void **>(&c->d_mu_pad), mu_e, 4u * (Np + 2));
+        }
     }
     if (rc != LBP_OK) { release(c); return rc; }
     *out = c;
@@ -204,6 +298,17 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
 extern "C" int lbp_free_code(lbp_code *code) {
     if (!code) return LBP_EINVAL;
     release(code);
+    return LBP_OK;
+}
+
+extern "C" int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type,
+                                int32_t *cyclic) {
+    if (!code) return LBP_EINVAL;
+    const bool on = code->surface != 0;
+    if (d) *d = on ? code->surf.d : 0;
+    if (T) *T = on ? code->surf.T : 0;
+    if (type) *type = on ? code->surf.type : 0;
+    if (cyclic) *cyclic = on ? code->surf.cyclic : 0;
     return LBP_OK;
 }
 

@@ -46,7 +46,7 @@ int tuned_slot(int msg, int rule) {
 }
 
 struct BpPlan {
-    bool ell = false, graph_smem = true, state_smem = true, idx32 = false;
+    bool ell = false, graph_smem = true, state_smem = true, idx32 = false, surface = false;
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -89,9 +89,29 @@ int validate_params(const lbp_params *p) {
 
 // Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
 // group does not fit in shared memory.
+// Graph form of K_bp for a code with an implicit (Table III) graph: the
+// request (1 index image, 2 implicit), else LBP_GRAPH=table|implicit, else the
+// tuned form, else the image when it fits shared memory beside one shot's
+// state (evaluating the formulas costs more issue slots than the image's
+// shared-memory index loads) and the implicit graph when it does not (the
+// image would otherwise be read from L2 on every iteration).
+int graph_form(const lbp_code *c, int mi, int req_graph, size_t state_bytes) {
+    if (!c->surface) return 1;
+    if (req_graph == 1 || req_graph == 2) return req_graph;
+    if (const char *env = std::getenv("LBP_GRAPH")) {
+        if (!std::strcmp(env, "table")) return 1;
+        if (!std::strcmp(env, "implicit")) return 2;
+    }
+    if (c->tuned_graph[mi] == 1 || c->tuned_graph[mi] == 2) return c->tuned_graph[mi];
+    const bool image_fits = c->ell.idx_bytes == 2 &&
+                            c->ell.bytes + state_bytes <= static_cast<size_t>(c->smem_optin);
+    return image_fits ? 1 : 2;
+}
+
 int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out, int req_S = 0,
-            int req_G = 0) {
+            int req_G = 0, int req_graph = 0) {
     const int W32 = (c->m + 31) / 32;
+    const int mi = tuned_slot(msg, rule);
     BpPlan p;
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
     uint32_t off = 0;
@@ -103,6 +123,49 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     p.state_bytes = off;
     size_t image = c->ell.bytes;
     const size_t budget0 = static_cast<size_t>(c->smem_optin);
+    if (graph_form(c, mi, req_graph, off) == 2) {
+        // Implicit graph: nothing but the state in shared memory.
+        p.ell = true;
+        p.surface = true;
+        p.graph_smem = false;
+        p.state_smem = off <= budget0;
+        int S = 1, G = 1024;
+        if (p.state_smem) {
+            const int S_fit = static_cast<int>(budget0 / off);
+            if (S_fit >= 6) { G = 96; S = S_fit < 10 ? S_fit : 10; }
+            else if (S_fit >= 4) { G = 256; S = 4; }
+            else if (S_fit >= 2) { G = 512; S = 2; }
+            if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] == 2) {
+                G = c->tuned_G[mi];
+                S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
+            }
+            int s_req = req_S, g_req = req_G;
+            if (!g_req) {
+                if (const char *env = std::getenv("LBP_BP_SHAPE")) {
+                    if (std::sscanf(env, "%d,%d", &s_req, &g_req) != 2) s_req = g_req = 0;
+                }
+            }
+            if (g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 || g_req == 256 || g_req == 512 ||
+                g_req == 1024) {
+                G = g_req;
+                S = s_req > 0 && s_req < S_fit ? s_req : S_fit;
+            }
+            if (S * G > 1024) S = 1024 / G;
+            if (G > 32 && S > 15) S = 15;
+        } else {
+            G = req_G == 1024 ? 1024 : 512;
+            S = 1024 / G;
+        }
+        if (S < 1) S = 1;
+        p.groups = S;
+        p.G = G;
+        p.smem = p.state_smem ? static_cast<size_t>(S) * off : static_cast<size_t>(16) * S;
+        const int64_t need = (num_shots + S - 1) / S;
+        p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
+        if (p.grid < 1) p.grid = 1;
+        *out = p;
+        return LBP_OK;
+    }
     p.ell = c->d_ell != nullptr;
     p.idx32 = p.ell && c->ell.idx_bytes == 4;
     if (p.ell && (p.idx32 || image + off > budget0)) {
@@ -160,8 +223,7 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     int G = 32;
     while (G < 128 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
     if (p.ell && G == 128 && S_fit >= 6) G = 96;
-    const int mi = tuned_slot(msg, rule);
-    if (c->tuned_G[mi] > 0) {
+    if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] != 2) {
         G = c->tuned_G[mi];
         S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
     }
@@ -326,9 +388,9 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
 int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                          uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                          void *ws, size_t ws_bytes, cudaStream_t stream, int req_S, int req_G,
-                         float *bp_ms) {
+                         float *bp_ms, int req_graph) {
     BpPlan bp;
-    int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G);
+    int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G, req_graph);
     if (rc) return rc;
     OsdPlan op;
     OsdWarpPlan wp;
@@ -387,7 +449,10 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
-        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32};
+        e.surf = c->surf;
+        e.mu_tab = c->d_mu_pad;
+        const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32,
+                              bp.surface};
         const bool sp = prm->rule == LBP_RULE_SUM_PRODUCT;
         switch (prm->msg) {
             case LBP_MSG_F32:
@@ -594,27 +659,34 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     const int mi = tuned_slot(params->msg, params->rule);
     code->tuned_G[mi] = 0;
     code->tuned_groups[mi] = 0;
+    code->tuned_graph[mi] = 0;
     const int Gs[] = {32, 64, 96, 128, 192, 256, 512, 1024};
     float best = -1.0f;
-    int best_S = 0, best_G = 0;
-    for (int G : Gs) {
-        BpPlan probe;
-        if (plan_bp(code, params->msg, params->rule, num_shots, &probe, 1024, G) != LBP_OK) continue;
-        if (probe.G != G) continue;                    // shape not available for this code
-        const int S = probe.groups;
-        float ms = 0.0f, warm = 0.0f;
-        rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
-                                       iters_out, nullptr, workspace, workspace_bytes, s, S, G, &warm);
-        if (rc == LBP_ENOMEM || rc == LBP_ENOSYS) continue;   // candidate does not fit: skip it
-        if (rc) return rc;
-        rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
-                                       iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms);
-        if (rc) return rc;
-        if (ms > 0.0f && (best < 0.0f || ms < best)) { best = ms; best_S = S; best_G = G; }
+    int best_S = 0, best_G = 0, best_graph = 0;
+    // Candidates: every thread count, with the index image and, for a
+    // recognised surface code, with the implicit graph.
+    for (int graph = 1; graph <= (code->surface ? 2 : 1); ++graph) {
+        for (int G : Gs) {
+            BpPlan probe;
+            if (plan_bp(code, params->msg, params->rule, num_shots, &probe, 1024, G, graph) != LBP_OK) continue;
+            if (probe.G != G) continue;                    // shape not available for this code
+            const int S = probe.groups;
+            float ms = 0.0f, warm = 0.0f;
+            rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                           iters_out, nullptr, workspace, workspace_bytes, s, S, G, &warm,
+                                           graph);
+            if (rc == LBP_ENOMEM || rc == LBP_ENOSYS) continue;   // candidate does not fit: skip it
+            if (rc) return rc;
+            rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                           iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms, graph);
+            if (rc) return rc;
+            if (ms > 0.0f && (best < 0.0f || ms < best)) { best = ms; best_S = S; best_G = G; best_graph = graph; }
+        }
     }
     if (best_G > 0) {
         code->tuned_G[mi] = best_G;
         code->tuned_groups[mi] = best_S;
+        code->tuned_graph[mi] = best_graph;
     } else {
         // No candidate ran: decode once with the default shape so the outputs
         // are lbp_decode's (or report why it cannot run).

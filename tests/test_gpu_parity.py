@@ -155,12 +155,14 @@ def test_lottery_baseline_policies(policy):
 
 
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
-def test_d27_table2_spacetime_32bit_image(msg):
+@pytest.mark.parametrize("form", ["table", "implicit"])
+def test_d27_table2_spacetime_32bit_image(msg, form, monkeypatch):
     """The d=27 space-time matrix in the exact form whose size Table II prints
     (unrotated code, cyclic time boundary: 18,954 x 56,889, nnz 112,320): its
-    message offsets exceed 16 bits, so the kernel uses the 32-bit image from
-    global memory."""
+    message offsets exceed 16 bits, so the image path uses the 32-bit image
+    from global memory; the implicit path (Table III formulas) reads none."""
     from paper_2605_00038_gb300.inputs.codes import unrotated_surface
+    monkeypatch.setenv("LBP_GRAPH", form)
     _, hz = unrotated_surface(27)
     st = spacetime(hz, 27, "cyclic")
     assert (st.n, st.nnz) == (56889, 112320)
