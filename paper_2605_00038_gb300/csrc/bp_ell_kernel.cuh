@@ -41,6 +41,7 @@
 
 #include "bp_common.cuh"
 #include "bp_graph.cuh"
+#include "bp_lottery.cuh"
 #include "internal.h"
 
 namespace lbp {
@@ -266,131 +267,9 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             // ---- lottery (Alg. 3, or a baseline policy of Sec. III-B) ---------
             if (a.lottery && it >= a.lottery_skip && it < I - 1) {
                 if (t < 32) {
-                    const uint32_t *sp = shat + prev * W32;
-                    uint32_t N = 0;
-                    for (int w0 = 0; w0 < W32; w0 += 32) {
-                        const int w = w0 + lane;
-                        const uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
-                        uint32_t pc = __popc(word);
-                        #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
-                        N += pc;
-                    }
-                    if (N > 0) {
-                        const uint64_t g = a.shot_offset + b;
-                        const uint64_t r64 = splitmix64_at(a.seed, (g << 24) + static_cast<uint64_t>(it));
-                        const uint32_t u = static_cast<uint32_t>(r64), u2 = static_cast<uint32_t>(r64 >> 32);
-                        int cstar = -1;
-                        if (a.policy == LBP_LOTTERY_WORST_UNRELIABLE || a.policy == LBP_LOTTERY_WORST_RANDOM) {
-                            // Worst CN: most columns estimated in error, lowest row on ties.
-                            int bn = -1, bcr = 0x7fffffff;
-                            for (int w = lane; w < W32; w += 32) {
-                                uint32_t word = sp[w] ^ s_w[w];
-                                while (word) {
-                                    const int c = w * 32 + __ffs(word) - 1;
-                                    word &= word - 1u;
-                                    int ne = 0;
-                                    #pragma unroll
-                                    uint32_t vv[DC], unused[DC];
-                                    gr.cols2(c >> 1, vv, unused);
-                                    if (c & 1) {
-                                        #pragma unroll
-                                        for (int k = 0; k < DC; ++k) vv[k] = unused[k];
-                                    }
-                                    #pragma unroll
-                                    for (int k = 0; k < DC; ++k) {
-                                        const uint32_t v = vv[k];
-                                        ne += (v < static_cast<uint32_t>(n) && lam[v] <= 0.0f) ? 1 : 0;
-                                    }
-                                    if (ne > bn || (ne == bn && c < bcr)) { bn = ne; bcr = c; }
-                                }
-                            }
-                            #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                const int on = __shfl_xor_sync(0xffffffffu, bn, o);
-                                const int oc = __shfl_xor_sync(0xffffffffu, bcr, o);
-                                if (on > bn || (on == bn && oc < bcr)) { bn = on; bcr = oc; }
-                            }
-                            cstar = bcr;
-                        } else {
-                            // Random CN: member k = floor(u N / 2^32) of U, ascending rows.
-                            const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(u) * N) >> 32);
-                            uint32_t base = 0;
-                            for (int w0 = 0; w0 < W32 && cstar < 0; w0 += 32) {
-                                const int w = w0 + lane;
-                                uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
-                                const uint32_t pc = __popc(word);
-                                uint32_t incl = pc;
-                                #pragma unroll
-                                for (int o = 1; o < 32; o <<= 1) {
-                                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                                    if (lane >= o) incl += y;
-                                }
-                                const uint32_t excl = incl - pc;
-                                const bool mine = (k >= base + excl) && (k < base + incl);
-                                const unsigned own = __ballot_sync(0xffffffffu, mine);
-                                if (own) {
-                                    int pick = 0;
-                                    if (mine) {
-                                        uint32_t rr = k - base - excl;
-                                        while (rr--) word &= word - 1u;
-                                        pick = w * 32 + (__ffs(word) - 1);
-                                    }
-                                    cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
-                                }
-                                base += __shfl_sync(0xffffffffu, incl, 31);
-                            }
-                        }
-                        int bc = -1, bv = 0x7fffffff;
-                        float ba = 0.0f;
-                        // Lane k < DC holds slot k of c* (n when absent).
-                        const int vl = lane < DC ? static_cast<int>(gr.col(lane, cstar)) : n;
-                        if (a.policy == LBP_LOTTERY_WORST_RANDOM || a.policy == LBP_LOTTERY_RANDOM_RANDOM) {
-                            // Random VN: column floor(u2 deg / 2^32) of c* in ascending
-                            // order (rank of each present column among the slots).
-                            const bool present = lane < DC && vl < n;
-                            const int deg = __popc(__ballot_sync(0xffffffffu, present));
-                            const int kk = static_cast<int>((static_cast<uint64_t>(u2) * static_cast<uint32_t>(deg)) >> 32);
-                            int rank = 0;
-                            #pragma unroll
-                            for (int o = 0; o < DC; ++o) {
-                                const int w = __shfl_sync(0xffffffffu, vl, o);
-                                rank += (w < vl) ? 1 : 0;
-                            }
-                            const unsigned pick = __ballot_sync(0xffffffffu, present && rank == kk);
-                            bv = __shfl_sync(0xffffffffu, vl, __ffs(pick) - 1);
-                            bc = 0;
-                        } else {
-                            // Unreliable VN (the proposed rule first prefers the column
-                            // with the most unsatisfied checks), then lowest column.
-                            if (lane < DC) {
-                                const int v = vl;
-                                if (v < n) {
-                                    bv = v;
-                                    bc = 0;
-                                    if (a.policy == LBP_LOTTERY_PROPOSED) {
-                                        #pragma unroll
-                                        for (int kk = 0; kk < DV; ++kk) {
-                                            const unsigned o = gr.ent(kk, v);
-                                            const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
-                                            if (r < static_cast<unsigned>(m))
-                                                bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
-                                        }
-                                    }
-                                    ba = fabsf(lam[v]);
-                                }
-                            }
-                            #pragma unroll
-                            for (int o = 4; o > 0; o >>= 1) {
-                                const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
-                                const float oa = __shfl_xor_sync(0xffffffffu, ba, o);
-                                const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                                const bool better = oc > bc || (oc == bc && (oa < ba || (oa == ba && ov < bv)));
-                                if (better) { bc = oc; ba = oa; bv = ov; }
-                            }
-                        }
-                        if (lane == 0 && bc >= 0) lam[bv] = -lam[bv];
-                    }
+                    const int vs = lottery_pick<DC, DV>(gr, shat + prev * W32, s_w, W32, lane, a.seed,
+                                                        a.shot_offset + b, it, a.policy, lam, m, R, a.magic);
+                    if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
                 }
                 group_sync<G>(bar);
             }

@@ -49,9 +49,12 @@ struct EllGraph {
     const float *mu_;
     const float2 *mu2_;
     int Mp, Np, mpairs, npairs;
+    uint32_t pad;            // column id of absent neighbours (n)
+    static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
 
     __device__ __forceinline__ EllGraph(const EllImage &img, const uint8_t *gbase, const SurfaceDesc &,
-                                        const float *, int, int) {
+                                        const float *, int, int n_) {
+        pad = static_cast<uint32_t>(n_);
         cidx = reinterpret_cast<const IdxT *>(gbase + img.off_cidx);
         cidx2 = reinterpret_cast<const IP *>(cidx);
         vent = reinterpret_cast<const IdxT *>(gbase + img.off_vent);
@@ -83,6 +86,7 @@ struct EllGraph {
     }
     __device__ __forceinline__ uint32_t col(int k, int c) const { return cidx[k * Mp + c]; }
     __device__ __forceinline__ uint32_t ent(int k, int v) const { return vent[k * Np + v]; }
+    __device__ __forceinline__ uint32_t orig(uint32_t v) const { return v; }
     __device__ __forceinline__ float mu(uint32_t v) const { return mu_[v]; }
     __device__ __forceinline__ float2 mu2(int q) const { return mu2_[q]; }
 };
@@ -94,12 +98,14 @@ struct SurfaceGraph {
     SurfaceDesc s;
     const float *mu_tab;     // mu[Np + 2] (global) when mu is not uniform per block
     uint32_t m, n, Mp, R, M0;
+    uint32_t pad;            // column id of absent neighbours (n)
+    static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
 
     __device__ __forceinline__ SurfaceGraph(const EllImage &img, const uint8_t *, const SurfaceDesc &sd,
                                             const float *mt, int m_, int n_)
         : s(sd), mu_tab(mt), m(static_cast<uint32_t>(m_)), n(static_cast<uint32_t>(n_)),
           Mp(static_cast<uint32_t>(img.Mp)), R(static_cast<uint32_t>(img.Mp) + 2u),
-          M0(static_cast<uint32_t>(sd.T) * sd.nr) {}
+          M0(static_cast<uint32_t>(sd.T) * sd.nr), pad(static_cast<uint32_t>(n_)) {}
 
     // Table III: the six neighbours of check c = t m_r + j (absent ones = n).
     __device__ __forceinline__ void cols(uint32_t c, uint32_t (&v)[DC]) const {
@@ -195,6 +201,7 @@ struct SurfaceGraph {
         ents(static_cast<uint32_t>(v), o);
         return k == 0 ? o[0] : o[1];
     }
+    __device__ __forceinline__ uint32_t orig(uint32_t v) const { return v; }
     __device__ __forceinline__ float mu(uint32_t v) const {
         if (v >= n) return __int_as_float(0x7f800000);
         if (s.mu_uniform) return v < M0 ? s.mu_data : s.mu_meas;

@@ -1,0 +1,145 @@
+// The lottery (Alg. 3) and the four baseline sign-flip policies of Sec. III-B,
+// shared by the BP kernels.  Run by the 32 lanes of a group's first warp after
+// the termination test of iteration `it`; returns the stored index of the
+// column whose LLR is to be negated (v*), the same in every lane, or -1 when
+// no check is unsatisfied.
+//
+//   U   = s_hat(i-1) xor s (bit words sp ^ s_w); N = |U|
+//   u   = SplitMix64(seed, (g << 24) + i): low 32 bits choose the check,
+//         high 32 bits the column of the random-VN policies
+//   CN  random: the k-th member of U in ascending row order, k = floor(u N / 2^32);
+//       worst:  the member with the most columns at lambda <= 0, lowest row on ties
+//   VN  proposed: most unsatisfied checks, then least |lambda|, then lowest column;
+//       unreliable: least |lambda|, then lowest column;
+//       random: column floor(u2 deg / 2^32) of c* in ascending column order.
+//
+// Acc gives the graph as the kernel stores it: col(k, c) is the stored index
+// of check c's slot-k column (acc.pad when absent), ent(k, v) the message
+// offset slot * R + check of stored column v's k-th check (absent checks:
+// an offset whose row is not a check, or one at or past acc.ent_end), orig(v)
+// the column id in H (ties are broken on it).
+#pragma once
+
+#include <cstdint>
+
+#include "bp_common.cuh"
+
+namespace lbp {
+
+template <int DC, int DV, typename Acc>
+__device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, const uint32_t *s_w, int W32,
+                                            int lane, uint64_t seed, uint64_t g, int it, int policy,
+                                            const float *lam, int m, int R, uint32_t magic) {
+    uint32_t N = 0;
+    for (int w0 = 0; w0 < W32; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
+        uint32_t pc = __popc(word);
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
+        N += pc;
+    }
+    if (N == 0) return -1;
+    const uint64_t r64 = splitmix64_at(seed, (g << 24) + static_cast<uint64_t>(it));
+    const uint32_t u = static_cast<uint32_t>(r64), u2 = static_cast<uint32_t>(r64 >> 32);
+    int cstar = -1;
+    if (policy == LBP_LOTTERY_WORST_UNRELIABLE || policy == LBP_LOTTERY_WORST_RANDOM) {
+        int bn = -1, bcr = 0x7fffffff;
+        for (int w = lane; w < W32; w += 32) {
+            uint32_t word = sp[w] ^ s_w[w];
+            while (word) {
+                const int c = w * 32 + __ffs(word) - 1;
+                word &= word - 1u;
+                int ne = 0;
+                #pragma unroll
+                for (int k = 0; k < DC; ++k) {
+                    const uint32_t v = acc.col(k, c);
+                    ne += (v != acc.pad && lam[v] <= 0.0f) ? 1 : 0;
+                }
+                if (ne > bn || (ne == bn && c < bcr)) { bn = ne; bcr = c; }
+            }
+        }
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int on = __shfl_xor_sync(0xffffffffu, bn, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, bcr, o);
+            if (on > bn || (on == bn && oc < bcr)) { bn = on; bcr = oc; }
+        }
+        cstar = bcr;
+    } else {
+        const uint32_t k = static_cast<uint32_t>((static_cast<uint64_t>(u) * N) >> 32);
+        uint32_t base = 0;
+        for (int w0 = 0; w0 < W32 && cstar < 0; w0 += 32) {
+            const int w = w0 + lane;
+            uint32_t word = (w < W32) ? (sp[w] ^ s_w[w]) : 0u;
+            const uint32_t pc = __popc(word);
+            uint32_t incl = pc;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - pc;
+            const bool mine = (k >= base + excl) && (k < base + incl);
+            const unsigned own = __ballot_sync(0xffffffffu, mine);
+            if (own) {
+                int pick = 0;
+                if (mine) {
+                    uint32_t rr = k - base - excl;
+                    while (rr--) word &= word - 1u;
+                    pick = w * 32 + (__ffs(word) - 1);
+                }
+                cstar = __shfl_sync(0xffffffffu, pick, __ffs(own) - 1);
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    // Lane k < DC holds slot k of c*; ov is its column id in H (ties, order).
+    const uint32_t vl = lane < DC ? acc.col(lane, cstar) : acc.pad;
+    const bool present = vl != acc.pad;
+    const uint32_t ov = present ? acc.orig(vl) : 0xffffffffu;
+    if (policy == LBP_LOTTERY_WORST_RANDOM || policy == LBP_LOTTERY_RANDOM_RANDOM) {
+        const int deg = __popc(__ballot_sync(0xffffffffu, present));
+        const int kk = static_cast<int>((static_cast<uint64_t>(u2) * static_cast<uint32_t>(deg)) >> 32);
+        int rank = 0;
+        #pragma unroll
+        for (int o = 0; o < DC; ++o) {
+            const uint32_t w = __shfl_sync(0xffffffffu, ov, o);
+            rank += (w < ov) ? 1 : 0;
+        }
+        const unsigned pick = __ballot_sync(0xffffffffu, present && rank == kk);
+        return static_cast<int>(__shfl_sync(0xffffffffu, vl, __ffs(pick) - 1));
+    }
+    int bc = -1;
+    float ba = 0.0f;
+    uint32_t bo = 0xffffffffu, bv = acc.pad;
+    if (present) {
+        bv = vl;
+        bo = ov;
+        bc = 0;
+        if (policy == LBP_LOTTERY_PROPOSED) {
+            #pragma unroll
+            for (int kk = 0; kk < DV; ++kk) {
+                const uint32_t o = acc.ent(kk, vl);
+                const uint32_t r = o - __umulhi(o, magic) * static_cast<uint32_t>(R);
+                if (o < acc.ent_end && r < static_cast<uint32_t>(m))
+                    bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;
+            }
+        }
+        ba = fabsf(lam[vl]);
+    }
+    #pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const float oa = __shfl_xor_sync(0xffffffffu, ba, o);
+        const uint32_t oo = __shfl_xor_sync(0xffffffffu, bo, o);
+        const uint32_t ovv = __shfl_xor_sync(0xffffffffu, bv, o);
+        const bool better = oc > bc || (oc == bc && (oa < ba || (oa == ba && oo < bo)));
+        if (better) { bc = oc; ba = oa; bo = oo; bv = ovv; }
+    }
+    bv = __shfl_sync(0xffffffffu, bv, 0);
+    bc = __shfl_sync(0xffffffffu, bc, 0);
+    return bc >= 0 ? static_cast<int>(bv) : -1;
+}
+
+}  // namespace lbp
