@@ -61,9 +61,9 @@ struct OsdPlan {
 
 struct OsdWarpPlan {
     bool ok = false;
-    int warps = 0, grid = 0, C = 0, wn = 0, m_pad = 1;
-    uint32_t image = 0, region = 0, off_keys = 0, off_rflag = 0, off_pivk = 0, off_pivb = 0,
-             off_saug = 0, off_x = 0, off_pcol = 0, off_prow = 0, off_pend = 0;
+    int warps = 0, grid = 0, C = 0, wn = 0;
+    uint32_t image = 0, region = 0, off_keys = 0, off_tmp = 0, off_hist = 0, off_rflag = 0, off_pivk = 0,
+             off_pivb = 0, off_saug = 0, off_x = 0, off_pcol = 0, off_prow = 0, off_pend = 0;
     size_t smem = 0;
 };
 
@@ -280,7 +280,6 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     OsdWarpPlan p;
     if (!c->d_image || c->m < 1 || c->n < 1) { *out = p; return; }
     p.wn = (c->n + 63) / 64;
-    while (p.m_pad < c->m) p.m_pad <<= 1;
     p.C = c->m < 192 ? c->m : 192;
     if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
         const int v = std::atoi(env);
@@ -288,14 +287,20 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     }
     const int W32 = (c->m + 31) / 32;
     uint32_t off = 0;
-    p.off_keys = off;  off = align16u(off + 8u * p.m_pad);
-    p.off_rflag = off; off = align16u(off + 2u * c->m);
+    p.off_keys = off;  off = align16u(off + 8u * c->m);
+    // The radix sort's buffer shares its bytes with the pivot arrays, which
+    // are first written after the sort.
+    const uint32_t u0 = off;
+    p.off_tmp = u0;
     p.off_pivk = off;  off = align16u(off + 2u * c->n);
+    p.off_pcol = off;  off = align16u(off + 2u * c->m);
+    p.off_prow = off;  off = align16u(off + 2u * c->m);
+    if (off < u0 + align16u(8u * c->m)) off = u0 + align16u(8u * c->m);
+    p.off_hist = off;  off = align16u(off + 4u * 256);
+    p.off_rflag = off; off = align16u(off + 2u * c->m);
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);
     p.off_x = off;     off = align16u(off + 8u * p.wn);
-    p.off_pcol = off;  off = align16u(off + 2u * c->m);
-    p.off_prow = off;  off = align16u(off + 2u * c->m);
     p.off_pend = off;  off = align16u(off + 8u * p.C);
     p.region = off;
     p.image = c->img.off_col_ptr;             // row_ptr and col_idx only
@@ -489,7 +494,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             std::memset(&ow, 0, sizeof(ow));
             ow.image = c->d_image;
             ow.img = c->img;
-            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.m_pad = wp.m_pad; ow.C = wp.C;
+            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.C = wp.C;
             ow.syn = syn; ow.err = err; ow.osd_out = osd_out;
             ow.counters = counters;
             ow.osd_list = a.osd_list; ow.osd_llr = a.osd_llr;
@@ -498,6 +503,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             ow.image_bytes = wp.image;
             ow.region_bytes = wp.region;
             ow.off_keys = wp.off_keys; ow.off_rflag = wp.off_rflag; ow.off_pivk = wp.off_pivk;
+            ow.off_tmp = wp.off_tmp; ow.off_hist = wp.off_hist;
             ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
             ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
             rc = set_smem(osd_warp_kernel<kOsdMaxWarps>, wp.smem);

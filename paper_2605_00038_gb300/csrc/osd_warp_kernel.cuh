@@ -16,8 +16,10 @@
 //    included, then waits for its next event.  Columns where no row meets are
 //    dependent on earlier ones and skipped.  So the scan costs one event per
 //    row plus one per elimination, not one step per column.
-//  * Rows are sorted once by their first key (warp bitonic sort of
-//    (K, row) pairs).  Runs of events that concern a single row, with no
+//  * Rows are sorted once by their first key: a stable LSD radix sort of
+//    the 48 key bits of (K, row) pairs, 8 bits per pass, ranks within a warp
+//    step from __match_any_sync (rows with equal K are one event, so their
+//    order does not matter).  Runs of events that concern a single row, with no
 //    changed row waiting at or before them, commit 32 at a time: each lane's
 //    row becomes the pivot of its column.  Events with several rows are
 //    handled one at a time.
@@ -43,7 +45,7 @@ namespace lbp {
 struct OsdWarpArgs {
     const uint8_t *image;          // CSR image (GraphImage layout); only row_ptr / col_idx are read
     GraphImage img;
-    int32_t m, n, wn, m_pad, C;
+    int32_t m, n, wn, C;
     const uint64_t *syn;
     uint64_t *err;
     uint8_t *osd_out;
@@ -54,7 +56,8 @@ struct OsdWarpArgs {
     uint64_t *slots;               // [total warps][C][wn] dense rows
     uint32_t image_bytes;          // bytes of the image prefix staged (row_ptr + col_idx)
     uint32_t region_bytes;         // per-warp shared memory
-    uint32_t off_keys, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow, off_pend;
+    uint32_t off_keys, off_tmp, off_hist, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow,
+        off_pend;             // off_tmp (radix sort buffer) overlaps pivk / pcol / prow
 };
 
 constexpr uint64_t kNoKey = ~0ull;
@@ -93,7 +96,9 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
     const int total = gridDim.x * (blockDim.x >> 5);
     uint8_t *reg = smem + a.image_bytes + static_cast<size_t>(wid) * a.region_bytes;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(reg + a.off_keys);     // [m_pad] (K << 16 | row)
+    uint64_t *keys = reinterpret_cast<uint64_t *>(reg + a.off_keys);     // [m] (K << 16 | row)
+    uint64_t *tmp = reinterpret_cast<uint64_t *>(reg + a.off_tmp);       // [m] sort buffer
+    uint32_t *hist = reinterpret_cast<uint32_t *>(reg + a.off_hist);     // [256] digit counts
     uint16_t *rflag = reinterpret_cast<uint16_t *>(reg + a.off_rflag);   // [m] dense slot or 0xffff
     uint16_t *pivk = reinterpret_cast<uint16_t *>(reg + a.off_pivk);     // [n] pivot index of column
     uint32_t *pivb = reinterpret_cast<uint32_t *>(reg + a.off_pivb);     // [W32] row is a pivot
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     uint64_t *pend = reinterpret_cast<uint64_t *>(reg + a.off_pend);     // [C] waiting changed rows
     uint64_t *slots = a.slots + static_cast<size_t>(gw) * a.C * a.wn;
 
-    const int m = a.m, n = a.n, wn = a.wn, C = a.C, m_pad = a.m_pad;
+    const int m = a.m, n = a.n, wn = a.wn, C = a.C;
     const int W32 = (m + 31) >> 5;
     const int wm64 = (m + 63) >> 6;
     const uint32_t queue = a.counters[1];
@@ -115,19 +120,16 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
         const float *lam = a.osd_llr + static_cast<size_t>(q) * n;
 
         // ---- rows keyed by their first column, sorted -----------------------
-        for (int r = lane; r < m_pad; r += 32) {
+        for (int r = lane; r < m; r += 32) {
             uint64_t k = kNoKey;
-            if (r < m) {
-                for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-                    const uint64_t kc = col_key(lam, col_idx[e]);
-                    k = kc < k ? kc : k;
-                }
-                if (k != kNoKey) k = (k << 16) | static_cast<uint32_t>(r);
+            for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                const uint64_t kc = col_key(lam, col_idx[e]);
+                k = kc < k ? kc : k;
             }
+            if (k != kNoKey) k = (k << 16) | static_cast<uint32_t>(r);
             keys[r] = k;
+            rflag[r] = 0xffffu;
         }
-        for (int r = lane; r < m; r += 32) rflag[r] = 0xffffu;
-        for (int v = lane; v < n; v += 32) pivk[v] = 0xffffu;
         const uint32_t *sp = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
         for (int w = lane; w < W32; w += 32) {
             uint32_t x = sp[w];
@@ -137,18 +139,56 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
         }
         for (int w = lane; w < wn; w += 32) X[w] = 0ull;
         __syncwarp();
-        for (int k = 2; k <= m_pad; k <<= 1) {
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int i = lane; i < m_pad; i += 32) {
-                    const int l = i ^ jj;
-                    if (l > i) {
-                        const uint64_t x = keys[i], y = keys[l];
-                        if ((x > y) == ((i & k) == 0)) { keys[i] = y; keys[l] = x; }
-                    }
+        // Stable LSD radix sort of keys[0, m) on bits 16..63, 8 bits a pass;
+        // six passes leave the result in keys.
+        for (int pass = 0; pass < 6; ++pass) {
+            const uint64_t *src = (pass & 1) ? tmp : keys;
+            uint64_t *dst = (pass & 1) ? keys : tmp;
+            const int sh = 16 + 8 * pass;
+            for (int d = lane; d < 256; d += 32) hist[d] = 0u;
+            __syncwarp();
+            for (int j0 = 0; j0 < m; j0 += 32) {
+                const int i = j0 + lane;
+                const unsigned act = __ballot_sync(0xffffffffu, i < m);
+                if (i < m) {
+                    const unsigned dg = static_cast<unsigned>(src[i] >> sh) & 255u;
+                    const unsigned peers = __match_any_sync(act, dg);
+                    if (lane == __ffs(peers) - 1) hist[dg] += __popc(peers);
+                }
+                __syncwarp();
+            }
+            // Exclusive prefix over the 256 counts: 8 per lane, then across lanes.
+            uint32_t c8[8], tot = 0;
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) { c8[j] = hist[lane * 8 + j]; tot += c8[j]; }
+            uint32_t incl = tot;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t run = incl - tot;
+            __syncwarp();
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) { hist[lane * 8 + j] = run; run += c8[j]; }
+            __syncwarp();
+            for (int j0 = 0; j0 < m; j0 += 32) {
+                const int i = j0 + lane;
+                const unsigned act = __ballot_sync(0xffffffffu, i < m);
+                if (i < m) {
+                    const uint64_t x = src[i];
+                    const unsigned dg = static_cast<unsigned>(x >> sh) & 255u;
+                    const unsigned peers = __match_any_sync(act, dg);
+                    const unsigned before = __popc(peers & ((1u << lane) - 1u));
+                    dst[hist[dg] + before] = x;
+                    __syncwarp(act);
+                    if (lane == __ffs(peers) - 1) hist[dg] += __popc(peers);
                 }
                 __syncwarp();
             }
         }
+        for (int v = lane; v < n; v += 32) pivk[v] = 0xffffu;      // tmp is dead from here on
+        __syncwarp();
 
         // ---- forward elimination, event by event ------------------------------
         int ptr = 0, rank = 0, npend = 0, nslots = 0;
@@ -156,13 +196,13 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
         bool overflow = false;
         while (!overflow) {
             const int i = ptr + lane;
-            const uint64_t ki = (i < m_pad) ? keys[i] : kNoKey;
+            const uint64_t ki = (i < m) ? keys[i] : kNoKey;
             const uint64_t Ki = ki == kNoKey ? kNoKey : (ki >> 16);
             uint64_t Kprev = __shfl_up_sync(0xffffffffu, Ki, 1);
             if (lane == 0) Kprev = (ptr > 0) ? (keys[ptr - 1] >> 16) : kNoKey - 1;
             uint64_t Knext = __shfl_down_sync(0xffffffffu, Ki, 1);
             if (lane == 31) {
-                const uint64_t kn = (i + 1 < m_pad) ? keys[i + 1] : kNoKey;
+                const uint64_t kn = (i + 1 < m) ? keys[i + 1] : kNoKey;
                 Knext = kn == kNoKey ? kNoKey : (kn >> 16);
             }
             const bool single = Ki != kNoKey && Ki != Kprev && Ki != Knext &&
@@ -192,7 +232,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             int nsorted = 0;
             while (true) {
                 const int j = ptr + nsorted + lane;
-                const uint64_t kj = (j < m_pad) ? keys[j] : kNoKey;
+                const uint64_t kj = (j < m) ? keys[j] : kNoKey;
                 const bool eq = kj != kNoKey && (kj >> 16) == Kev;
                 const unsigned bal = __ballot_sync(0xffffffffu, eq);
                 const int run = (~bal) ? __ffs(~bal) - 1 : 32;
