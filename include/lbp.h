@@ -143,11 +143,12 @@ int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type
  * only when params->osd is set (the LLRs of shots handed to OSD).
  *
  * Tuning: OSD keeps rows of H sparse until an elimination changes them; the
- * changed rows take dense copies from a per-warp pool of min(m, 192) rows.
- * The environment variable LBP_OSD_POOL_ROWS (read at every call) lowers that
- * bound; a shot that needs more rows is solved by the block-wide OSD kernel
- * instead, with the same result.  Set it identically for lbp_workspace_size
- * and lbp_decode. */
+ * changed rows take dense copies from a per-warp pool of C rows, by default
+ * max(192, m / 2) (at most m), lowered so that the pools of all warps stay
+ * within 1 GiB but never below min(m, 192).  The environment variable
+ * LBP_OSD_POOL_ROWS (read at every call) sets C (1..m); a shot that needs
+ * more rows is solved by the block-wide OSD kernel instead, with the same
+ * result.  Set it identically for lbp_workspace_size and lbp_decode. */
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).

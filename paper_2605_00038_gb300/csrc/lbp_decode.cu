@@ -280,11 +280,6 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     OsdWarpPlan p;
     if (!c->d_image || c->m < 1 || c->n < 1) { *out = p; return; }
     p.wn = (c->n + 63) / 64;
-    p.C = c->m < 192 ? c->m : 192;
-    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
-        const int v = std::atoi(env);
-        if (v > 0 && v < p.C) p.C = v;
-    }
     const int W32 = (c->m + 31) / 32;
     uint32_t off = 0;
     p.off_keys = off;  off = align16u(off + 8u * c->m);
@@ -301,13 +296,34 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);
     p.off_x = off;     off = align16u(off + 8u * p.wn);
-    p.off_pend = off;  off = align16u(off + 8u * p.C);
-    p.region = off;
+    p.off_pend = off;
     p.image = c->img.off_col_ptr;             // row_ptr and col_idx only
     const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
+    auto warps_for = [&](int C) {
+        const size_t region = align16u(p.off_pend + 8u * C);
+        const size_t w = budget / region;
+        return static_cast<int>(w < kOsdMaxWarps ? w : kOsdMaxWarps);
+    };
+    // Pool rows C (changed rows a shot may hold before it is handed to
+    // K_osd): half of m, at least 192, with the pool at most 1 GiB of
+    // workspace; LBP_OSD_POOL_ROWS overrides.  Codes whose elimination
+    // changes many rows (the unrotated d=11 space-time code needs ~450 at
+    // p = 0.003) would otherwise send a quarter of their OSD shots to K_osd.
+    int C = c->m / 2 > 192 ? c->m / 2 : 192;
+    if (C > c->m) C = c->m;
+    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
+        const int v = std::atoi(env);
+        if (v > 0 && v <= c->m) C = v;
+    } else if (warps_for(C) >= 1) {
+        const size_t per_row = static_cast<size_t>(c->sm_count) * warps_for(C) * p.wn * 8u;
+        const size_t cap = (static_cast<size_t>(1) << 30) / per_row;
+        const int floor_c = c->m < 192 ? c->m : 192;
+        if (static_cast<size_t>(C) > cap) C = cap > static_cast<size_t>(floor_c) ? static_cast<int>(cap) : floor_c;
+    }
+    p.C = C;
+    p.region = align16u(p.off_pend + 8u * C);
     if (static_cast<size_t>(p.region) * 2 > budget) { *out = p; return; }
-    p.warps = static_cast<int>(budget / p.region);
-    if (p.warps > kOsdMaxWarps) p.warps = kOsdMaxWarps;
+    p.warps = warps_for(C);
     p.smem = p.image + static_cast<size_t>(p.warps) * p.region;
     const int64_t need = (num_shots + p.warps - 1) / p.warps;
     p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
