@@ -195,6 +195,14 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         int it = 0;
         for (; it < I; ++it) {
             const float f = scale_at(a.scale_mode, a.scale_const, it);
+            const bool lot = a.lottery && it >= a.lottery_skip && it < I - 1;
+            // The group's last warp (the least loaded in both phases) runs the
+            // lottery; a random check is drawn while the other warps finish
+            // their check-phase rounds.
+            const bool lw = t >= G - 32;
+            const bool early = lottery_random_check(a.policy);
+            int cpre = -1;
+            uint32_t u2pre = 0;
             // ---- C2V, two adjacent checks per thread ---------------------------
             for (int pr = t; pr < mpairs; pr += G) {
                 const int c = 2 * pr;
@@ -227,6 +235,9 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 #pragma unroll
                 for (int k = 0; k < DC; ++k) beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
             }
+            if (lot && early && lw)
+                cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, a.seed, a.shot_offset + b, it,
+                                         a.policy, lam, u2pre);
             group_sync<G>(bar);
             // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
@@ -265,10 +276,14 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             }
             if (!group_sync_or<G>(bar, mism)) { converged = true; break; }
             // ---- lottery (Alg. 3, or a baseline policy of Sec. III-B) ---------
-            if (a.lottery && it >= a.lottery_skip && it < I - 1) {
-                if (t < 32) {
-                    const int vs = lottery_pick<DC, DV>(gr, shat + prev * W32, s_w, W32, lane, a.seed,
-                                                        a.shot_offset + b, it, a.policy, lam, m, R, a.magic);
+            if (lot) {
+                if (lw) {
+                    const uint32_t *sp = shat + prev * W32;
+                    if (!early)
+                        cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it, a.policy,
+                                                 lam, u2pre);
+                    const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, a.policy, lam, m, R,
+                                                          a.magic);
                     if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
                 }
                 group_sync<G>(bar);

@@ -1,8 +1,10 @@
 // The lottery (Alg. 3) and the four baseline sign-flip policies of Sec. III-B,
-// shared by the BP kernels.  Run by the 32 lanes of a group's first warp after
-// the termination test of iteration `it`; returns the stored index of the
-// column whose LLR is to be negated (v*), the same in every lane, or -1 when
-// no check is unsatisfied.
+// shared by the BP kernels.  Run by the 32 lanes of one warp of the group;
+// lottery_pick returns the stored index of the column whose LLR is to be
+// negated (v*), the same in every lane, or -1 when no check is unsatisfied.
+// It is lottery_check (c*) followed by lottery_column (v*); a kernel may run
+// the first half early, during iteration i's check phase, when the policy
+// draws the check at random (it then depends only on s_hat(i-1) and s).
 //
 //   U   = s_hat(i-1) xor s (bit words sp ^ s_w); N = |U|
 //   u   = SplitMix64(seed, (g << 24) + i): low 32 bits choose the check,
@@ -26,10 +28,18 @@
 
 namespace lbp {
 
-template <int DC, int DV, typename Acc>
-__device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, const uint32_t *s_w, int W32,
-                                            int lane, uint64_t seed, uint64_t g, int it, int policy,
-                                            const float *lam, int m, int R, uint32_t magic) {
+// True for the policies whose check depends only on U and the draw, not on
+// the posteriors of this iteration (so it can be drawn early).
+__device__ __forceinline__ bool lottery_random_check(int policy) {
+    return policy != LBP_LOTTERY_WORST_UNRELIABLE && policy != LBP_LOTTERY_WORST_RANDOM;
+}
+
+// First half: the check c* (or -1 when U is empty) and the high 32 bits u2
+// of the draw, the same in every lane.
+template <int DC, typename Acc>
+__device__ __forceinline__ int lottery_check(const Acc &acc, const uint32_t *sp, const uint32_t *s_w, int W32,
+                                             int lane, uint64_t seed, uint64_t g, int it, int policy,
+                                             const float *lam, uint32_t &u2_out) {
     uint32_t N = 0;
     for (int w0 = 0; w0 < W32; w0 += 32) {
         const int w = w0 + lane;
@@ -41,7 +51,8 @@ __device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, 
     }
     if (N == 0) return -1;
     const uint64_t r64 = splitmix64_at(seed, (g << 24) + static_cast<uint64_t>(it));
-    const uint32_t u = static_cast<uint32_t>(r64), u2 = static_cast<uint32_t>(r64 >> 32);
+    const uint32_t u = static_cast<uint32_t>(r64);
+    u2_out = static_cast<uint32_t>(r64 >> 32);
     int cstar = -1;
     if (policy == LBP_LOTTERY_WORST_UNRELIABLE || policy == LBP_LOTTERY_WORST_RANDOM) {
         int bn = -1, bcr = 0x7fffffff;
@@ -94,6 +105,15 @@ __device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, 
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
+    return cstar;
+}
+
+// Second half: the column v* of check c* (stored index, or -1).
+template <int DC, int DV, typename Acc>
+__device__ __forceinline__ int lottery_column(const Acc &acc, int cstar, uint32_t u2, const uint32_t *sp,
+                                              const uint32_t *s_w, int lane, int policy, const float *lam,
+                                              int m, int R, uint32_t magic) {
+    if (cstar < 0) return -1;
     // Lane k < DC holds slot k of c*; ov is its column id in H (ties, order).
     const uint32_t vl = lane < DC ? acc.col(lane, cstar) : acc.pad;
     const bool present = vl != acc.pad;
@@ -140,6 +160,15 @@ __device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, 
     bv = __shfl_sync(0xffffffffu, bv, 0);
     bc = __shfl_sync(0xffffffffu, bc, 0);
     return bc >= 0 ? static_cast<int>(bv) : -1;
+}
+
+template <int DC, int DV, typename Acc>
+__device__ __forceinline__ int lottery_pick(const Acc &acc, const uint32_t *sp, const uint32_t *s_w, int W32,
+                                            int lane, uint64_t seed, uint64_t g, int it, int policy,
+                                            const float *lam, int m, int R, uint32_t magic) {
+    uint32_t u2 = 0;
+    const int cstar = lottery_check<DC>(acc, sp, s_w, W32, lane, seed, g, it, policy, lam, u2);
+    return lottery_column<DC, DV>(acc, cstar, u2, sp, s_w, lane, policy, lam, m, R, magic);
 }
 
 }  // namespace lbp
