@@ -31,9 +31,12 @@
 // they fit (kGraphSmem, kStateSmem); otherwise they are read from global
 // memory (the image is L2-resident; the state goes to a per-group slice of the
 // workspace), which is how the d=25 space-time code runs.
+// Lottery: the group's last warp, which has the fewest rounds in both phases,
+// runs lottery_pick's two halves; for the random-check policies it draws c*
+// right after its check-phase rounds (c* depends only on s_hat(i-1), s and the
+// draw), so after the termination test only the column step v* remains.
 // Everything else (groups of G threads per shot, named barriers, s_hat
-// scatter, early termination, lottery, outputs, OSD hand-off) is as in
-// bp_kernel.
+// scatter, early termination, outputs, OSD hand-off) is as in bp_kernel.
 #pragma once
 
 #include <cuda_fp16.h>
