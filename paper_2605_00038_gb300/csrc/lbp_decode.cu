@@ -149,6 +149,9 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
                 g_req == 1024) {
                 G = g_req;
                 S = s_req > 0 && s_req < S_fit ? s_req : S_fit;
+            } else if (num_shots <= c->sm_count) {
+                S = 1;              // a batch that does not fill the GPU: one shot per CTA
+                G = 256;
             }
             if (S * G > 1024) S = 1024 / G;
             if (G > 32 && S > 15) S = 15;
@@ -237,6 +240,11 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     if (s_req > 0 && (g_req == 32 || g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 || g_req == 256)) {
         G = g_req;
         S = s_req < S_fit ? s_req : S_fit;
+    } else if (num_shots <= c->sm_count) {
+        // A batch that does not fill the GPU: one shot per CTA, 256 threads
+        // each, for the lowest latency (the SMs would idle anyway).
+        S = 1;
+        G = 256;
     }
     if (!p.ell && G != 32 && G != 64 && G != 128 && G != 256) G = 128;
     if (S * G > 1024) S = 1024 / G;
