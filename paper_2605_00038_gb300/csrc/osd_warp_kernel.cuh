@@ -30,8 +30,9 @@
 //    block-wide kernel K_osd, which computes the same e.
 //  * Backward substitution over the pivots in reverse order, 32 per batch:
 //    each lane folds in the solution bits of later batches and records which
-//    pivots of its own batch its row touches; a 32-step scan then resolves the
-//    batch from its last pivot down.  The solution bits sit at the original
+//    pivots of its own batch its row touches (changed rows are scanned by the
+//    whole warp); the batch is then resolved level by level, all pivots whose
+//    dependencies are known at once.  The solution bits sit at the original
 //    column indices, so they are the output directly (no inverse
 //    permutation).
 #pragma once
@@ -377,15 +378,24 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
 
         if (!nosol) {
             // ---- backward substitution, 32 pivots per batch -------------------
+            // Lane k of a batch holds pivot k's equation x_k = s'_k + sum of
+            // the later pivots' x over its row's other pivot columns: `part`
+            // folds in those of later batches, `dep` marks those inside the
+            // batch.  Rows of H are scanned by their own lane; changed (dense)
+            // rows by the whole warp, one word per lane.  The batch is then
+            // solved level by level: every pivot whose dependencies are known
+            // resolves in the same step (dependencies point only to higher
+            // pivots, so each step resolves at least the highest open one).
             for (int hi = rank; hi > 0;) {
                 const int lo = hi > 32 ? hi - 32 : 0;
                 const int k = lo + lane;
                 unsigned part = 0u, dep = 0u;
+                int slot = 0xffff;
                 if (k < hi) {
                     const int p = prow[k];
                     part = (saug[p >> 5] >> (p & 31)) & 1u;
-                    const int s = rflag[p];
-                    if (s == 0xffff) {
+                    slot = rflag[p];
+                    if (slot == 0xffff) {
                         for (int e = row_ptr[p]; e < row_ptr[p + 1]; ++e) {
                             const int u = col_idx[e];
                             const int kk = pivk[u];
@@ -393,27 +403,41 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                             if (kk >= hi) part ^= (X32[u >> 5] >> (u & 31)) & 1u;
                             else if (kk > k) dep |= 1u << (kk - lo);
                         }
-                    } else {
-                        const uint64_t *row = slots + static_cast<size_t>(s) * wn;
-                        for (int w = 0; w < wn; ++w) {
-                            uint64_t x = row[w];
-                            while (x) {
-                                const int bit = __ffsll(static_cast<long long>(x)) - 1;
-                                x &= x - 1;
-                                const int u = w * 64 + bit;
-                                const int kk = pivk[u];
-                                if (kk == 0xffff || kk == k) continue;
-                                if (kk >= hi) part ^= (X32[u >> 5] >> (u & 31)) & 1u;
-                                else if (kk > k) dep |= 1u << (kk - lo);
-                            }
-                        }
                     }
                 }
-                unsigned E = 0u;
-                for (int L = hi - lo - 1; L >= 0; --L) {
+                unsigned dense = __ballot_sync(0xffffffffu, k < hi && slot != 0xffff);
+                while (dense) {
+                    const int src = __ffs(dense) - 1;
+                    dense &= dense - 1u;
+                    const int ss = __shfl_sync(0xffffffffu, slot, src);
+                    const int k0 = lo + src;
+                    const uint64_t *row = slots + static_cast<size_t>(ss) * wn;
+                    unsigned mp = 0u, md = 0u;
+                    for (int w = lane; w < wn; w += 32) {
+                        uint64_t x = row[w];
+                        while (x) {
+                            const int bit = __ffsll(static_cast<long long>(x)) - 1;
+                            x &= x - 1;
+                            const int u = w * 64 + bit;
+                            const int kk = pivk[u];
+                            if (kk == 0xffff || kk == k0) continue;
+                            if (kk >= hi) mp ^= (X32[u >> 5] >> (u & 31)) & 1u;
+                            else if (kk > k0) md |= 1u << (kk - lo);
+                        }
+                    }
+                    const unsigned pp = __popc(__ballot_sync(0xffffffffu, mp != 0u)) & 1u;
+                    const unsigned dd = __reduce_or_sync(0xffffffffu, md);
+                    if (lane == src) { part ^= pp; dep |= dd; }
+                }
+                const unsigned valid = __ballot_sync(0xffffffffu, k < hi);
+                unsigned E = 0u, done = 0u;
+                while (done != valid) {
+                    const bool open = k < hi && !((done >> lane) & 1u);
+                    const bool ready = open && (dep & ~done) == 0u;
                     const unsigned mine = part ^ (__popc(dep & E) & 1u);
-                    const unsigned eL = __shfl_sync(0xffffffffu, mine, L);
-                    E |= eL << L;
+                    const unsigned rb = __ballot_sync(0xffffffffu, ready);
+                    E |= __ballot_sync(0xffffffffu, ready && mine);
+                    done |= rb;
                 }
                 if (k < hi && ((E >> lane) & 1u)) {
                     const int u = pcol[k];
