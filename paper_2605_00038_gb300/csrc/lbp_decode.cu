@@ -292,14 +292,15 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     uint32_t off = 0;
     p.off_keys = off;  off = align16u(off + 8u * c->m);
     // The radix sort's buffer shares its bytes with the pivot arrays, which
-    // are first written after the sort.
+    // are first written after the sort ...
     const uint32_t u0 = off;
     p.off_tmp = u0;
     p.off_pivk = off;  off = align16u(off + 2u * c->n);
     p.off_pcol = off;  off = align16u(off + 2u * c->m);
     p.off_prow = off;  off = align16u(off + 2u * c->m);
-    if (off < u0 + align16u(8u * c->m)) off = u0 + align16u(8u * c->m);
-    p.off_hist = off;  off = align16u(off + 4u * 256);
+    // ... and so does its digit histogram, placed after the buffer.
+    p.off_hist = u0 + align16u(8u * c->m);
+    if (off < p.off_hist + 4u * 256) off = p.off_hist + 4u * 256;
     p.off_rflag = off; off = align16u(off + 2u * c->m);
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);

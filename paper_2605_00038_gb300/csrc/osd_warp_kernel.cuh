@@ -58,7 +58,7 @@ struct OsdWarpArgs {
     uint32_t image_bytes;          // bytes of the image prefix staged (row_ptr + col_idx)
     uint32_t region_bytes;         // per-warp shared memory
     uint32_t off_keys, off_tmp, off_hist, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow,
-        off_pend;             // off_tmp (radix sort buffer) overlaps pivk / pcol / prow
+        off_pend;             // off_tmp and off_hist (radix sort) overlap pivk / pcol / prow
 };
 
 constexpr uint64_t kNoKey = ~0ull;
