@@ -133,10 +133,24 @@ int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
  * the implicit graph: every neighbour index is evaluated from the formulas,
  * no index image is read (LBP_GRAPH=table|implicit selects the form, else
  * lbp_tune's choice, else the image when it fits shared memory beside one
- * shot's state and the implicit graph when it does not).  Both forms give
+ * shot's state, else the round-periodic graph of lbp_code_rounds, else the
+ * implicit graph).  Both forms give
  * identical results.  *d = 0 when not recognised; any output pointer may be
  * NULL. */
 int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type, int32_t *cyclic);
+
+/* Whether lbp_load_code recognised H as a space-time matrix of Eq. 1 for some
+ * round check matrix H_r (m_r x n_r, rows of at most 4 ones, columns of at
+ * most 2): T >= 2 rounds of H_r's rows shifted by t * n_r, then T - 1 (open
+ * time boundary, *cyclic 0) or T (cyclic, 1) blocks of m_r measurement
+ * columns, block b in rounds b and b + 1.  Such a code can run K_bp on the
+ * round-periodic graph: one round's index table in shared memory, the round
+ * offset and the measurement columns by arithmetic, with the same results as
+ * the full index image.  LBP_GRAPH=round selects it; by default it is used
+ * when the full image does not fit shared memory beside one shot's state
+ * (the d=25 space-time codes).  *T = 0 when not recognised; any output
+ * pointer may be NULL. */
+int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r, int32_t *cyclic);
 
 /* Bytes of device workspace lbp_decode needs for num_shots shots with these
  * parameters (0 on invalid input).  The size grows linearly with num_shots

@@ -72,6 +72,7 @@ struct BpEllArgs {
     uint8_t *gstate;          // per-group state slices when not in shared memory
     uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
     SurfaceDesc surf;         // implicit graph (SurfaceGraph)
+    RoundDesc rnd;            // round-periodic graph (RoundGraph)
     const float *mu_tab;      // its mu[Np + 2] when not uniform per block
 };
 
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     const int m = a.m, n = a.n, I = a.max_iter;
     const int Mp = a.img.Mp, Np = a.img.Np, R = Mp + 2;
     const int mpairs = Mp >> 1, npairs = Np >> 1;
-    const GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.mu_tab, m, n);
+    const GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.rnd, a.mu_tab, m, n);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
 
     const int grp = threadIdx.x / G;

@@ -83,8 +83,31 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     }
 }
 
+// Round-periodic graph: the round image staged into shared memory; state in
+// shared memory (any G) or in the workspace (G = 512, 1024).
+template <typename MsgT, int kRule>
+int launch_round(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    using GR = RoundGraph<6, 2>;
+    if (s.state_smem) {
+        switch (s.G) {
+            case 64: return launch_graph_one<MsgT, kRule, 64, 6, 2, true, true, GR>(s, a, st);
+            case 96: return launch_graph_one<MsgT, kRule, 96, 6, 2, true, true, GR>(s, a, st);
+            case 128: return launch_graph_one<MsgT, kRule, 128, 6, 2, true, true, GR>(s, a, st);
+            case 192: return launch_graph_one<MsgT, kRule, 192, 6, 2, true, true, GR>(s, a, st);
+            case 256: return launch_graph_one<MsgT, kRule, 256, 6, 2, true, true, GR>(s, a, st);
+            case 512: return launch_graph_one<MsgT, kRule, 512, 6, 2, true, true, GR>(s, a, st);
+            case 1024: return launch_graph_one<MsgT, kRule, 1024, 6, 2, true, true, GR>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
+    }
+    if (s.G == 512) return launch_graph_one<MsgT, kRule, 512, 6, 2, true, false, GR>(s, a, st);
+    if (s.G == 1024) return launch_graph_one<MsgT, kRule, 1024, 6, 2, true, false, GR>(s, a, st);
+    return LBP_ENOSYS;
+}
+
 template <typename MsgT, int kRule>
 int launch_ell(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
+    if (s.round) return DC == 6 && DV == 2 ? launch_round<MsgT, kRule>(s, a, st) : LBP_ENOSYS;
     if (s.surface) return launch_surface<MsgT, kRule>(s, a, st);
     if (DC == 6 && DV == 2) return launch_ell_g<MsgT, kRule, 6, 2>(s, a, st);
     if (DC == 6 && DV == 3) return launch_ell_g<MsgT, kRule, 6, 3>(s, a, st);

@@ -8,6 +8,11 @@
 //    read from shared memory or, for large codes, from global memory; a
 //    thread reads the indices of its two adjacent checks / columns as one
 //    paired access.
+//  * RoundGraph: any space-time matrix of Eq. 1 (a round matrix H_r on the
+//    diagonal, identity measurement blocks between rounds): one round's index
+//    table in shared memory, the round offset and the measurement columns by
+//    arithmetic; slots as for SurfaceGraph (round columns, then blocks t - 1
+//    and t), so the same sums in the same order.
 //  * SurfaceGraph: the unrotated surface-code space-time matrix, whose
 //    indices Table III gives by closed formulas (VN0..VN3 data qubits of the
 //    round, VN4 / VN5 the measurement blocks before and after it); the column
@@ -53,7 +58,7 @@ struct EllGraph {
     static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
 
     __device__ __forceinline__ EllGraph(const EllImage &img, const uint8_t *gbase, const SurfaceDesc &,
-                                        const float *, int, int n_) {
+                                        const RoundDesc &, const float *, int, int n_) {
         pad = static_cast<uint32_t>(n_);
         cidx = reinterpret_cast<const IdxT *>(gbase + img.off_cidx);
         cidx2 = reinterpret_cast<const IP *>(cidx);
@@ -102,7 +107,7 @@ struct SurfaceGraph {
     static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
 
     __device__ __forceinline__ SurfaceGraph(const EllImage &img, const uint8_t *, const SurfaceDesc &sd,
-                                            const float *mt, int m_, int n_)
+                                            const RoundDesc &, const float *mt, int m_, int n_)
         : s(sd), mu_tab(mt), m(static_cast<uint32_t>(m_)), n(static_cast<uint32_t>(n_)),
           Mp(static_cast<uint32_t>(img.Mp)), R(static_cast<uint32_t>(img.Mp) + 2u),
           M0(static_cast<uint32_t>(sd.T) * sd.nr), pad(static_cast<uint32_t>(n_)) {}
@@ -205,6 +210,101 @@ struct SurfaceGraph {
     __device__ __forceinline__ float mu(uint32_t v) const {
         if (v >= n) return __int_as_float(0x7f800000);
         if (s.mu_uniform) return v < M0 ? s.mu_data : s.mu_meas;
+        return __ldg(mu_tab + v);
+    }
+    __device__ __forceinline__ float2 mu2(int q) const {
+        return make_float2(mu(2u * static_cast<uint32_t>(q)), mu(2u * static_cast<uint32_t>(q) + 1u));
+    }
+};
+
+template <int DC, int DV>
+struct RoundGraph {
+    static_assert(DV >= 2, "a measurement column has two checks");
+    static constexpr bool kImage = true;     // the round image is staged like an index image
+    RoundDesc r;
+    const uint16_t *rcidx;
+    const uint32_t *rvent;
+    const float *mu_tab;     // mu[Np + 2] (global) when mu is not uniform per block
+    uint32_t m, n, Mp, R, M0;
+    uint32_t pad;            // column id of absent neighbours (n)
+    static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
+
+    __device__ __forceinline__ RoundGraph(const EllImage &img, const uint8_t *gbase, const SurfaceDesc &,
+                                          const RoundDesc &rd, const float *mt, int m_, int n_)
+        : r(rd), rcidx(reinterpret_cast<const uint16_t *>(gbase + rd.off_rcidx)),
+          rvent(reinterpret_cast<const uint32_t *>(gbase + rd.off_rvent)), mu_tab(mt),
+          m(static_cast<uint32_t>(m_)), n(static_cast<uint32_t>(n_)), Mp(static_cast<uint32_t>(img.Mp)),
+          R(static_cast<uint32_t>(img.Mp) + 2u), M0(static_cast<uint32_t>(rd.T) * rd.nr),
+          pad(static_cast<uint32_t>(n_)) {}
+
+    // Check c = t m_r + j: the round columns of H_r's row j shifted to round
+    // t, then the measurement blocks t - 1 and t (absent ones = n).
+    __device__ __forceinline__ void cols(uint32_t c, uint32_t (&v)[DC]) const {
+        #pragma unroll
+        for (int k = 0; k < DC; ++k) v[k] = n;
+        if (c >= m) return;
+        const uint32_t t = __umulhi(c, r.mg_mr), j = c - t * r.mr, bd = t * r.nr;
+        #pragma unroll
+        for (int k = 0; k < DC - 2; ++k) {
+            const uint32_t q = rcidx[k * r.mr + j];
+            if (q < r.nr) v[k] = bd + q;
+        }
+        int b4 = static_cast<int>(t) - 1;
+        if (b4 < 0 && r.cyclic) b4 = r.T - 1;
+        if (b4 >= 0 && b4 < r.nb) v[DC - 2] = M0 + static_cast<uint32_t>(b4) * r.mr + j;
+        if (static_cast<int>(t) < r.nb) v[DC - 1] = M0 + t * r.mr + j;
+    }
+    // Column v: a round column's checks in its round (from the round image),
+    // or a measurement column's two checks, ascending.
+    __device__ __forceinline__ void ents(uint32_t v, uint32_t (&o)[DV]) const {
+        #pragma unroll
+        for (int k = 0; k < DV; ++k) o[k] = Mp;
+        if (v >= n) return;
+        if (v < M0) {
+            const uint32_t t = __umulhi(v, r.mg_nr), q = v - t * r.nr, add = t * r.mr;
+            #pragma unroll
+            for (int k = 0; k < DV; ++k) {
+                const uint32_t e = rvent[k * r.nr + q];
+                if (e != 0xffffffffu) o[k] = e + add;
+            }
+        } else {
+            // Block b: slot DC - 1 of check (b, j), slot DC - 2 of check (b + 1, j).
+            const uint32_t u = v - M0, b = __umulhi(u, r.mg_mr), j = u - b * r.mr;
+            const uint32_t b1 = b + 1u == static_cast<uint32_t>(r.T) ? 0u : b + 1u;
+            const uint32_t ca = b * r.mr + j, cb = b1 * r.mr + j;
+            const uint32_t oa = (DC - 1) * R + ca, ob = (DC - 2) * R + cb;
+            if (cb > ca) { o[0] = oa; o[1] = ob; }
+            else { o[0] = ob; o[1] = oa; }
+        }
+    }
+    __device__ __forceinline__ void cols2(int pr, uint32_t (&x)[DC], uint32_t (&y)[DC]) const {
+        cols(2u * static_cast<uint32_t>(pr), x);
+        cols(2u * static_cast<uint32_t>(pr) + 1u, y);
+    }
+    __device__ __forceinline__ void ents2(int q, uint32_t (&x)[DV], uint32_t (&y)[DV]) const {
+        ents(2u * static_cast<uint32_t>(q), x);
+        ents(2u * static_cast<uint32_t>(q) + 1u, y);
+    }
+    __device__ __forceinline__ uint32_t col(int k, int c) const {
+        uint32_t v[DC];
+        cols(static_cast<uint32_t>(c), v);
+        uint32_t x = v[0];
+        #pragma unroll
+        for (int i = 1; i < DC; ++i) if (i == k) x = v[i];
+        return x;
+    }
+    __device__ __forceinline__ uint32_t ent(int k, int v) const {
+        uint32_t o[DV];
+        ents(static_cast<uint32_t>(v), o);
+        uint32_t x = o[0];
+        #pragma unroll
+        for (int i = 1; i < DV; ++i) if (i == k) x = o[i];
+        return x;
+    }
+    __device__ __forceinline__ uint32_t orig(uint32_t v) const { return v; }
+    __device__ __forceinline__ float mu(uint32_t v) const {
+        if (v >= n) return __int_as_float(0x7f800000);
+        if (r.mu_uniform) return v < M0 ? r.mu_data : r.mu_meas;
         return __ldg(mu_tab + v);
     }
     __device__ __forceinline__ float2 mu2(int q) const {

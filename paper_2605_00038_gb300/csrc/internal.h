@@ -56,6 +56,26 @@ struct SurfaceDesc {
     float mu_data, mu_meas;
 };
 
+// Space-time matrix of Eq. 1 for any per-round check matrix H_r (m_r x n_r):
+// rows t m_r + j (t < T) hold H_r's row j shifted by t n_r plus the
+// measurement columns T n_r + b m_r + j of blocks b = t - 1 and b = t that
+// exist (nb = T - 1 blocks with an open time boundary, T when cyclic).
+// Recognised by lbp_load_code for every H of that form; the BP kernel then
+// stores one round's index table instead of the whole graph.
+// Round image: rcidx[DC - 2][m_r] (uint16) the round columns of each round
+// check in ascending order (n_r when absent), then rvent[DV][n_r] (uint32)
+// slot * R + j of each round column's round checks ascending (~0 when
+// absent).  A check's slots are its round columns (0 .. DC - 3), then the
+// measurement blocks t - 1 (slot DC - 2) and t (slot DC - 1).
+struct RoundDesc {
+    int32_t T, nb, cyclic;
+    uint32_t mr, nr;
+    uint32_t mg_mr, mg_nr;   // floor(2^32 / x) + 1 for exact x / divisor
+    uint32_t bytes, off_rcidx, off_rvent;
+    int32_t mu_uniform;
+    float mu_data, mu_meas;
+};
+
 }  // namespace lbp
 
 struct lbp_code;
@@ -101,6 +121,10 @@ struct lbp_code {
     int surface;
     lbp::SurfaceDesc surf;
     float *d_mu_pad;
+    // Round-periodic graph (Eq. 1 with any round matrix) and its round image.
+    int round;
+    lbp::RoundDesc rnd;
+    uint8_t *d_round;
     // BP launch shape chosen by lbp_tune per message type (0 = not tuned):
     // groups per CTA and threads per group.
     int tuned_groups[6], tuned_G[6];   // per (rule, message type), lbp_tune

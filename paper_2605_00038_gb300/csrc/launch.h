@@ -13,6 +13,7 @@ struct LaunchShape {
     size_t smem;
     bool graph_smem, state_smem, idx32;
     bool surface;            // implicit surface-code graph (no index image)
+    bool round;              // round-periodic graph (one round's index image)
 };
 
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);

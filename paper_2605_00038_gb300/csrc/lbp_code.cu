@@ -26,6 +26,7 @@ void release(lbp_code *c) {
     cudaFree(c->d_image);
     cudaFree(c->d_ell);
     cudaFree(c->d_mu_pad);
+    cudaFree(c->d_round);
     cudaFree(c->d_row_ptr);
     cudaFree(c->d_col_idx);
     cudaFree(c->d_mu);
@@ -112,6 +113,94 @@ bool detect_surface(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t 
                 *out = s;
                 return true;
             }
+        }
+    }
+    return false;
+}
+
+// Recognise H as the space-time matrix of Eq. 1 of some round matrix H_r
+// (T >= 2 rounds, open or cyclic time boundary): row t m_r + j must hold H_r's
+// row j (read from round 0) shifted by t n_r, then the measurement columns of
+// blocks t - 1 and t that exist.  H_r's rows may have at most DC - 2 columns
+// and its columns at most DV rows.  On a match fills *out and the round image.
+bool detect_round(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                  const std::vector<float> &mu, int DC, int DV, int32_t Mp, lbp::RoundDesc *out,
+                  std::vector<uint8_t> *image) {
+    for (int64_t T = 2; T <= m; ++T) {
+        if (m % T) continue;
+        const int64_t mr = m / T;
+        for (int cyclic = 0; cyclic < 2; ++cyclic) {
+            const int64_t nb = cyclic ? T : T - 1;
+            const int64_t rest = static_cast<int64_t>(n) - nb * mr;
+            if (rest <= 0 || rest % T) continue;
+            const int64_t nr = rest / T, M0 = T * nr;
+            const uint64_t big = static_cast<uint64_t>(n > m ? n : m), div = static_cast<uint64_t>(nr > mr ? nr : mr);
+            if (nr >= 65535 || big * div >= (1ull << 32)) continue;    // exact multiply-high divisions
+            bool ok = true;
+            for (int64_t c = 0; c < m && ok; ++c) {
+                const int64_t t = c / mr, j = c % mr;
+                const int32_t a = row_ptr[c], e = row_ptr[c + 1];
+                const int32_t a0 = row_ptr[j], e0 = row_ptr[j + 1];
+                int32_t nd = 0;                       // round columns of row (t, j)
+                while (a + nd < e && col_idx[a + nd] < M0) ++nd;
+                int32_t nd0 = 0;
+                while (a0 + nd0 < e0 && col_idx[a0 + nd0] < M0) ++nd0;
+                if (nd != nd0 || nd > DC - 2) { ok = false; break; }
+                for (int32_t k = 0; k < nd; ++k) {
+                    if (col_idx[a0 + k] >= nr || col_idx[a + k] != col_idx[a0 + k] + t * nr) { ok = false; break; }
+                }
+                if (!ok) break;
+                int64_t want[2];
+                int nw = 0;
+                for (int64_t b = t - 1; b <= t; ++b) {
+                    int64_t bb = b;
+                    if (cyclic) bb = (b + T) % T;
+                    if (bb >= 0 && bb < nb) want[nw++] = M0 + bb * mr + j;
+                }
+                if (nw == 2 && want[0] > want[1]) std::swap(want[0], want[1]);
+                if (nw == 2 && want[0] == want[1]) { ok = false; break; }
+                if (e - (a + nd) != nw) { ok = false; break; }
+                for (int k = 0; k < nw; ++k)
+                    if (col_idx[a + nd + k] != want[k]) { ok = false; break; }
+            }
+            if (!ok) continue;
+            // Round columns' checks (ascending) and their slots.
+            std::vector<int32_t> deg(nr, 0);
+            for (int64_t j = 0; j < mr; ++j)
+                for (int32_t e = row_ptr[j]; e < row_ptr[j + 1] && col_idx[e] < M0; ++e) deg[col_idx[e]]++;
+            int maxdeg = 0;
+            for (int64_t q = 0; q < nr; ++q) maxdeg = deg[q] > maxdeg ? deg[q] : maxdeg;
+            if (maxdeg > DV) continue;
+            lbp::RoundDesc d;
+            std::memset(&d, 0, sizeof(d));
+            d.T = static_cast<int32_t>(T); d.nb = static_cast<int32_t>(nb); d.cyclic = cyclic;
+            d.mr = static_cast<uint32_t>(mr); d.nr = static_cast<uint32_t>(nr);
+            d.mg_mr = magic(d.mr); d.mg_nr = magic(d.nr);
+            d.off_rcidx = 0;
+            d.off_rvent = align16(2u * (DC - 2) * d.mr);
+            d.bytes = align16(d.off_rvent + 4u * DV * d.nr);
+            image->assign(d.bytes, 0);
+            uint16_t *rcidx = reinterpret_cast<uint16_t *>(image->data() + d.off_rcidx);
+            uint32_t *rvent = reinterpret_cast<uint32_t *>(image->data() + d.off_rvent);
+            const uint32_t R = static_cast<uint32_t>(Mp) + 2u;
+            for (size_t i = 0; i < static_cast<size_t>(DC - 2) * mr; ++i) rcidx[i] = static_cast<uint16_t>(nr);
+            for (size_t i = 0; i < static_cast<size_t>(DV) * nr; ++i) rvent[i] = 0xffffffffu;
+            std::vector<int32_t> fill(nr, 0);
+            for (int64_t j = 0; j < mr; ++j) {
+                int k = 0;
+                for (int32_t e = row_ptr[j]; e < row_ptr[j + 1] && col_idx[e] < M0; ++e, ++k) {
+                    const int32_t q = col_idx[e];
+                    rcidx[static_cast<size_t>(k) * mr + j] = static_cast<uint16_t>(q);
+                    rvent[static_cast<size_t>(fill[q]++) * nr + q] = static_cast<uint32_t>(k) * R + static_cast<uint32_t>(j);
+                }
+            }
+            d.mu_uniform = 1;
+            d.mu_data = mu[0];
+            d.mu_meas = nb > 0 ? mu[M0] : 0.0f;
+            for (int64_t v = 0; v < n && d.mu_uniform; ++v)
+                if (mu[v] != (v < M0 ? d.mu_data : d.mu_meas)) d.mu_uniform = 0;
+            *out = d;
+            return true;
         }
     }
     return false;
@@ -289,6 +378,15 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
             if (!c->surf.mu_uniform)
                 rc = upload(reinterpret_cast<void **>(&c->d_mu_pad), mu_e, 4u * (Np + 2));
         }
+        // Round-periodic graph: one round's index table (Eq. 1 structure).
+        std::vector<uint8_t> rimg;
+        if (rc == LBP_OK && ell_dc == 6 && ell_dv == 2 &&
+            detect_round(m, n, row_ptr, col_idx, mu, ell_dc, ell_dv, Mp, &c->rnd, &rimg)) {
+            c->round = 1;
+            rc = upload(reinterpret_cast<void **>(&c->d_round), rimg.data(), rimg.size());
+            if (rc == LBP_OK && !c->rnd.mu_uniform && !c->d_mu_pad)
+                rc = upload(reinterpret_cast<void **>(&c->d_mu_pad), mu_e, 4u * (Np + 2));
+        }
     }
     if (rc != LBP_OK) { release(c); return rc; }
     *out = c;
@@ -309,6 +407,16 @@ extern "C" int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, in
     if (T) *T = on ? code->surf.T : 0;
     if (type) *type = on ? code->surf.type : 0;
     if (cyclic) *cyclic = on ? code->surf.cyclic : 0;
+    return LBP_OK;
+}
+
+extern "C" int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r, int32_t *cyclic) {
+    if (!code) return LBP_EINVAL;
+    const bool on = code->round != 0;
+    if (T) *T = on ? code->rnd.T : 0;
+    if (m_r) *m_r = on ? static_cast<int32_t>(code->rnd.mr) : 0;
+    if (n_r) *n_r = on ? static_cast<int32_t>(code->rnd.nr) : 0;
+    if (cyclic) *cyclic = on ? code->rnd.cyclic : 0;
     return LBP_OK;
 }
 

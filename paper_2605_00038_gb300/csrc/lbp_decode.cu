@@ -46,7 +46,7 @@ int tuned_slot(int msg, int rule) {
 }
 
 struct BpPlan {
-    bool ell = false, graph_smem = true, state_smem = true, idx32 = false, surface = false;
+    bool ell = false, graph_smem = true, state_smem = true, idx32 = false, surface = false, round = false;
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -89,23 +89,28 @@ int validate_params(const lbp_params *p) {
 
 // Plan K_bp for this code and message type; returns LBP_ENOSYS if even one
 // group does not fit in shared memory.
-// Graph form of K_bp for a code with an implicit (Table III) graph: the
-// request (1 index image, 2 implicit), else LBP_GRAPH=table|implicit, else the
-// tuned form, else the image when it fits shared memory beside one shot's
-// state (evaluating the formulas costs more issue slots than the image's
-// shared-memory index loads) and the implicit graph when it does not (the
-// image would otherwise be read from L2 on every iteration).
+// Graph form of K_bp: 1 the index image, 2 the implicit Table III graph,
+// 3 the round-periodic graph (one round's index table); the request, else
+// LBP_GRAPH=table|implicit|round, else the tuned form, among the forms this
+// code has.  By default the index image where it fits shared memory beside
+// one shot's state (it costs the fewest instructions), else the round
+// graph, else the implicit graph (the image would otherwise be read from L2
+// on every iteration), else the image from global memory.
 int graph_form(const lbp_code *c, int mi, int req_graph, size_t state_bytes) {
-    if (!c->surface) return 1;
-    if (req_graph == 1 || req_graph == 2) return req_graph;
+    auto ok = [&](int f) { return f == 1 || (f == 2 && c->surface) || (f == 3 && c->round); };
+    if (req_graph >= 1 && req_graph <= 3) return ok(req_graph) ? req_graph : -1;
     if (const char *env = std::getenv("LBP_GRAPH")) {
         if (!std::strcmp(env, "table")) return 1;
-        if (!std::strcmp(env, "implicit")) return 2;
+        if (!std::strcmp(env, "implicit") && ok(2)) return 2;
+        if (!std::strcmp(env, "round") && ok(3)) return 3;
     }
-    if (c->tuned_graph[mi] == 1 || c->tuned_graph[mi] == 2) return c->tuned_graph[mi];
+    if (c->tuned_graph[mi] > 0 && ok(c->tuned_graph[mi])) return c->tuned_graph[mi];
     const bool image_fits = c->ell.idx_bytes == 2 &&
                             c->ell.bytes + state_bytes <= static_cast<size_t>(c->smem_optin);
-    return image_fits ? 1 : 2;
+    if (image_fits) return 1;
+    if (c->round) return 3;
+    if (c->surface) return 2;
+    return 1;
 }
 
 int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out, int req_S = 0,
@@ -123,19 +128,25 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     p.state_bytes = off;
     size_t image = c->ell.bytes;
     const size_t budget0 = static_cast<size_t>(c->smem_optin);
-    if (graph_form(c, mi, req_graph, off) == 2) {
-        // Implicit graph: nothing but the state in shared memory.
+    const int form = graph_form(c, mi, req_graph, off);
+    if (form < 0) return LBP_ENOSYS;
+    if (form == 2 || form == 3) {
+        // Implicit or round-periodic graph: the state and at most a small
+        // round image in shared memory.
+        const size_t rimg = form == 3 ? c->rnd.bytes : 0;
+        const size_t budget_s = budget0 > rimg ? budget0 - rimg : 0;
         p.ell = true;
-        p.surface = true;
-        p.graph_smem = false;
-        p.state_smem = off <= budget0;
+        p.surface = form == 2;
+        p.round = form == 3;
+        p.graph_smem = form == 3;
+        p.state_smem = off <= budget_s;
         int S = 1, G = 1024;
         if (p.state_smem) {
-            const int S_fit = static_cast<int>(budget0 / off);
+            const int S_fit = static_cast<int>(budget_s / off);
             if (S_fit >= 6) { G = 96; S = S_fit < 10 ? S_fit : 10; }
             else if (S_fit >= 4) { G = 256; S = 4; }
             else if (S_fit >= 2) { G = 512; S = 2; }
-            if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] == 2) {
+            if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] == form) {
                 G = c->tuned_G[mi];
                 S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
             }
@@ -162,7 +173,7 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
         if (S < 1) S = 1;
         p.groups = S;
         p.G = G;
-        p.smem = p.state_smem ? static_cast<size_t>(S) * off : static_cast<size_t>(16) * S;
+        p.smem = rimg + (p.state_smem ? static_cast<size_t>(S) * off : static_cast<size_t>(16) * S);
         const int64_t need = (num_shots + S - 1) / S;
         p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
         if (p.grid < 1) p.grid = 1;
@@ -226,7 +237,7 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     int G = 32;
     while (G < 128 && G * 2 <= 1024 / (S > 0 ? S : 1) && (G < c->m / 4 || G < c->n / 16)) G *= 2;
     if (p.ell && G == 128 && S_fit >= 6) G = 96;
-    if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] != 2) {
+    if (c->tuned_G[mi] > 0 && c->tuned_graph[mi] == 1) {
         G = c->tuned_G[mi];
         S = c->tuned_groups[mi] < S_fit ? c->tuned_groups[mi] : S_fit;
     }
@@ -480,9 +491,14 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
         e.surf = c->surf;
+        e.rnd = c->rnd;
         e.mu_tab = c->d_mu_pad;
+        if (bp.round) {
+            e.image = c->d_round;                         // staged instead of the index image
+            e.img.bytes = c->rnd.bytes;
+        }
         const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32,
-                              bp.surface};
+                              bp.surface, bp.round};
         const bool sp = prm->rule == LBP_RULE_SUM_PRODUCT;
         switch (prm->msg) {
             case LBP_MSG_F32:
@@ -696,7 +712,9 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     int best_S = 0, best_G = 0, best_graph = 0;
     // Candidates: every thread count, with the index image and, for a
     // recognised surface code, with the implicit graph.
-    for (int graph = 1; graph <= (code->surface ? 2 : 1); ++graph) {
+    for (int graph = 1; graph <= 3; ++graph) {
+        if (graph == 2 && !code->surface) continue;
+        if (graph == 3 && !code->round) continue;
         for (int G : Gs) {
             BpPlan probe;
             if (plan_bp(code, params->msg, params->rule, num_shots, &probe, 1024, G, graph) != LBP_OK) continue;

@@ -25,7 +25,7 @@ LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
 (LBP_LOTTERY_PROPOSED, LBP_LOTTERY_WORST_UNRELIABLE, LBP_LOTTERY_WORST_RANDOM,
  LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM) = range(5)
 
-EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface",
+EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface", "lbp_code_rounds",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_submit", "lbp_server_poll", "lbp_server_wait",
             "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
@@ -70,6 +70,8 @@ def lib():
         L.lbp_code_info.argtypes = [vp, vp, vp, vp]
         L.lbp_code_surface.restype = ctypes.c_int
         L.lbp_code_surface.argtypes = [vp, vp, vp, vp, vp]
+        L.lbp_code_rounds.restype = ctypes.c_int
+        L.lbp_code_rounds.argtypes = [vp, vp, vp, vp, vp]
         L.lbp_workspace_size.restype = sz
         L.lbp_workspace_size.argtypes = [vp, P, i64]
         L.lbp_host_workspace_size.restype = sz
@@ -173,6 +175,14 @@ def lbp_code_surface(code: Code):
     _check(lib().lbp_code_surface(code.ptr, ctypes.byref(d), ctypes.byref(T), ctypes.byref(ty),
                                   ctypes.byref(cy)), "lbp_code_surface")
     return d.value, T.value, ty.value, cy.value
+
+
+def lbp_code_rounds(code: Code):
+    """(T, m_r, n_r, cyclic) of a recognised space-time matrix of Eq. 1, T = 0 if none."""
+    T, mr, nr, cy = (ctypes.c_int32() for _ in range(4))
+    _check(lib().lbp_code_rounds(code.ptr, ctypes.byref(T), ctypes.byref(mr), ctypes.byref(nr),
+                                 ctypes.byref(cy)), "lbp_code_rounds")
+    return T.value, mr.value, nr.value, cy.value
 
 
 def lbp_workspace_size(code: Code, params: lbp_params, num_shots: int) -> int:

@@ -155,7 +155,7 @@ def test_lottery_baseline_policies(policy):
 
 
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
-@pytest.mark.parametrize("form", ["table", "implicit"])
+@pytest.mark.parametrize("form", ["table", "implicit", "round"])
 def test_d27_table2_spacetime_32bit_image(msg, form, monkeypatch):
     """The d=27 space-time matrix in the exact form whose size Table II prints
     (unrotated code, cyclic time boundary: 18,954 x 56,889, nnz 112,320): its
