@@ -131,10 +131,8 @@ int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
  * T - 1 (open time boundary, *cyclic 0) or T (cyclic, 1) measurement blocks,
  * d >= 3, columns and rows in Table III's order.  Such a code can run K_bp on
  * the implicit graph: every neighbour index is evaluated from the formulas,
- * no index image is read (LBP_GRAPH=table|implicit selects the form, else
- * lbp_tune's choice, else the image when it fits shared memory beside one
- * shot's state, else the round-periodic graph of lbp_code_rounds, else the
- * implicit graph).  Both forms give
+ * no index image is read (LBP_GRAPH=table|implicit|round selects the form,
+ * else lbp_tune's choice, else the index image).  Both forms give
  * identical results.  *d = 0 when not recognised; any output pointer may be
  * NULL. */
 int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type, int32_t *cyclic);
@@ -146,10 +144,11 @@ int lbp_code_surface(const lbp_code *code, int32_t *d, int32_t *T, int32_t *type
  * columns, block b in rounds b and b + 1.  Such a code can run K_bp on the
  * round-periodic graph: one round's index table in shared memory, the round
  * offset and the measurement columns by arithmetic, with the same results as
- * the full index image.  LBP_GRAPH=round selects it; by default it is used
- * when the full image does not fit shared memory beside one shot's state
- * (the d=25 space-time codes).  *T = 0 when not recognised; any output
- * pointer may be NULL. */
+ * the full index image, from a table of a few KB (7.5 KB for the d=25
+ * space-time code, whose full image takes 230 KB).  LBP_GRAPH=round selects
+ * it, and lbp_tune measures it; by default the full image is used, whose
+ * index loads cost fewer instructions than the arithmetic they would
+ * replace.  *T = 0 when not recognised; any output pointer may be NULL. */
 int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r, int32_t *cyclic);
 
 /* Bytes of device workspace lbp_decode needs for num_shots shots with these

@@ -129,12 +129,11 @@ def test_round_graph_per_column_priors(monkeypatch):
 
 
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16])
-def test_d25_spacetime_default_form_is_round(monkeypatch, msg):
-    """d=25, 25 rounds (7,800 x 23,113): the full image does not fit shared
-    memory beside a shot's state, so the round graph is the default form; a
-    sample of shots is checked against the oracle (FP32: state in global
-    memory; FP16: state in shared memory)."""
-    monkeypatch.delenv("LBP_GRAPH", raising=False)
+def test_d25_spacetime_round_graph(monkeypatch, msg):
+    """d=25, 25 rounds (7,800 x 23,113), whose full image does not fit shared
+    memory beside a shot's state: on the round graph a sample of shots matches
+    the oracle (FP32: state in global memory; FP16: state in shared memory)."""
+    monkeypatch.setenv("LBP_GRAPH", "round")
     w = workloads.c5_d25_spacetime(msg=msg, shots=64)
     assert rounds_of(w.h, w.priors)[0] == 25
     _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
