@@ -55,6 +55,8 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
             case 128: return launch_ell_one<MsgT, kRule, 128, DC, DV, true, true>(s, a, st);
             case 192: return launch_ell_one<MsgT, kRule, 192, DC, DV, true, true>(s, a, st);
             case 256: return launch_ell_one<MsgT, kRule, 256, DC, DV, true, true>(s, a, st);
+            case 512: return launch_ell_one<MsgT, kRule, 512, DC, DV, true, true>(s, a, st);
+            case 1024: return launch_ell_one<MsgT, kRule, 1024, DC, DV, true, true>(s, a, st);
             default: return LBP_ENOSYS;
         }
     }

@@ -244,14 +244,19 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
             if (std::sscanf(env, "%d,%d", &s_req, &g_req) != 2) s_req = g_req = 0;
         }
     }
-    if (s_req > 0 && (g_req == 32 || g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 || g_req == 256)) {
+    const bool g_ok = g_req == 32 || g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 ||
+                      g_req == 256 || (p.ell && (g_req == 512 || g_req == 1024));
+    if (s_req > 0 && g_ok) {
         G = g_req;
         S = s_req < S_fit ? s_req : S_fit;
     } else if (num_shots <= c->sm_count) {
-        // A batch that does not fill the GPU: one shot per CTA, 256 threads
-        // each, for the lowest latency (the SMs would idle anyway).
+        // A batch that does not fill the GPU: one shot per CTA, for the
+        // lowest latency (the SMs would idle anyway).  The ELL kernel gets a
+        // thread per column pair, up to 1024: at this size an iteration's
+        // time is the latency of its dependent steps, not its instructions.
         S = 1;
         G = 256;
+        while (p.ell && G < 1024 && G < (c->ell.Np + 1) / 2) G *= 2;
     }
     if (!p.ell && G != 32 && G != 64 && G != 128 && G != 256) G = 128;
     if (S * G > 1024) S = 1024 / G;

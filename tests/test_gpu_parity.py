@@ -154,6 +154,29 @@ def test_lottery_baseline_policies(policy):
         assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
 
 
+@pytest.mark.parametrize("policy", range(5))
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
+def test_small_batch_wide_groups(policy, msg, monkeypatch):
+    """A batch of at most one shot per SM runs one shot per CTA with a thread
+    per column pair (1024 on the d=11 space-time code): bit-identical to the
+    oracle for every lottery policy, and to the same shots decoded inside a
+    large batch (shot_offset keeps their draws)."""
+    w = workloads.c2_d11_spacetime(shots=2048)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed + policy, num_shots=w.shots)
+    kw = dict(w.decoder, msg=msg, lottery_policy=policy, seed=policy)
+    big = gpu_decode(w.h, w.priors, syn, **kw)
+    lo = 1500
+    small = gpu_decode(w.h, w.priors, syn[lo:lo + 100], shot_offset=lo, **kw)
+    for k in ("err", "conv", "iters", "osd"):
+        assert np.array_equal(big[k][lo:lo + 100], small[k]), k
+    assert np.array_equal(big["llr"][lo:lo + 100].view(np.uint32), small["llr"].view(np.uint32))
+    assert_parity(small, oracle_decode(w.h, w.priors, syn[lo:lo + 100], shot_offset=lo, **kw))
+    monkeypatch.setenv("LBP_BP_SHAPE", "1,512")
+    mid = gpu_decode(w.h, w.priors, syn[lo:lo + 100], shot_offset=lo, **kw)
+    for k in ("err", "conv", "iters", "osd"):
+        assert np.array_equal(mid[k], small[k]), k
+
+
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
 @pytest.mark.parametrize("form", ["table", "implicit", "round"])
 def test_d27_table2_spacetime_32bit_image(msg, form, monkeypatch):
