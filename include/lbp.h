@@ -161,7 +161,11 @@ int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r
  * within 1 GiB but never below min(m, 192).  The environment variable
  * LBP_OSD_POOL_ROWS (read at every call) sets C (1..m); a shot that needs
  * more rows is solved by the block-wide OSD kernel instead, with the same
- * result.  Set it identically for lbp_workspace_size and lbp_decode. */
+ * result.  Set it identically for lbp_workspace_size and lbp_decode.
+ * A call with num_shots at most the SM count runs OSD in its latency layout
+ * (one warp per CTA, lambda and the pool in shared memory, C as many rows
+ * as fit, capped by LBP_OSD_POOL_ROWS); LBP_OSD_LAT=0 turns that off.  The
+ * workspace size does not depend on it. */
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).

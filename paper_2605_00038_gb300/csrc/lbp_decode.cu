@@ -64,6 +64,8 @@ struct OsdWarpPlan {
     int warps = 0, grid = 0, C = 0, wn = 0;
     uint32_t image = 0, region = 0, off_keys = 0, off_tmp = 0, off_hist = 0, off_rflag = 0, off_pivk = 0,
              off_pivb = 0, off_saug = 0, off_x = 0, off_pcol = 0, off_prow = 0, off_pend = 0;
+    uint32_t off_lb = 0, off_pool = 0;
+    bool lat = false;
     size_t smem = 0;
 };
 
@@ -353,6 +355,41 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     *out = p;
 }
 
+// Latency layout of K_osd_warp, for a batch of at most one shot per SM: one
+// warp per CTA, whose region also holds lambda's order bits [n] and a pool of
+// as many dense rows as fit (at most m), so the event chain never leaves
+// shared memory.  LBP_OSD_LAT=0 turns it off; LBP_OSD_POOL_ROWS caps C.
+bool plan_osd_lat(const lbp_code *c, int64_t num_shots, const OsdWarpPlan &wp, OsdWarpPlan *out) {
+    if (!wp.ok || num_shots > c->sm_count) return false;
+    if (const char *env = std::getenv("LBP_OSD_LAT")) {
+        if (!std::strcmp(env, "0")) return false;
+    }
+    OsdWarpPlan p = wp;
+    const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
+    const size_t lbb = align16u(4u * static_cast<uint32_t>(c->n));
+    const size_t per_row = 8u + 8u * static_cast<size_t>(p.wn);          // pend entry + pool row
+    const size_t fixed = static_cast<size_t>(p.off_pend) + lbb + 32u;    // alignment slack
+    if (budget < fixed + 32u * per_row) return false;
+    size_t C = (budget - fixed) / per_row;
+    if (C > static_cast<size_t>(c->m)) C = static_cast<size_t>(c->m);
+    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
+        const long v = std::atol(env);
+        if (v > 0 && static_cast<size_t>(v) < C) C = static_cast<size_t>(v);
+    }
+    p.C = static_cast<int>(C);
+    p.off_lb = align16u(p.off_pend + 8u * p.C);
+    p.off_pool = align16u(p.off_lb + 4u * static_cast<uint32_t>(c->n));
+    p.region = align16u(p.off_pool + 8u * static_cast<uint32_t>(p.C) * static_cast<uint32_t>(p.wn));
+    p.warps = 1;
+    p.smem = static_cast<size_t>(p.image) + p.region;
+    if (p.smem > static_cast<size_t>(c->smem_optin)) return false;
+    const int64_t g = num_shots < c->sm_count ? num_shots : c->sm_count;
+    p.grid = static_cast<int>(g < 1 ? 1 : g);
+    p.lat = true;
+    *out = p;
+    return true;
+}
+
 WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, const OsdPlan *op,
                 const OsdWarpPlan *wp, const BpPlan *bp) {
     WsLayout w;
@@ -532,6 +569,8 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     if (rc) return rc;
     if (prm->osd) {
         if (wp.ok) {
+            OsdWarpPlan lp;
+            if (plan_osd_lat(c, B, wp, &lp)) wp = lp;
             OsdWarpArgs ow;
             std::memset(&ow, 0, sizeof(ow));
             ow.image = c->d_image;
@@ -548,10 +587,16 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             ow.off_tmp = wp.off_tmp; ow.off_hist = wp.off_hist;
             ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
             ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
-            rc = set_smem(osd_warp_kernel<kOsdMaxWarps>, wp.smem);
+            ow.off_lb = wp.off_lb; ow.off_pool = wp.off_pool;
+            rc = wp.lat ? set_smem(osd_warp_kernel<1, true>, wp.smem)
+                        : set_smem(osd_warp_kernel<kOsdMaxWarps, false>, wp.smem);
             if (rc) return rc;
             void *tw = timing_begin(stream);
-            osd_warp_kernel<kOsdMaxWarps><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
+            if (wp.lat) {
+                osd_warp_kernel<1, true><<<wp.grid, 32, wp.smem, stream>>>(ow);
+            } else {
+                osd_warp_kernel<kOsdMaxWarps, false><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
+            }
             timing_end(tw, stream, kTimeOsd);
             rc = check_launch();
             if (rc) return rc;

@@ -28,6 +28,10 @@
 //    the CSR image of H.  Measured: about 40 changed rows per shot on the d=11
 //    space-time code.  A shot that needs more than C rows goes to the
 //    block-wide kernel K_osd, which computes the same e.
+//  * Latency layout (kLat, for batches of at most one shot per SM): one warp
+//    per CTA, whose shared memory also holds the order bits of the shot's
+//    lambda (read once, coalesced) and the dense-row pool, so every step of
+//    the event chain is a shared-memory access instead of an L2 round trip.
 //  * Backward substitution over the pivots in reverse order, 32 per batch:
 //    each lane folds in the solution bits of later batches and records which
 //    pivots of its own batch its row touches (changed rows are scanned by the
@@ -40,6 +44,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "osd_kernel.cuh"
 
 namespace lbp {
 
@@ -59,14 +64,16 @@ struct OsdWarpArgs {
     uint32_t region_bytes;         // per-warp shared memory
     uint32_t off_keys, off_tmp, off_hist, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow,
         off_pend;             // off_tmp and off_hist (radix sort) overlap pivk / pcol / prow
+    uint32_t off_lb, off_pool;     // latency layout: lambda order bits [n], dense-row pool [C][wn]
 };
 
 constexpr uint64_t kNoKey = ~0ull;
 
-// 48-bit column key: order-preserving bits of lambda (ties: column index).
-__device__ __forceinline__ uint64_t col_key(const float *lam, int v) {
-    const uint32_t u = __float_as_uint(__fadd_rn(__ldg(lam + v), 0.0f));   // -0 -> +0
-    const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+// 48-bit column key: order-preserving bits of lambda (ties: column index),
+// from lambda in global memory or from its order bits lb in shared memory.
+template <bool kLat>
+__device__ __forceinline__ uint64_t col_key(const float *lam, const uint32_t *lb, int v) {
+    const uint32_t o = kLat ? lb[v] : order_bits(__ldg(lam + v));
     return (static_cast<uint64_t>(o) << 16) | static_cast<uint32_t>(v);
 }
 
@@ -79,7 +86,7 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
     return x;
 }
 
-template <int MaxWarps>
+template <int MaxWarps, bool kLat>
 __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     {
@@ -109,7 +116,9 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     uint16_t *pcol = reinterpret_cast<uint16_t *>(reg + a.off_pcol);     // [m] column of pivot k
     uint16_t *prow = reinterpret_cast<uint16_t *>(reg + a.off_prow);     // [m] row of pivot k
     uint64_t *pend = reinterpret_cast<uint64_t *>(reg + a.off_pend);     // [C] waiting changed rows
-    uint64_t *slots = a.slots + static_cast<size_t>(gw) * a.C * a.wn;
+    uint32_t *lb = kLat ? reinterpret_cast<uint32_t *>(reg + a.off_lb) : nullptr;  // [n] lambda order bits
+    uint64_t *slots = kLat ? reinterpret_cast<uint64_t *>(reg + a.off_pool)
+                           : a.slots + static_cast<size_t>(gw) * a.C * a.wn;
 
     const int m = a.m, n = a.n, wn = a.wn, C = a.C;
     const int W32 = (m + 31) >> 5;
@@ -119,12 +128,17 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     for (uint32_t q = gw; q < queue; q += total) {
         const uint32_t b = a.osd_list[q];
         const float *lam = a.osd_llr + static_cast<size_t>(q) * n;
+        if (kLat) {
+            #pragma unroll 4
+            for (int v = lane; v < n; v += 32) lb[v] = order_bits(__ldg(lam + v));
+            __syncwarp();
+        }
 
         // ---- rows keyed by their first column, sorted -----------------------
         for (int r = lane; r < m; r += 32) {
             uint64_t k = kNoKey;
             for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-                const uint64_t kc = col_key(lam, col_idx[e]);
+                const uint64_t kc = col_key<kLat>(lam, lb, col_idx[e]);
                 k = kc < k ? kc : k;
             }
             if (k != kNoKey) k = (k << 16) | static_cast<uint32_t>(r);
@@ -316,7 +330,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                             while (x) {
                                 const int bit = __ffsll(static_cast<long long>(x)) - 1;
                                 x &= x - 1;
-                                const uint64_t kc = col_key(lam, w * 64 + bit);
+                                const uint64_t kc = col_key<kLat>(lam, lb, w * 64 + bit);
                                 kmin = kc < kmin ? kc : kmin;
                             }
                         }

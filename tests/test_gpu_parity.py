@@ -228,6 +228,31 @@ def test_osd_pool_overflow_falls_back_to_block_kernel(pool, monkeypatch):
         assert (g["osd"] != lbp.LBP_OSD_NOT_RUN).sum() > 10
 
 
+@pytest.mark.parametrize("pool", [None, "2"])
+def test_osd_latency_layout_small_batches(pool, monkeypatch):
+    """Batches of at most one shot per SM run K_osd_warp's latency layout (one
+    warp per CTA, lambda order bits and the row pool in shared memory): the
+    same outputs as the oracle and as the throughput layout; with a 2-row pool
+    most shots overflow to K_osd, still bit-identical."""
+    if pool:
+        monkeypatch.setenv("LBP_OSD_POOL_ROWS", pool)
+    hz, _ = rotated_surface(13)
+    st = spacetime(hz, 13)
+    pri = spacetime_priors(hz, 13, 0.006, 0.006)
+    cases = [(st, pri, lbp.LBP_MSG_I8), (workloads.c3_bb144(0.05).h, np.full(144, 0.05), lbp.LBP_MSG_F16)]
+    for h, pri_h, msg in cases:
+        _, syn = sampler.sample(h, pri_h, seed=32, num_shots=100)
+        kw = dict(max_iter=100, lottery=1, osd=1, msg=msg, seed=6)
+        g = gpu_decode(h, pri_h, syn, **kw)
+        assert (g["osd"] != lbp.LBP_OSD_NOT_RUN).sum() >= 8
+        assert_parity(g, oracle_decode(h, pri_h, syn, **kw))
+        monkeypatch.setenv("LBP_OSD_LAT", "0")
+        t = gpu_decode(h, pri_h, syn, **kw)
+        monkeypatch.delenv("LBP_OSD_LAT")
+        for k in ("err", "conv", "iters", "osd"):
+            assert np.array_equal(g[k], t[k]), k
+
+
 def test_general_kernel_on_high_degree_code():
     """Row weights up to 12 and column weights up to 7 exceed the bounded-degree
     layout, so this runs the general CSR kernel."""
