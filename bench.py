@@ -398,6 +398,7 @@ def run_gpu(args):
 
     if not args.no_extras and rank == 0 and world == 1:
         line["serving"] = run_serving()
+        line["serving_one_launch_fifo"] = run_serving(policy=(0, False))
         line["matched_ler"] = run_matched()
         line["precision"] = run_precision()
         line["lottery_design_space"] = run_policies()
@@ -421,14 +422,17 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11):
+def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11, policy=None):
     """Serving mix: Poisson arrivals of 1-4096-shot requests over ten resident
     codes (rotated surface space-time d = 5..17 with d rounds, BB 72/144/288
     code capacity) and five noise levels 1e-3..5e-3; Lottery BP + OSD-0,
     I = 100, INT8 messages.  Capacity first (all requests queued at once), then
     open-loop arrivals at 50 / 80 / 95 % of it.  Messages are Int3.4 (INT8),
     the format the paper's hardware uses; FP16 messages roughly double the
-    lottery's OSD invoke rate on these surface codes."""
+    lottery's OSD invoke rate on these surface codes.  policy: None for the
+    server's default scheduling (launches of at most 16 Mi edge-shots,
+    single-launch requests on a high-priority stream), or (chunk_work,
+    priority) for lbp_server_configure."""
     import torch
     from paper_2605_00038_gb300 import lbp
     from paper_2605_00038_gb300.decoder import Decoder
@@ -465,6 +469,8 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
                          prm=dec.params(max_iter=100, lottery=1, osd=1, msg=2, seed=seed,
                                         shot_offset=i << 16)))
     srv = lbp.lbp_server_create(8 << 30, 16)
+    if policy is not None:
+        lbp.lbp_server_configure(srv, policy[0], policy[1])
 
     def submit(r):
         return lbp.lbp_server_submit(srv, decs[(r["ci"], r["pi"])].code, r["prm"], r["B"], r["syn"],
@@ -480,7 +486,9 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     dt = time.perf_counter() - t0
     total_shots = sum(r["B"] for r in reqs)
     cap_req = len(reqs) / dt
-    out = {"codes": len(codes), "noise_levels": len(ps), "requests": len(reqs),
+    out = {"policy": ("chunk_work 16 Mi edge-shots, priority" if policy is None else
+                      "chunk_work %d, priority %d" % (policy[0], int(policy[1]))),
+           "codes": len(codes), "noise_levels": len(ps), "requests": len(reqs),
            "mean_request_shots": total_shots / len(reqs), "capacity_shots_per_s": total_shots / dt,
            "capacity_requests_per_s": cap_req, "rates": []}
     for load in (0.5, 0.8, 0.95):

@@ -163,9 +163,9 @@ int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r
  * more rows is solved by the block-wide OSD kernel instead, with the same
  * result.  Set it identically for lbp_workspace_size and lbp_decode.
  * A call with num_shots at most the SM count runs OSD in its latency layout
- * (one warp per CTA, lambda and the pool in shared memory, C as many rows
- * as fit, capped by LBP_OSD_POOL_ROWS); LBP_OSD_LAT=0 turns that off.  The
- * workspace size does not depend on it. */
+ * (one warp per CTA; lambda and the first pool rows that fit in shared
+ * memory, the other rows of the same C in the workspace); LBP_OSD_LAT=0
+ * turns that off.  The workspace size does not depend on it. */
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).
@@ -239,6 +239,21 @@ typedef struct lbp_server lbp_server;
 /* Create a server on the current device.  Errors: LBP_EINVAL (arena_bytes <
  * 4096 or max_inflight outside [1, 64]), LBP_ENOMEM, LBP_ECUDA. */
 int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_server **out);
+
+/* Scheduling policy (defaults: chunk_work = 16 Mi edge-shots, priority = 1).
+ * The decode kernels are persistent, so a launch holds its SMs until it ends.
+ * A request of more than chunk_work edge-shots (num_shots x nnz(H)) runs as
+ * consecutive launches of at most that much work, each shot keeping its own
+ * draws (shot_offset advances), so work that arrives meanwhile waits for one
+ * launch, not the whole request; chunk_work = 0 keeps one launch per request.
+ * With priority = 1, requests that fit one launch run on a high-priority
+ * stream and start ahead of queued chunks of larger requests.  Results do
+ * not depend on the policy.  Applies to requests admitted after the call.
+ * A request of at most one shot per SM takes lbp_decode's small-batch
+ * latency layouts only when nothing else is in flight, since they hold
+ * whole SMs; otherwise it runs the throughput layouts.
+ * Errors: LBP_EINVAL (chunk_work < 0, priority not 0 or 1). */
+int lbp_server_configure(lbp_server *server, int64_t chunk_work, int priority);
 
 /* Queue a decode (buffers as for lbp_decode_host, osd_out may be NULL) and
  * return its ticket.  LBP_E2BIG if the request can never fit the arena. */

@@ -85,9 +85,13 @@ namespace lbp {
 // The decode path behind lbp_decode: plan, workspace layout and launches of
 // K_bp and the OSD kernels on `stream`, using `ws_bytes` bytes at `ws`
 // (device, 256-byte aligned) as scratch.  Parameters are already validated.
+// alone: nothing else runs on the device meanwhile, so a batch of at most one
+// shot per SM may take the latency layouts (a CTA per shot with up to 1024
+// BP threads; OSD with one warp and the whole shared memory per CTA), which
+// would crowd out concurrent work.
 int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                   uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
-                  void *ws, size_t ws_bytes, cudaStream_t stream);
+                  void *ws, size_t ws_bytes, cudaStream_t stream, bool alone = true);
 
 // Same, with an explicit BP launch shape (groups per CTA, threads per group;
 // 0, 0 = the code's tuned or default shape) and graph form (1 index image,
@@ -97,7 +101,7 @@ int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uin
 int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                          uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                          void *ws, size_t ws_bytes, cudaStream_t stream, int groups, int G,
-                         float *bp_ms, int graph = 0);
+                         float *bp_ms, int graph = 0, bool alone = true);
 
 }  // namespace lbp
 

@@ -65,6 +65,7 @@ struct OsdWarpPlan {
     uint32_t image = 0, region = 0, off_keys = 0, off_tmp = 0, off_hist = 0, off_rflag = 0, off_pivk = 0,
              off_pivb = 0, off_saug = 0, off_x = 0, off_pcol = 0, off_prow = 0, off_pend = 0;
     uint32_t off_lb = 0, off_pool = 0;
+    int Cs = 0;
     bool lat = false;
     size_t smem = 0;
 };
@@ -112,7 +113,7 @@ int graph_form(const lbp_code *c, int mi, int req_graph, size_t state_bytes) {
 }
 
 int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out, int req_S = 0,
-            int req_G = 0, int req_graph = 0) {
+            int req_G = 0, int req_graph = 0, bool alone = true) {
     const int W32 = (c->m + 31) / 32;
     const int mi = tuned_slot(msg, rule);
     BpPlan p;
@@ -253,12 +254,13 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
         S = s_req < S_fit ? s_req : S_fit;
     } else if (num_shots <= c->sm_count) {
         // A batch that does not fill the GPU: one shot per CTA, for the
-        // lowest latency (the SMs would idle anyway).  The ELL kernel gets a
-        // thread per column pair, up to 1024: at this size an iteration's
-        // time is the latency of its dependent steps, not its instructions.
+        // lowest latency (the SMs would idle anyway).  Alone on the device,
+        // the ELL kernel gets a thread per column pair, up to 1024: at this
+        // size an iteration's time is the latency of its dependent steps,
+        // not its instructions.
         S = 1;
         G = 256;
-        while (p.ell && G < 1024 && G < (c->ell.Np + 1) / 2) G *= 2;
+        while (alone && p.ell && G < 1024 && G < (c->ell.Np + 1) / 2) G *= 2;
     }
     if (!p.ell && G != 32 && G != 64 && G != 128 && G != 256) G = 128;
     if (S * G > 1024) S = 1024 / G;
@@ -356,9 +358,10 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
 }
 
 // Latency layout of K_osd_warp, for a batch of at most one shot per SM: one
-// warp per CTA, whose region also holds lambda's order bits [n] and a pool of
-// as many dense rows as fit (at most m), so the event chain never leaves
-// shared memory.  LBP_OSD_LAT=0 turns it off; LBP_OSD_POOL_ROWS caps C.
+// warp per CTA, whose region also holds lambda's order bits [n] and the first
+// Cs rows of the dense-row pool (as many as fit, at most C); the pool keeps
+// the throughput layout's C rows, the rest in the workspace, so no more shots
+// overflow to K_osd.  LBP_OSD_LAT=0 turns it off.
 bool plan_osd_lat(const lbp_code *c, int64_t num_shots, const OsdWarpPlan &wp, OsdWarpPlan *out) {
     if (!wp.ok || num_shots > c->sm_count) return false;
     if (const char *env = std::getenv("LBP_OSD_LAT")) {
@@ -366,20 +369,14 @@ bool plan_osd_lat(const lbp_code *c, int64_t num_shots, const OsdWarpPlan &wp, O
     }
     OsdWarpPlan p = wp;
     const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
-    const size_t lbb = align16u(4u * static_cast<uint32_t>(c->n));
-    const size_t per_row = 8u + 8u * static_cast<size_t>(p.wn);          // pend entry + pool row
-    const size_t fixed = static_cast<size_t>(p.off_pend) + lbb + 32u;    // alignment slack
-    if (budget < fixed + 32u * per_row) return false;
-    size_t C = (budget - fixed) / per_row;
-    if (C > static_cast<size_t>(c->m)) C = static_cast<size_t>(c->m);
-    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
-        const long v = std::atol(env);
-        if (v > 0 && static_cast<size_t>(v) < C) C = static_cast<size_t>(v);
-    }
-    p.C = static_cast<int>(C);
-    p.off_lb = align16u(p.off_pend + 8u * p.C);
-    p.off_pool = align16u(p.off_lb + 4u * static_cast<uint32_t>(c->n));
-    p.region = align16u(p.off_pool + 8u * static_cast<uint32_t>(p.C) * static_cast<uint32_t>(p.wn));
+    const uint32_t lbb = align16u(4u * static_cast<uint32_t>(c->n));
+    p.off_lb = p.region;                       // after pend [C], as in the throughput layout
+    p.off_pool = align16u(p.off_lb + lbb);
+    if (budget < static_cast<size_t>(p.off_pool) + 8u * static_cast<size_t>(p.wn)) return false;
+    size_t Cs = (budget - p.off_pool) / (8u * static_cast<size_t>(p.wn));
+    if (Cs > static_cast<size_t>(p.C)) Cs = static_cast<size_t>(p.C);
+    p.Cs = static_cast<int>(Cs);
+    p.region = align16u(p.off_pool + 8u * static_cast<uint32_t>(p.Cs) * static_cast<uint32_t>(p.wn));
     p.warps = 1;
     p.smem = static_cast<size_t>(p.image) + p.region;
     if (p.smem > static_cast<size_t>(c->smem_optin)) return false;
@@ -459,17 +456,17 @@ namespace lbp {
 
 int decode_device(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                   uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
-                  void *ws, size_t ws_bytes, cudaStream_t stream) {
+                  void *ws, size_t ws_bytes, cudaStream_t stream, bool alone) {
     return decode_device_shaped(c, prm, B, syn, err, conv, osd_out, iters, llr, ws, ws_bytes, stream,
-                                0, 0, nullptr);
+                                0, 0, nullptr, 0, alone);
 }
 
 int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, const uint64_t *syn,
                          uint64_t *err, uint8_t *conv, uint8_t *osd_out, int32_t *iters, float *llr,
                          void *ws, size_t ws_bytes, cudaStream_t stream, int req_S, int req_G,
-                         float *bp_ms, int req_graph) {
+                         float *bp_ms, int req_graph, bool alone) {
     BpPlan bp;
-    int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G, req_graph);
+    int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G, req_graph, alone);
     if (rc) return rc;
     OsdPlan op;
     OsdWarpPlan wp;
@@ -570,7 +567,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     if (prm->osd) {
         if (wp.ok) {
             OsdWarpPlan lp;
-            if (plan_osd_lat(c, B, wp, &lp)) wp = lp;
+            if (alone && plan_osd_lat(c, B, wp, &lp)) wp = lp;
             OsdWarpArgs ow;
             std::memset(&ow, 0, sizeof(ow));
             ow.image = c->d_image;
@@ -587,7 +584,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             ow.off_tmp = wp.off_tmp; ow.off_hist = wp.off_hist;
             ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
             ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
-            ow.off_lb = wp.off_lb; ow.off_pool = wp.off_pool;
+            ow.off_lb = wp.off_lb; ow.off_pool = wp.off_pool; ow.Cs = wp.Cs;
             rc = wp.lat ? set_smem(osd_warp_kernel<1, true>, wp.smem)
                         : set_smem(osd_warp_kernel<kOsdMaxWarps, false>, wp.smem);
             if (rc) return rc;

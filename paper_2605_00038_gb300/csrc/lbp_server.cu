@@ -14,6 +14,16 @@
 // Each request's results depend only on its code, parameters (seed and
 // shot_offset included) and syndromes, never on what else is in flight.
 //
+// Latency under load: the decode kernels are persistent (one CTA per SM
+// loops over the shots), so a launch holds the SMs it got until it ends and
+// work queued behind it waits that long.  Two rules bound the wait:
+//  * a request larger than chunk_work edge-shots (shots x nnz(H)) runs as
+//    consecutive launches of at most that much work on its stream, with
+//    shot_offset advanced so every shot draws as it would in one launch;
+//  * a request that fits one launch runs on a high-priority stream, so the
+//    block scheduler starts it ahead of queued chunks of larger requests.
+// lbp_server_configure sets both.
+//
 // The arena is one cudaMalloc made at creation; admission uses first-fit over
 // it, so no allocation happens while serving.
 #include <algorithm>
@@ -52,7 +62,8 @@ struct Request {
 };
 
 struct Slot {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // normal priority
+    cudaStream_t stream_hi = nullptr;   // highest priority
     cudaEvent_t done = nullptr;
     bool busy = false;
     Request req;
@@ -97,8 +108,16 @@ struct Layout {
     size_t syn, err, conv, osd, iters, ws, ws_bytes, total;
 };
 
-bool request_layout(const lbp_code *c, const lbp_params *p, int64_t B, Layout *L) {
-    const size_t wsz = lbp_workspace_size(c, p, B);
+// Shots per launch: chunk_work edge-shots, at least one shot; 0 = no limit.
+int64_t chunk_shots(const lbp_code *c, int64_t chunk_work, int64_t B) {
+    if (chunk_work <= 0) return B;
+    const int64_t nnz = c->nnz > 0 ? c->nnz : 1;
+    const int64_t k = chunk_work / nnz;
+    return k < 1 ? 1 : (k < B ? k : B);
+}
+
+bool request_layout(const lbp_code *c, const lbp_params *p, int64_t B, int64_t chunk, Layout *L) {
+    const size_t wsz = lbp_workspace_size(c, p, chunk < B ? chunk : B);
     if (wsz == 0) return false;
     const size_t wm = (c->m + 63) / 64, wn = (c->n + 63) / 64;
     size_t off = 0;
@@ -124,6 +143,8 @@ struct lbp_server {
     std::map<int64_t, std::pair<int, double>> finished;   // ticket -> (status, latency s)
     std::map<int64_t, bool> known;                         // tickets not yet collected
     int64_t next_ticket = 1;
+    int64_t chunk_work = int64_t(16) << 20;   // edge-shots per launch (0: one launch per request)
+    bool priority = true;                      // single-launch requests on the high-priority stream
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
@@ -137,19 +158,29 @@ namespace {
 void launch(lbp_server *s, int si) {
     Slot &sl = s->slots[si];
     Request &r = sl.req;
+    const int64_t B = r.shots;
+    const int64_t chunk = chunk_shots(r.code, s->chunk_work, B);
     Layout L;
-    request_layout(r.code, &r.params, r.shots, &L);
+    request_layout(r.code, &r.params, B, chunk, &L);
     uint8_t *base = s->arena_base + r.arena_off;
     const size_t wm = (r.code->m + 63) / 64, wn = (r.code->n + 63) / 64;
-    const int64_t B = r.shots;
-    cudaStream_t st = sl.stream;
+    cudaStream_t st = (s->priority && chunk >= B) ? sl.stream_hi : sl.stream;
+    // The latency layouts of small batches take whole SMs; only a request
+    // that starts with nothing else in flight may use them.
+    bool alone = true;
+    for (size_t i = 0; i < s->slots.size(); ++i)
+        if (static_cast<int>(i) != si && s->slots[i].busy) alone = false;
     int rc = LBP_OK;
     if (cudaMemcpyAsync(base + L.syn, r.syn, 8 * wm * B, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = LBP_ECUDA;
-    if (rc == LBP_OK)
-        rc = lbp::decode_device(r.code, &r.params, B, reinterpret_cast<const uint64_t *>(base + L.syn),
-                                reinterpret_cast<uint64_t *>(base + L.err), base + L.conv, base + L.osd,
-                                reinterpret_cast<int32_t *>(base + L.iters), nullptr, base + L.ws,
-                                L.ws_bytes, st);
+    for (int64_t s0 = 0; rc == LBP_OK && s0 < B; s0 += chunk) {
+        const int64_t nb = chunk < B - s0 ? chunk : B - s0;
+        lbp_params p = r.params;
+        p.shot_offset += static_cast<uint64_t>(s0);
+        rc = lbp::decode_device(r.code, &p, nb, reinterpret_cast<const uint64_t *>(base + L.syn) + s0 * wm,
+                                reinterpret_cast<uint64_t *>(base + L.err) + s0 * wn, base + L.conv + s0,
+                                base + L.osd + s0, reinterpret_cast<int32_t *>(base + L.iters) + s0, nullptr,
+                                base + L.ws, L.ws_bytes, st, alone);
+    }
     if (rc == LBP_OK) {
         bool ok = cudaMemcpyAsync(r.err, base + L.err, 8 * wn * B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
         ok = ok && cudaMemcpyAsync(r.conv, base + L.conv, B, cudaMemcpyDeviceToHost, st) == cudaSuccess;
@@ -194,7 +225,7 @@ void run(lbp_server *s) {
             if (free_slot < 0) break;
             Request &r = s->waiting.front();
             Layout L;
-            request_layout(r.code, &r.params, r.shots, &L);
+            request_layout(r.code, &r.params, r.shots, chunk_shots(r.code, s->chunk_work, r.shots), &L);
             size_t off = 0;
             if (!s->arena.alloc(L.total, &off)) break;           // wait for memory to free up
             Slot &sl = s->slots[free_slot];
@@ -235,12 +266,19 @@ extern "C" int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_serve
     }
     s->arena.init(arena_bytes);
     s->slots.resize(max_inflight);
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
     for (auto &sl : s->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        if (cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             for (auto &x : s->slots) {
                 if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.stream_hi) cudaStreamDestroy(x.stream_hi);
                 if (x.done) cudaEventDestroy(x.done);
             }
             cudaFree(s->arena_base);
@@ -253,6 +291,14 @@ extern "C" int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_serve
     return LBP_OK;
 }
 
+extern "C" int lbp_server_configure(lbp_server *s, int64_t chunk_work, int priority) {
+    if (!s || chunk_work < 0 || (priority != 0 && priority != 1)) return LBP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->chunk_work = chunk_work;
+    s->priority = priority != 0;
+    return LBP_OK;
+}
+
 extern "C" int lbp_server_submit(lbp_server *s, const lbp_code *code, const lbp_params *params,
                                  int64_t num_shots, const uint64_t *syndromes, uint64_t *err_out,
                                  uint8_t *converged, uint8_t *osd_out, int32_t *iters_out,
@@ -261,9 +307,10 @@ extern "C" int lbp_server_submit(lbp_server *s, const lbp_code *code, const lbp_
         !iters_out)
         return LBP_EINVAL;
     if (code->device != s->device) return LBP_EINVAL;
-    Layout L;
-    if (!request_layout(code, params, num_shots, &L)) return LBP_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
+    Layout L;
+    if (!request_layout(code, params, num_shots, chunk_shots(code, s->chunk_work, num_shots), &L))
+        return LBP_EINVAL;
     if (L.total > s->arena.size) return LBP_E2BIG;            // can never be admitted
     if (s->stop) return LBP_EINVAL;
     Request r;
@@ -321,7 +368,9 @@ extern "C" int lbp_server_destroy(lbp_server *s) {
     if (s->worker.joinable()) s->worker.join();
     for (auto &sl : s->slots) {
         cudaStreamSynchronize(sl.stream);
+        cudaStreamSynchronize(sl.stream_hi);
         cudaStreamDestroy(sl.stream);
+        cudaStreamDestroy(sl.stream_hi);
         cudaEventDestroy(sl.done);
     }
     cudaFree(s->arena_base);

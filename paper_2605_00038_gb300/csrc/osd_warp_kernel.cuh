@@ -30,8 +30,10 @@
 //    block-wide kernel K_osd, which computes the same e.
 //  * Latency layout (kLat, for batches of at most one shot per SM): one warp
 //    per CTA, whose shared memory also holds the order bits of the shot's
-//    lambda (read once, coalesced) and the dense-row pool, so every step of
-//    the event chain is a shared-memory access instead of an L2 round trip.
+//    lambda (read once, coalesced) and the first Cs rows of the dense-row
+//    pool, so most steps of the event chain are shared-memory accesses
+//    instead of L2 round trips.  Rows past Cs stay in the workspace, so the
+//    pool holds as many rows as in the throughput layout.
 //  * Backward substitution over the pivots in reverse order, 32 per batch:
 //    each lane folds in the solution bits of later batches and records which
 //    pivots of its own batch its row touches (changed rows are scanned by the
@@ -64,7 +66,8 @@ struct OsdWarpArgs {
     uint32_t region_bytes;         // per-warp shared memory
     uint32_t off_keys, off_tmp, off_hist, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow,
         off_pend;             // off_tmp and off_hist (radix sort) overlap pivk / pcol / prow
-    uint32_t off_lb, off_pool;     // latency layout: lambda order bits [n], dense-row pool [C][wn]
+    uint32_t off_lb, off_pool;     // latency layout: lambda order bits [n], pool rows [Cs][wn]
+    int32_t Cs;                    // latency layout: pool rows in shared memory (0 otherwise)
 };
 
 constexpr uint64_t kNoKey = ~0ull;
@@ -117,8 +120,13 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     uint16_t *prow = reinterpret_cast<uint16_t *>(reg + a.off_prow);     // [m] row of pivot k
     uint64_t *pend = reinterpret_cast<uint64_t *>(reg + a.off_pend);     // [C] waiting changed rows
     uint32_t *lb = kLat ? reinterpret_cast<uint32_t *>(reg + a.off_lb) : nullptr;  // [n] lambda order bits
-    uint64_t *slots = kLat ? reinterpret_cast<uint64_t *>(reg + a.off_pool)
-                           : a.slots + static_cast<size_t>(gw) * a.C * a.wn;
+    uint64_t *gslots = a.slots + static_cast<size_t>(gw) * a.C * a.wn;
+    uint64_t *sslots = kLat ? reinterpret_cast<uint64_t *>(reg + a.off_pool) : nullptr;
+    const int Cs = kLat ? a.Cs : 0;
+    // Row s of the pool: shared memory for s < Cs, else the workspace.
+    auto pool_row = [&](int s) -> uint64_t * {
+        return (s < Cs ? sslots : gslots) + static_cast<size_t>(s) * a.wn;
+    };
 
     const int m = a.m, n = a.n, wn = a.wn, C = a.C;
     const int W32 = (m + 31) >> 5;
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                         if (s == 0xffff) {
                             if (nslots >= C) { overflow = true; break; }
                             s = nslots++;
-                            row = slots + static_cast<size_t>(s) * wn;
+                            row = pool_row(s);
                             for (int w = lane; w < wn; w += 32) row[w] = 0ull;
                             __syncwarp();
                             for (int e = row_ptr[rr] + lane; e < row_ptr[rr + 1]; e += 32) {
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                             if (lane == 0) rflag[rr] = static_cast<uint16_t>(s);
                             __syncwarp();
                         } else {
-                            row = slots + static_cast<size_t>(s) * wn;
+                            row = pool_row(s);
                         }
                         if (pslot == 0xffff) {
                             for (int e = row_ptr[p] + lane; e < row_ptr[p + 1]; e += 32) {
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                                 atomicXor(reinterpret_cast<unsigned int *>(row) + (u >> 5), 1u << (u & 31));
                             }
                         } else {
-                            const uint64_t *prw = slots + static_cast<size_t>(pslot) * wn;
+                            const uint64_t *prw = pool_row(pslot);
                             for (int w = lane; w < wn; w += 32) row[w] ^= prw[w];
                         }
                         __syncwarp();
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                     dense &= dense - 1u;
                     const int ss = __shfl_sync(0xffffffffu, slot, src);
                     const int k0 = lo + src;
-                    const uint64_t *row = slots + static_cast<size_t>(ss) * wn;
+                    const uint64_t *row = pool_row(ss);
                     unsigned mp = 0u, md = 0u;
                     for (int w = lane; w < wn; w += 32) {
                         uint64_t x = row[w];

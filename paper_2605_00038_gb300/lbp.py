@@ -27,8 +27,8 @@ LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface", "lbp_code_rounds",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
-            "lbp_server_create", "lbp_server_submit", "lbp_server_poll", "lbp_server_wait",
-            "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
+            "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
+            "lbp_server_wait", "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
             "lbp_strerror"]
 
 
@@ -85,6 +85,8 @@ def lib():
         L.lbp_tune.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, sz, vp]
         L.lbp_server_create.restype = ctypes.c_int
         L.lbp_server_create.argtypes = [sz, ctypes.c_int, ctypes.POINTER(vp)]
+        L.lbp_server_configure.restype = ctypes.c_int
+        L.lbp_server_configure.argtypes = [vp, i64, ctypes.c_int]
         L.lbp_server_submit.restype = ctypes.c_int
         L.lbp_server_submit.argtypes = [vp, vp, P, i64, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
         L.lbp_server_poll.restype = ctypes.c_int
@@ -293,6 +295,11 @@ def lbp_server_create(arena_bytes: int, max_inflight: int) -> Server:
     out = ctypes.c_void_p()
     _check(lib().lbp_server_create(arena_bytes, max_inflight, ctypes.byref(out)), "lbp_server_create")
     return Server(out.value)
+
+
+def lbp_server_configure(server: Server, chunk_work: int, priority: bool = True):
+    _check(lib().lbp_server_configure(server.ptr, int(chunk_work), int(bool(priority))),
+           "lbp_server_configure")
 
 
 def lbp_server_submit(server: Server, code: Code, params: lbp_params, num_shots: int, syndromes,

@@ -69,16 +69,22 @@ def _device_bytes(dec, r):
     return lbp.lbp_workspace_size(dec.code, prm, B) + io + 256
 
 
-@pytest.mark.parametrize("tight,inflight", [(False, 8), (True, 4)])
-def test_results_alone_equal_results_in_the_mix(tight, inflight):
+@pytest.mark.parametrize("tight,inflight,chunk", [(False, 8, None), (True, 4, None), (False, 8, 30000),
+                                                  (True, 3, 0)])
+def test_results_alone_equal_results_in_the_mix(tight, inflight, chunk):
     """tight: the arena holds about 1.5 of the largest request, so admission
-    waits for memory, not for a free stream."""
+    waits for memory, not for a free stream.  chunk: the server's chunk_work
+    (None: default; 30000 edge-shots splits most requests into many launches
+    on normal- and high-priority streams; 0: one launch per request, no
+    priorities)."""
     codes = _codes()
     decs = [Decoder(h, pri) for h, pri in codes]
     reqs = _requests(codes, 40, seed=int(tight))
     ref = [_alone(decs, codes, r) for r in reqs]
     arena = (512 << 20) if not tight else int(1.5 * max(_device_bytes(decs[r["ci"]], r) for r in reqs))
     srv = lbp.lbp_server_create(arena, inflight)
+    if chunk is not None:
+        lbp.lbp_server_configure(srv, chunk, chunk != 0)
     bufs = []
     for r in reqs:
         h = codes[r["ci"]][0]
@@ -114,6 +120,15 @@ def test_results_alone_equal_results_in_the_mix(tight, inflight):
         assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it)
     for d in decs:
         d.close()
+
+
+def test_configure_rejects_bad_policy():
+    srv = lbp.lbp_server_create(1 << 20, 2)
+    assert lbp.lib().lbp_server_configure(srv.ptr, -1, 1) == lbp.LBP_EINVAL
+    assert lbp.lib().lbp_server_configure(srv.ptr, 100, 2) == lbp.LBP_EINVAL
+    assert lbp.lib().lbp_server_configure(None, 100, 1) == lbp.LBP_EINVAL
+    lbp.lbp_server_configure(srv, 0, False)
+    srv.close()
 
 
 def test_request_larger_than_the_arena_is_refused():
