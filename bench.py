@@ -537,8 +537,10 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     """Matched-LER head-to-head on identical shots of the rotated d=7 surface
     code, 7 noisy rounds, p = 0.012: (A) plain NMS BP + OSD-0, FP32 messages,
     one batched lbp_decode; (B) Lottery BP + OSD-0, INT8 (Int3.4) messages, served in
-    4096-shot requests through lbp_server.  Logical error rates with Wilson
-    95% intervals and the paired McNemar test, throughput and p99 latency."""
+    4096-shot requests through lbp_server, with the proposed flip rule and
+    with the worst-check / least-reliable-column rule of Sec. III-B.  Logical
+    error rates with Wilson 95% intervals and the paired McNemar test against
+    (A), throughput and p50 / p99 request latency."""
     import torch
     from paper_2605_00038_gb300 import evaluate, lbp
     from paper_2605_00038_gb300.decoder import Decoder
@@ -565,47 +567,52 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
     torch.cuda.synchronize()
     ta = ev0.elapsed_time(ev1) / 1e3
     fa = evaluate.logical_failures(spec, true_d, ra.err, ra.converged, ra.osd)
-    # Arm B: Lottery BP + OSD-0, INT8, served.
-    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
-    hs = pin(syn.shape, torch.int64)
-    hs.numpy()[:] = syn.view(np.int64)
-    wn = (h.n + 63) // 64
-    herr, hconv, hosd, hit = pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8), pin(shots, torch.int32)
-    srv = lbp.lbp_server_create(8 << 30, 16)
-    reqs = []
-    for lo in range(0, shots, request):
-        B = min(request, shots - lo)
-        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=2, seed=seed, shot_offset=lo)
-        reqs.append((lo, B, prm))
-    lbp.lbp_server_wait(srv, lbp.lbp_server_submit(srv, dec.code, reqs[0][2], reqs[0][1], hs[:reqs[0][1]],
-                                                   herr[:reqs[0][1]], hconv[:reqs[0][1]], hosd[:reqs[0][1]],
-                                                   hit[:reqs[0][1]]))
-    t0 = time.perf_counter()
-    tks = [lbp.lbp_server_submit(srv, dec.code, prm, B, hs[lo:lo + B], herr[lo:lo + B], hconv[lo:lo + B],
-                                 hosd[lo:lo + B], hit[lo:lo + B]) for lo, B, prm in reqs]
-    lats = [lbp.lbp_server_wait(srv, t) for t in tks]
-    tb = time.perf_counter() - t0
-    srv.close()
-    fb = evaluate.logical_failures(spec, true_d, herr.cuda(), hconv.cuda(), hosd.cuda())
-    ka, kb = int(fa.sum().item()), int(fb.sum().item())
-    only_a = int((fa & ~fb).sum().item())
-    only_b = int((fb & ~fa).sum().item())
-    dec.close()
-    return {
+    ka = int(fa.sum().item())
+    out = {
         "workload": "rotated_d7_st7_p0.012", "shots": shots,
         "plain_bp_osd_fp32_batched": {
             "ler": ka / shots, "ler_ci95": evaluate.wilson(ka, shots), "shots_per_s": shots / ta,
             "latency_ms": ta * 1e3, "osd_invoke_rate": float((ra.osd != 0).float().mean().item()),
             "mean_iters": float(ra.iters.float().mean().item())},
-        "lottery_bp_osd_int8_served": {
-            "ler": kb / shots, "ler_ci95": evaluate.wilson(kb, shots), "shots_per_s": shots / tb,
-            "request_shots": request, "p50_ms": float(np.quantile(lats, 0.5) * 1e3),
-            "p99_ms": float(np.quantile(lats, 0.99) * 1e3),
-            "osd_invoke_rate": float((hosd != 0).float().mean().item()),
-            "mean_iters": float(hit.float().mean().item())},
-        "ler_relative_difference": (kb - ka) / max(ka, 1), "mcnemar_discordant": [only_a, only_b],
-        "mcnemar_p": evaluate.mcnemar_p(only_a, only_b),
     }
+    # Arms B: Lottery BP + OSD-0, INT8, served.
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+    hs = pin(syn.shape, torch.int64)
+    hs.numpy()[:] = syn.view(np.int64)
+    wn = (h.n + 63) // 64
+    herr, hconv, hosd, hit = pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8), pin(shots, torch.int32)
+    for key, policy in (("lottery_bp_osd_int8_served", lbp.LBP_LOTTERY_PROPOSED),
+                        ("lottery_worst_unreliable_bp_osd_int8_served", lbp.LBP_LOTTERY_WORST_UNRELIABLE)):
+        srv = lbp.lbp_server_create(8 << 30, 16)
+        reqs = []
+        for lo in range(0, shots, request):
+            B = min(request, shots - lo)
+            prm = dec.params(max_iter=100, lottery=1, lottery_policy=policy, osd=1, msg=2, seed=seed,
+                             shot_offset=lo)
+            reqs.append((lo, B, prm))
+        lbp.lbp_server_wait(srv, lbp.lbp_server_submit(srv, dec.code, reqs[0][2], reqs[0][1], hs[:reqs[0][1]],
+                                                       herr[:reqs[0][1]], hconv[:reqs[0][1]],
+                                                       hosd[:reqs[0][1]], hit[:reqs[0][1]]))
+        t0 = time.perf_counter()
+        tks = [lbp.lbp_server_submit(srv, dec.code, prm, B, hs[lo:lo + B], herr[lo:lo + B], hconv[lo:lo + B],
+                                     hosd[lo:lo + B], hit[lo:lo + B]) for lo, B, prm in reqs]
+        lats = [lbp.lbp_server_wait(srv, t) for t in tks]
+        tb = time.perf_counter() - t0
+        srv.close()
+        fb = evaluate.logical_failures(spec, true_d, herr.cuda(), hconv.cuda(), hosd.cuda())
+        kb = int(fb.sum().item())
+        only_a = int((fa & ~fb).sum().item())
+        only_b = int((fb & ~fa).sum().item())
+        out[key] = {
+            "policy": policy, "ler": kb / shots, "ler_ci95": evaluate.wilson(kb, shots),
+            "shots_per_s": shots / tb, "request_shots": request,
+            "p50_ms": float(np.quantile(lats, 0.5) * 1e3), "p99_ms": float(np.quantile(lats, 0.99) * 1e3),
+            "osd_invoke_rate": float((hosd != 0).float().mean().item()),
+            "mean_iters": float(hit.float().mean().item()),
+            "ler_relative_difference": (kb - ka) / max(ka, 1), "mcnemar_discordant": [only_a, only_b],
+            "mcnemar_p": evaluate.mcnemar_p(only_a, only_b)}
+    dec.close()
+    return out
 
 
 def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int = 31):
