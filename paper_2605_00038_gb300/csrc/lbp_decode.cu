@@ -320,7 +320,13 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     p.off_rflag = off; off = align16u(off + 2u * c->m);
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);
-    p.off_x = off;     off = align16u(off + 8u * p.wn);
+    // The solution bits are written after the elimination, when the sorted
+    // keys are dead: they share the keys' bytes when they fit there.
+    if (p.wn <= c->m) {
+        p.off_x = p.off_keys;
+    } else {
+        p.off_x = off;  off = align16u(off + 8u * p.wn);
+    }
     p.off_pend = off;
     p.image = c->img.off_col_ptr;             // row_ptr and col_idx only
     const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;

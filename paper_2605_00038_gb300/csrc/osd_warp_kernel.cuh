@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     uint16_t *pivk = reinterpret_cast<uint16_t *>(reg + a.off_pivk);     // [n] pivot index of column
     uint32_t *pivb = reinterpret_cast<uint32_t *>(reg + a.off_pivb);     // [W32] row is a pivot
     uint32_t *saug = reinterpret_cast<uint32_t *>(reg + a.off_saug);     // [W32] reduced syndrome
-    uint64_t *X = reinterpret_cast<uint64_t *>(reg + a.off_x);           // [wn] solution by column
+    uint64_t *X = reinterpret_cast<uint64_t *>(reg + a.off_x);           // [wn] solution (may alias keys)
     uint32_t *X32 = reinterpret_cast<uint32_t *>(X);
     uint16_t *pcol = reinterpret_cast<uint16_t *>(reg + a.off_pcol);     // [m] column of pivot k
     uint16_t *prow = reinterpret_cast<uint16_t *>(reg + a.off_prow);     // [m] row of pivot k
@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             saug[w] = x;
             pivb[w] = 0u;
         }
-        for (int w = lane; w < wn; w += 32) X[w] = 0ull;
         __syncwarp();
         // Stable LSD radix sort of keys[0, m) on bits 16..63, 8 bits a pass;
         // six passes leave the result in keys.
@@ -392,6 +391,10 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             __syncwarp();
             continue;
         }
+
+        // The solution bits may share the sorted keys' bytes, dead from here on.
+        for (int w = lane; w < wn; w += 32) X[w] = 0ull;
+        __syncwarp();
 
         // ---- consistency: rows without a pivot must end with s' = 0 ---------------
         unsigned bad = 0u;
