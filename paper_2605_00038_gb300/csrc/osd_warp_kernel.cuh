@@ -80,13 +80,14 @@ __device__ __forceinline__ uint64_t col_key(const float *lam, const uint32_t *lb
     return (static_cast<uint64_t>(o) << 16) | static_cast<uint32_t>(v);
 }
 
+// Warp minimum of a 64-bit key: the least high word, then the least low word
+// among the lanes holding it (two redux.sync; every lane takes part in both).
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
-        x = y < x ? y : x;
-    }
-    return x;
+    const uint32_t hi = static_cast<uint32_t>(x >> 32);
+    const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t lo = hi == mhi ? static_cast<uint32_t>(x) : 0xffffffffu;
+    const uint32_t mlo = __reduce_min_sync(0xffffffffu, lo);
+    return (static_cast<uint64_t>(mhi) << 32) | mlo;
 }
 
 template <int MaxWarps, bool kLat>
@@ -271,9 +272,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                 const int j = j0 + lane;
                 if (j < npend && (pend[j] >> 16) == Kev) best = min(best, static_cast<int>(pend[j] & 0xffffu));
             }
-            #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-            const int p = best;
+            const int p = __reduce_min_sync(0xffffffffu, best);
             const unsigned sp_bit = (saug[p >> 5] >> (p & 31)) & 1u;
             const int pslot = rflag[p];
             // Every other candidate r: r <- r + row p, then it waits at its next
