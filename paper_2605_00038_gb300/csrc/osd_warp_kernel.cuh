@@ -350,7 +350,9 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                     }
                 }
             }
-            // Drop the waiting entries consumed by this event.
+            // Drop the waiting entries consumed by this event; the smallest
+            // key among those kept is the next pending event.
+            uint64_t mn = kNoKey;
             if (!overflow) {
                 int kept = 0;
                 for (int j0 = 0; j0 < npend; j0 += 32) {
@@ -359,7 +361,10 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                     const bool keep = j < npend && (e >> 16) != Kev;
                     const unsigned bk = __ballot_sync(0xffffffffu, keep);
                     __syncwarp();
-                    if (keep) pend[kept + __popc(bk & ((1u << lane) - 1u))] = e;
+                    if (keep) {
+                        pend[kept + __popc(bk & ((1u << lane) - 1u))] = e;
+                        mn = e < mn ? e : mn;
+                    }
                     kept += __popc(bk);
                     __syncwarp();
                 }
@@ -375,10 +380,6 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             }
             ++rank;
             ptr += nsorted;
-            // Smallest waiting key.
-            uint64_t mn = kNoKey;
-            for (int j = lane; j < npend; j += 32) mn = pend[j] < mn ? pend[j] : mn;
-            __syncwarp();
             pmin = warp_min_u64(mn);
         }
 
