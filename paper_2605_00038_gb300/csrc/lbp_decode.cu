@@ -307,32 +307,36 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     const int W32 = (c->m + 31) / 32;
     uint32_t off = 0;
     p.off_keys = off;  off = align16u(off + 8u * c->m);
-    // The radix sort's buffer shares its bytes with the pivot arrays, which
-    // are first written after the sort ...
+    // Only the keys and the radix sort's buffer and digit histogram are live
+    // during the sort; the elimination's arrays, first written after it,
+    // share their bytes.
     const uint32_t u0 = off;
     p.off_tmp = u0;
-    p.off_pivk = off;  off = align16u(off + 2u * c->n);
+    p.off_hist = u0 + align16u(8u * c->m);
+    const uint32_t sort_end = p.off_hist + 4u * 256;
     p.off_pcol = off;  off = align16u(off + 2u * c->m);
     p.off_prow = off;  off = align16u(off + 2u * c->m);
-    // ... and so does its digit histogram, placed after the buffer.
-    p.off_hist = u0 + align16u(8u * c->m);
-    if (off < p.off_hist + 4u * 256) off = p.off_hist + 4u * 256;
     p.off_rflag = off; off = align16u(off + 2u * c->m);
     p.off_pivb = off;  off = align16u(off + 4u * W32);
     p.off_saug = off;  off = align16u(off + 4u * W32);
-    // The solution bits are written after the elimination, when the sorted
-    // keys are dead: they share the keys' bytes when they fit there.
-    if (p.wn <= c->m) {
-        p.off_x = p.off_keys;
-    } else {
-        p.off_x = off;  off = align16u(off + 8u * p.wn);
-    }
     p.off_pend = off;
+    // The solution bits X [wn] and the column -> pivot index map [n], both
+    // built after the elimination, share the dead keys' bytes when they fit.
+    const uint32_t xb = align16u(8u * static_cast<uint32_t>(p.wn));
+    const bool in_keys = xb + 2u * static_cast<uint32_t>(c->n) <= 8u * static_cast<uint32_t>(c->m);
+    // End of the arrays live during the sort or the elimination.
+    auto live_end = [&](int C) -> uint32_t {
+        const uint32_t end = align16u(p.off_pend + 8u * static_cast<uint32_t>(C));
+        return end > align16u(sort_end) ? end : align16u(sort_end);
+    };
+    auto region_for = [&](int C) -> uint32_t {
+        const uint32_t end = live_end(C);
+        return in_keys ? end : align16u(end + xb + 2u * static_cast<uint32_t>(c->n));
+    };
     p.image = c->img.off_col_ptr;             // row_ptr and col_idx only
     const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
     auto warps_for = [&](int C) {
-        const size_t region = align16u(p.off_pend + 8u * C);
-        const size_t w = budget / region;
+        const size_t w = budget / region_for(C);
         return static_cast<int>(w < kOsdMaxWarps ? w : kOsdMaxWarps);
     };
     // Pool rows C (changed rows a shot may hold before it is handed to
@@ -352,7 +356,9 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
         if (static_cast<size_t>(C) > cap) C = cap > static_cast<size_t>(floor_c) ? static_cast<int>(cap) : floor_c;
     }
     p.C = C;
-    p.region = align16u(p.off_pend + 8u * C);
+    p.region = region_for(C);
+    p.off_x = in_keys ? p.off_keys : live_end(C);
+    p.off_pivk = p.off_x + xb;
     if (static_cast<size_t>(p.region) * 2 > budget) { *out = p; return; }
     p.warps = warps_for(C);
     p.smem = p.image + static_cast<size_t>(p.warps) * p.region;

@@ -65,7 +65,8 @@ struct OsdWarpArgs {
     uint32_t image_bytes;          // bytes of the image prefix staged (row_ptr + col_idx)
     uint32_t region_bytes;         // per-warp shared memory
     uint32_t off_keys, off_tmp, off_hist, off_rflag, off_pivk, off_pivb, off_saug, off_x, off_pcol, off_prow,
-        off_pend;             // off_tmp and off_hist (radix sort) overlap pivk / pcol / prow
+        off_pend;             // off_tmp / off_hist (sort) overlap the elimination's arrays;
+                              // off_x / off_pivk (after it) may overlap the keys
     uint32_t off_lb, off_pool;     // latency layout: lambda order bits [n], pool rows [Cs][wn]
     int32_t Cs;                    // latency layout: pool rows in shared memory (0 otherwise)
 };
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
     uint64_t *tmp = reinterpret_cast<uint64_t *>(reg + a.off_tmp);       // [m] sort buffer
     uint32_t *hist = reinterpret_cast<uint32_t *>(reg + a.off_hist);     // [256] digit counts
     uint16_t *rflag = reinterpret_cast<uint16_t *>(reg + a.off_rflag);   // [m] dense slot or 0xffff
-    uint16_t *pivk = reinterpret_cast<uint16_t *>(reg + a.off_pivk);     // [n] pivot index of column
+    uint16_t *pivk = reinterpret_cast<uint16_t *>(reg + a.off_pivk);     // [n] pivot index of column (after)
     uint32_t *pivb = reinterpret_cast<uint32_t *>(reg + a.off_pivb);     // [W32] row is a pivot
     uint32_t *saug = reinterpret_cast<uint32_t *>(reg + a.off_saug);     // [W32] reduced syndrome
     uint64_t *X = reinterpret_cast<uint64_t *>(reg + a.off_x);           // [wn] solution (may alias keys)
@@ -152,14 +153,6 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             }
             if (k != kNoKey) k = (k << 16) | static_cast<uint32_t>(r);
             keys[r] = k;
-            rflag[r] = 0xffffu;
-        }
-        const uint32_t *sp = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
-        for (int w = lane; w < W32; w += 32) {
-            uint32_t x = sp[w];
-            if (w == W32 - 1 && (m & 31)) x &= (1u << (m & 31)) - 1u;
-            saug[w] = x;
-            pivb[w] = 0u;
         }
         __syncwarp();
         // Stable LSD radix sort of keys[0, m) on bits 16..63, 8 bits a pass;
@@ -210,7 +203,18 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                 __syncwarp();
             }
         }
-        for (int v = lane; v < n; v += 32) pivk[v] = 0xffffu;      // tmp is dead from here on
+        // The sort's buffer is dead from here on: its bytes become the
+        // elimination's row flags, pivot and syndrome bits.
+        for (int r = lane; r < m; r += 32) rflag[r] = 0xffffu;
+        {
+            const uint32_t *sp = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
+            for (int w = lane; w < W32; w += 32) {
+                uint32_t x = sp[w];
+                if (w == W32 - 1 && (m & 31)) x &= (1u << (m & 31)) - 1u;
+                saug[w] = x;
+                pivb[w] = 0u;
+            }
+        }
         __syncwarp();
 
         // ---- forward elimination, event by event ------------------------------
@@ -238,7 +242,6 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
                     const int v = static_cast<int>(Ki & 0xffffu);
                     pcol[rank + lane] = static_cast<uint16_t>(v);
                     prow[rank + lane] = static_cast<uint16_t>(r);
-                    pivk[v] = static_cast<uint16_t>(rank + lane);
                     atomicOr(&pivb[r >> 5], 1u << (r & 31));
                 }
                 rank += L;
@@ -375,7 +378,6 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             if (lane == 0) {
                 pcol[rank] = static_cast<uint16_t>(v);
                 prow[rank] = static_cast<uint16_t>(p);
-                pivk[v] = static_cast<uint16_t>(rank);
                 pivb[p >> 5] |= 1u << (p & 31);
             }
             ++rank;
@@ -392,8 +394,12 @@ __global__ void __launch_bounds__(MaxWarps * 32) osd_warp_kernel(const OsdWarpAr
             continue;
         }
 
-        // The solution bits may share the sorted keys' bytes, dead from here on.
+        // The solution bits and the column -> pivot index map may share the
+        // sorted keys' bytes, dead from here on.
         for (int w = lane; w < wn; w += 32) X[w] = 0ull;
+        for (int v = lane; v < n; v += 32) pivk[v] = 0xffffu;
+        __syncwarp();
+        for (int k = lane; k < rank; k += 32) pivk[pcol[k]] = static_cast<uint16_t>(k);
         __syncwarp();
 
         // ---- consistency: rows without a pivot must end with s' = 0 ---------------
