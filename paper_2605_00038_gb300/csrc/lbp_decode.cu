@@ -298,7 +298,7 @@ int plan_osd(const lbp_code *c, int64_t num_shots, OsdPlan *out) {
 }
 
 // K_osd_warp plan: CSR prefix of the 16-bit image, then one region per warp.
-constexpr int kOsdMaxWarps = 16;
+constexpr int kOsdMaxWarps = 24;
 
 void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     OsdWarpPlan p;
