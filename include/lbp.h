@@ -115,7 +115,15 @@ void lbp_params_default(lbp_params *p);
  * The library copies what it needs (host buffers may be freed on return),
  * allocates the device-resident graph with cudaMalloc on the current device
  * and returns an opaque handle in *out.  Errors: LBP_EINVAL, LBP_ENOMEM,
- * LBP_ECUDA; *out is set to NULL on error. */
+ * LBP_ECUDA; *out is set to NULL on error.
+ *
+ * When the bounded-degree index image and one shot's FP32 state always fit
+ * in shared memory, the image gets a bank-aware layout: message rows padded
+ * to a multiple of 32 words and a table that regroups the check phase's
+ * pairs of checks into warps (chosen by a deterministic local search over
+ * the shared-memory bank conflicts of the posterior gathers).  Results are
+ * the same with or without it; LBP_BANK_LAYOUT=0 (read at load) turns it
+ * off. */
 int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *priors, lbp_code **out);
 

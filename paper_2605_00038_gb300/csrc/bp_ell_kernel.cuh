@@ -9,6 +9,9 @@
 //    with column n, whose prior and posterior are +inf: a neutral element of
 //    the check update (positive sign, never the minimum).  beta[k][c], row
 //    stride R = Mp + 2 (Mp = m rounded up to even), is the message on slot k.
+//    When the index image always sits in shared memory, R is Mp + 2 rounded
+//    up to a multiple of 32 words and a pair table orders the check phase
+//    (bank-aware layout, built by lbp_load_code).
 //  * Column side: vent[k][v] is the message offset k' * R + c of v's k-th
 //    check (ascending), padded with offset Mp, the message beta[0][Mp] = +0
 //    (x + 0 == x for every partial sum, which is never -0), so the LLR update
@@ -74,6 +77,10 @@ struct BpEllArgs {
     SurfaceDesc surf;         // implicit graph (SurfaceGraph)
     RoundDesc rnd;            // round-periodic graph (RoundGraph)
     const float *mu_tab;      // its mu[Np + 2] when not uniform per block
+    // Index-image form with the bank-aware layout (0, 0 otherwise): message
+    // row stride in words and the image offset of the check-pair table.
+    int32_t tab_R;
+    uint32_t off_ptab;
 };
 
 // Exclusive minima and signed outputs of one check (DC slots).
@@ -143,7 +150,12 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     const int m = a.m, n = a.n, I = a.max_iter;
-    const int Mp = a.img.Mp, Np = a.img.Np, R = Mp + 2;
+    // The bank-aware layout exists only for the index image staged in shared
+    // memory; every other instantiation keeps R = Mp + 2 and no pair table.
+    constexpr bool kTab = kGraphSmem && GraphT::kEll;
+    const int Mp = a.img.Mp, Np = a.img.Np, R = (kTab && a.tab_R > 0) ? a.tab_R : Mp + 2;
+    const uint16_t *ptab =
+        (kTab && a.off_ptab != 0u) ? reinterpret_cast<const uint16_t *>(smem + a.off_ptab) : nullptr;
     const int mpairs = Mp >> 1, npairs = Np >> 1;
     const GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.rnd, a.mu_tab, m, n);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
@@ -208,7 +220,8 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             int cpre = -1;
             uint32_t u2pre = 0;
             // ---- C2V, two adjacent checks per thread ---------------------------
-            for (int pr = t; pr < mpairs; pr += G) {
+            for (int ip = t; ip < mpairs; ip += G) {
+                const int pr = (kTab && ptab) ? static_cast<int>(ptab[ip]) : ip;
                 const int c = 2 * pr;
                 float al0[DC], al1[DC];
                 uint32_t v0[DC], v1[DC];

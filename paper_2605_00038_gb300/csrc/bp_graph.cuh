@@ -47,6 +47,7 @@ template <typename IdxT, int DC, int DV>
 struct EllGraph {
     using IP = typename Idx<IdxT>::P;
     static constexpr bool kImage = true;
+    static constexpr bool kEll = true;     // the index image (may carry the bank-aware layout)
     const IdxT *cidx;
     const IP *cidx2;
     const IdxT *vent;
@@ -100,6 +101,7 @@ template <int DC, int DV>
 struct SurfaceGraph {
     static_assert(DC == 6 && DV == 2, "surface-code space-time matrices have DC = 6, DV = 2");
     static constexpr bool kImage = false;
+    static constexpr bool kEll = false;
     SurfaceDesc s;
     const float *mu_tab;     // mu[Np + 2] (global) when mu is not uniform per block
     uint32_t m, n, Mp, R, M0;
@@ -221,6 +223,7 @@ template <int DC, int DV>
 struct RoundGraph {
     static_assert(DV >= 2, "a measurement column has two checks");
     static constexpr bool kImage = true;     // the round image is staged like an index image
+    static constexpr bool kEll = false;
     RoundDesc r;
     const uint16_t *rcidx;
     const uint32_t *rvent;

@@ -82,6 +82,19 @@ struct lbp_code;
 
 namespace lbp {
 
+// Per-shot state of the ELL kernel: messages [DC][R], posteriors [Np + 2],
+// syndrome words, three s_hat buffers, and 16 bytes of group scratch, each
+// part 16-byte aligned.
+inline uint32_t ell_state_bytes(int msg_bytes, int DC, int R, int Np, int m) {
+    auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+    const uint32_t W32 = static_cast<uint32_t>((m + 31) / 32);
+    uint32_t off = a16(static_cast<uint32_t>(msg_bytes) * DC * R);
+    off = a16(off + 4u * (Np + 2));
+    off = a16(off + 4u * W32);
+    off = a16(off + 12u * W32);
+    return a16(off + 16u);
+}
+
 // The decode path behind lbp_decode: plan, workspace layout and launches of
 // K_bp and the OSD kernels on `stream`, using `ws_bytes` bytes at `ws`
 // (device, 256-byte aligned) as scratch.  Parameters are already validated.
@@ -117,6 +130,12 @@ struct lbp_code {
     // ELL image (device), NULL when the code's degrees or sizes exceed it.
     uint8_t *d_ell;
     lbp::EllImage ell;
+    // Bank-aware layout of the index-image form, for codes whose image and
+    // FP32 state always fit in shared memory (0 otherwise): message rows of
+    // tab_R words (a multiple of 32) and, at image offset tab_off_ptab, the
+    // table of check pairs in the order the kernel's lanes take them.
+    int32_t tab_R;
+    uint32_t tab_off_ptab;
     // 32-bit device copies, used by OSD.
     int32_t *d_row_ptr, *d_col_idx;
     float *d_mu;

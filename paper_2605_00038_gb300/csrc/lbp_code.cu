@@ -18,6 +18,69 @@ namespace {
 
 uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
+// Order in which the index-image kernel's lanes take the check pairs.  In
+// the check phase, lane l of a warp's j-th step takes pair 32 j + l; each of
+// its DC slots then gathers the posteriors of its two checks' columns, and a
+// warp's 32 gathers cost as many shared-memory wavefronts as the most
+// distinct columns that fall in one of the 32 banks (column mod 32).  The
+// table keeps pair p at lane p mod 32, so the pair-indexed accesses (indices,
+// messages, syndrome words) stay conflict-free, and chooses which pairs of a
+// residue share a step so that the columns spread over the banks: simulated
+// annealing over swaps within a residue, with a fixed seed (deterministic),
+// minimising the summed wavefronts of the full steps.  Every pair is still
+// processed exactly once, so results do not depend on the table.
+std::vector<uint16_t> pair_table(const std::vector<uint8_t> &img, uint32_t off_cidx, int DC, int32_t Mp) {
+    const int mp = Mp / 2, steps = mp / 32;
+    std::vector<uint16_t> tab(static_cast<size_t>(mp));
+    for (int p = 0; p < mp; ++p) tab[p] = static_cast<uint16_t>(p);
+    if (steps < 2) return tab;
+    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(img.data() + off_cidx);
+    auto step_cost = [&](int j) {
+        int total = 0;
+        for (int k = 0; k < DC; ++k) {
+            for (int h = 0; h < 2; ++h) {
+                uint16_t ids[32];
+                int cnt[32] = {0};
+                int worst = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const uint16_t id = cidx[static_cast<size_t>(k) * Mp + 2 * tab[32 * j + l] + h];
+                    bool dup = false;
+                    for (int q = 0; q < l && !dup; ++q) dup = ids[q] == id;
+                    ids[l] = id;
+                    if (!dup && ++cnt[id & 31] > worst) worst = cnt[id & 31];
+                }
+                total += worst;
+            }
+        }
+        return total;
+    };
+    std::vector<int> cost(static_cast<size_t>(steps));
+    for (int j = 0; j < steps; ++j) cost[j] = step_cost(j);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        return st;
+    };
+    const long iters = std::min<long>(60000, 200L * mp);
+    for (long it = 0; it < iters; ++it) {
+        const double temp = 0.5 * (1.0 - static_cast<double>(it) / iters) + 0.01;
+        const int l = static_cast<int>(next() % 32);
+        const int j1 = static_cast<int>(next() % steps), j2 = static_cast<int>(next() % steps);
+        if (j1 == j2) continue;
+        std::swap(tab[32 * j1 + l], tab[32 * j2 + l]);
+        const int c1 = step_cost(j1), c2 = step_cost(j2);
+        const int d = c1 + c2 - cost[j1] - cost[j2];
+        const double u = static_cast<double>(next() >> 11) * (1.0 / 9007199254740992.0);
+        if (d <= 0 || std::exp(-d / temp) > u) {
+            cost[j1] = c1;
+            cost[j2] = c2;
+        } else {
+            std::swap(tab[32 * j1 + l], tab[32 * j2 + l]);
+        }
+    }
+    return tab;
+}
+
 void release(lbp_code *c) {
     if (!c) return;
     int prev = -1;
@@ -325,7 +388,8 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
     int ell_dc = 8, ell_dv = 4;
     if (maxdeg <= 6 && maxcol <= 2) { ell_dc = 6; ell_dv = 2; }
     else if (maxdeg <= 6 && maxcol <= 3) { ell_dc = 6; ell_dv = 3; }
-    const int32_t Mp = (m + 1) & ~1, Np = (n + 1) & ~1, R = Mp + 2;
+    const int32_t Mp = (m + 1) & ~1, Np = (n + 1) & ~1;
+    int32_t R = Mp + 2;
     // 16-bit indices when every message offset and column fits; otherwise
     // 32-bit (the kernel recovers an offset's check by a multiply-high
     // division, exact while DC * R^2 < 2^32).
@@ -344,6 +408,23 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         e.off_cidx = off; off = align16(off + ib * e.DC * Mp);
         e.off_vent = off; off = align16(off + ib * e.DV * Np);
         e.off_mu = off;   off = align16(off + 4u * (Np + 2));
+        // Bank-aware layout when the image (with its pair table) and one
+        // shot's FP32 state always fit in shared memory, so the index-image
+        // form never reads the image from global memory: message rows padded
+        // to a multiple of 32 words spread the column phase's message
+        // gathers over the banks (both slots of a column then share the bank
+        // pattern of its checks), and the pair table regroups the check phase.
+        const int32_t Rr = (R + 31) & ~31;
+        const uint32_t tab_bytes = align16(off + 2u * static_cast<uint32_t>(Mp / 2));
+        const char *bl = std::getenv("LBP_BANK_LAYOUT");
+        if (!(bl && !std::strcmp(bl, "0")) && fits16 && static_cast<int64_t>(ell_dc) * Rr < 65536 &&
+            static_cast<size_t>(tab_bytes) + lbp::ell_state_bytes(4, ell_dc, Rr, Np, m) <=
+                static_cast<size_t>(c->smem_optin)) {
+            R = Rr;
+            c->tab_R = Rr;
+            c->tab_off_ptab = off;
+            off = tab_bytes;
+        }
         e.bytes = off;
         std::vector<uint8_t> img(off, 0);
         auto put = [&](uint32_t base, size_t i, uint32_t v) {
@@ -369,6 +450,10 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
             }
         }
         for (int32_t v = 0; v < Np + 2; ++v) mu_e[v] = v < n ? mu[v] : INFINITY;
+        if (c->tab_R) {
+            const std::vector<uint16_t> tab = pair_table(img, e.off_cidx, e.DC, Mp);
+            std::memcpy(img.data() + c->tab_off_ptab, tab.data(), 2u * tab.size());
+        }
         rc = upload(reinterpret_cast<void **>(&c->d_ell), img.data(), off);
         // Implicit graph: the same shape (DC = 6, DV = 2, Mp, Np, R = Mp + 2)
         // with indices from Table III's formulas; priors that are not uniform

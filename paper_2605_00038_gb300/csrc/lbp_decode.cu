@@ -47,6 +47,7 @@ int tuned_slot(int msg, int rule) {
 
 struct BpPlan {
     bool ell = false, graph_smem = true, state_smem = true, idx32 = false, surface = false, round = false;
+    bool tab = false;            // index-image form with the bank-aware stride and pair table
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -118,17 +119,27 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     const int mi = tuned_slot(msg, rule);
     BpPlan p;
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
-    uint32_t off = 0;
-    p.off_beta = off; off = align16u(off + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * (c->ell.Mp + 2));
-    p.off_lam = off;  off = align16u(off + 4u * (c->ell.Np + 2));
-    p.off_s = off;    off = align16u(off + 4u * W32);
-    p.off_shat = off; off = align16u(off + 12u * W32);
-    p.off_misc = off; off = align16u(off + 16u);
-    p.state_bytes = off;
+    // Message rows: R = Mp + 2 words, or the bank-aware stride of the
+    // index-image form (always in shared memory) when the code has one.
+    auto state_layout = [&](int R) {
+        uint32_t o = 0;
+        p.off_beta = o; o = align16u(o + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * R);
+        p.off_lam = o;  o = align16u(o + 4u * (c->ell.Np + 2));
+        p.off_s = o;    o = align16u(o + 4u * W32);
+        p.off_shat = o; o = align16u(o + 12u * W32);
+        p.off_misc = o; o = align16u(o + 16u);
+        p.state_bytes = o;
+        return o;
+    };
+    uint32_t off = state_layout(c->ell.Mp + 2);
     size_t image = c->ell.bytes;
     const size_t budget0 = static_cast<size_t>(c->smem_optin);
     const int form = graph_form(c, mi, req_graph, off);
     if (form < 0) return LBP_ENOSYS;
+    if (form == 1 && c->tab_R > 0) {
+        off = state_layout(c->tab_R);
+        p.tab = true;
+    }
     if (form == 2 || form == 3) {
         // Implicit or round-periodic graph: the state and at most a small
         // round image in shared memory.
@@ -536,7 +547,10 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
         e.gstate = bp.state_smem ? nullptr : base + w.gstate;
-        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
+        const int R = bp.tab ? c->tab_R : c->ell.Mp + 2;
+        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(R) + 1);
+        e.tab_R = bp.tab ? c->tab_R : 0;
+        e.off_ptab = bp.tab ? c->tab_off_ptab : 0u;
         e.surf = c->surf;
         e.rnd = c->rnd;
         e.mu_tab = c->d_mu_pad;

@@ -154,6 +154,27 @@ def test_lottery_baseline_policies(policy):
         assert_parity(gpu_decode(h, pri, syn, **kw), oracle_decode(h, pri, syn, **kw))
 
 
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
+@pytest.mark.parametrize("rule", [lbp.LBP_RULE_MIN_SUM, lbp.LBP_RULE_SUM_PRODUCT])
+def test_bank_layout_changes_nothing(msg, rule, monkeypatch):
+    """The bank-aware image layout (padded message rows, regrouped check
+    pairs) against the plain one on the same syndromes: identical decisions,
+    flags, iteration counts, OSD outputs and LLR bits; and against the oracle
+    for min-sum."""
+    w = workloads.c2_d11_spacetime(shots=2500)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed + 3, num_shots=w.shots)
+    kw = dict(w.decoder, msg=msg, rule=rule, seed=5)
+    monkeypatch.setenv("LBP_GRAPH", "table")
+    a = gpu_decode(w.h, w.priors, syn, **kw)
+    monkeypatch.setenv("LBP_BANK_LAYOUT", "0")
+    b = gpu_decode(w.h, w.priors, syn, **kw)
+    for k in ("err", "conv", "iters", "osd"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["llr"].view(np.uint32), b["llr"].view(np.uint32))
+    if rule == lbp.LBP_RULE_MIN_SUM:
+        assert_parity(a, oracle_decode(w.h, w.priors, syn, **kw))
+
+
 @pytest.mark.parametrize("policy", range(5))
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
 def test_small_batch_wide_groups(policy, msg, monkeypatch):
