@@ -266,9 +266,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     # Launch-shape autotuning on the first batch (outside the timed region).
+    launch = None
     if not args.no_tune:
         tb = min(B, 131072)
         dec.tune(syn_d[0][:tb].contiguous(), prms[0], stream)
+        S_t, G_t, gf_t = lbp.lbp_code_tuned(dec.code, prms[0].msg, prms[0].rule)
+        launch = {"groups_per_cta": S_t, "threads_per_shot": G_t,
+                  "graph": {0: "default", 1: "index image", 2: "implicit", 3: "round"}.get(gf_t, str(gf_t))}
     for k in range(args.warmup):
         step(k)
     barrier()
@@ -333,7 +337,7 @@ def run_gpu(args):
                                  "frac": smem_bytes / bp_avg_s / smem_peak,
                                  "note": "binding unit per ncu: shared-memory pipe 87% busy, "
                                          "37% of load wavefronts bank conflicts"}}
-    line["kernels"] = {"bp_ms_per_step": bp_ms / args.steps, "osd_ms_per_step": osd_ms / args.steps,
+    line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps, "osd_ms_per_step": osd_ms / args.steps,
                        "mean_iters": iters_total / (B * args.steps),
                        "osd_invoke_rate": osd_total / (B * args.steps)}
 

@@ -197,8 +197,9 @@ int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots
 
 /* Autotuner for the BP kernel's launch shape (groups of threads per CTA and
  * threads per group, the "shot tile" and the threads working on one shot):
- * decodes the given batch once per candidate shape, twice each, timing the
- * BP kernel with CUDA events, and stores the fastest shape in `code` for its
+ * decodes the given batch once per candidate shape and graph form, three
+ * times each (a warm-up, then two timed runs of which the faster counts),
+ * timing the BP kernel with CUDA events, and stores the fastest in `code` for its
  * message type and check-node rule (params->msg, params->rule); later decodes
  * with that pair use it.
  * Every shape computes identical results, so on return the outputs hold
@@ -210,6 +211,13 @@ int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_shots,
              const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
              uint8_t *osd_out, int32_t *iters_out, void *workspace, size_t workspace_bytes,
              void *stream);
+
+/* The launch shape lbp_tune stored for (msg, rule): groups per CTA, threads
+ * per group and graph form (1 index image, 2 implicit surface-code graph,
+ * 3 round-periodic graph); all 0 when that pair has not been tuned.  Any
+ * output pointer may be NULL.  Errors: LBP_EINVAL (code NULL, msg not an
+ * LBP_MSG_* value, rule not an LBP_RULE_* value). */
+int lbp_code_tuned(const lbp_code *code, int32_t msg, int32_t rule, int32_t *groups, int32_t *G, int32_t *graph);
 
 /* Bytes of device workspace lbp_decode_host needs: lbp_workspace_size plus
  * device staging for the inputs and outputs.  When llr_out is requested the

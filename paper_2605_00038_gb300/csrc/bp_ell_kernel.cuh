@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             const bool early = lottery_random_check(a.policy);
             int cpre = -1;
             uint32_t u2pre = 0;
+            LotteryPrep lp;          // index-image instantiations in shared memory only
             // ---- C2V, two adjacent checks per thread ---------------------------
             for (int ip = t; ip < mpairs; ip += G) {
                 const int pr = (kTab && ptab) ? static_cast<int>(ptab[ip]) : ip;
@@ -252,9 +253,20 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 #pragma unroll
                 for (int k = 0; k < DC; ++k) beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
             }
-            if (lot && early && lw)
-                cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, a.seed, a.shot_offset + b, it,
-                                         a.policy, lam, u2pre);
+            if (lot && early && lw) {
+                if constexpr (kTab) {
+                    // c* and its columns now; after the termination test only
+                    // the |lambda| comparison remains.
+                    uint32_t u2 = 0;
+                    const uint32_t *sp = shat + prev * W32;
+                    const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it,
+                                                          a.policy, lam, u2);
+                    lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, a.policy, m, R, a.magic);
+                } else {
+                    cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, a.seed, a.shot_offset + b, it,
+                                             a.policy, lam, u2pre);
+                }
+            }
             group_sync<G>(bar);
             // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
@@ -296,12 +308,23 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             if (lot) {
                 if (lw) {
                     const uint32_t *sp = shat + prev * W32;
-                    if (!early)
-                        cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it, a.policy,
-                                                 lam, u2pre);
-                    const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, a.policy, lam, m, R,
-                                                          a.magic);
-                    if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
+                    if constexpr (kTab) {
+                        if (!early) {
+                            uint32_t u2 = 0;
+                            const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b,
+                                                                  it, a.policy, lam, u2);
+                            lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, a.policy, m, R, a.magic);
+                        }
+                        const int vs = lottery_finish(lp, lam);
+                        if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
+                    } else {
+                        if (!early)
+                            cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it, a.policy,
+                                                     lam, u2pre);
+                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, a.policy, lam, m, R,
+                                                              a.magic);
+                        if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
+                    }
                 }
                 group_sync<G>(bar);
             }

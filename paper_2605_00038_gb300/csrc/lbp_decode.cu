@@ -761,6 +761,16 @@ extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, i
     return LBP_OK;
 }
 
+extern "C" int lbp_code_tuned(const lbp_code *code, int32_t msg, int32_t rule, int32_t *groups, int32_t *G,
+                              int32_t *graph) {
+    if (!code || msg < 0 || msg > 2 || (rule != LBP_RULE_MIN_SUM && rule != LBP_RULE_SUM_PRODUCT)) return LBP_EINVAL;
+    const int mi = tuned_slot(msg, rule);
+    if (groups) *groups = code->tuned_groups[mi];
+    if (G) *G = code->tuned_G[mi];
+    if (graph) *graph = code->tuned_graph[mi];
+    return LBP_OK;
+}
+
 extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_shots,
                         const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                         uint8_t *osd_out, int32_t *iters_out, void *workspace, size_t workspace_bytes,
@@ -798,6 +808,13 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
             rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
                                            iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms, graph);
             if (rc) return rc;
+            // Two timed runs, the faster kept: close candidates (a few %
+            // apart) are otherwise picked by timing noise.
+            float ms2 = 0.0f;
+            rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
+                                           iters_out, nullptr, workspace, workspace_bytes, s, S, G, &ms2, graph);
+            if (rc) return rc;
+            if (ms2 > 0.0f && (ms <= 0.0f || ms2 < ms)) ms = ms2;
             if (ms > 0.0f && (best < 0.0f || ms < best)) { best = ms; best_S = S; best_G = G; best_graph = graph; }
         }
     }

@@ -25,7 +25,8 @@ LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
 (LBP_LOTTERY_PROPOSED, LBP_LOTTERY_WORST_UNRELIABLE, LBP_LOTTERY_WORST_RANDOM,
  LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM) = range(5)
 
-EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface", "lbp_code_rounds",
+EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface",
+            "lbp_code_rounds", "lbp_code_tuned",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
             "lbp_server_wait", "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
@@ -70,6 +71,8 @@ def lib():
         L.lbp_code_info.argtypes = [vp, vp, vp, vp]
         L.lbp_code_surface.restype = ctypes.c_int
         L.lbp_code_surface.argtypes = [vp, vp, vp, vp, vp]
+        L.lbp_code_tuned.restype = ctypes.c_int
+        L.lbp_code_tuned.argtypes = [vp, i32, i32, vp, vp, vp]
         L.lbp_code_rounds.restype = ctypes.c_int
         L.lbp_code_rounds.argtypes = [vp, vp, vp, vp, vp]
         L.lbp_workspace_size.restype = sz
@@ -185,6 +188,14 @@ def lbp_code_rounds(code: Code):
     _check(lib().lbp_code_rounds(code.ptr, ctypes.byref(T), ctypes.byref(mr), ctypes.byref(nr),
                                  ctypes.byref(cy)), "lbp_code_rounds")
     return T.value, mr.value, nr.value, cy.value
+
+
+def lbp_code_tuned(code: Code, msg: int, rule: int = 0):
+    """(groups per CTA, threads per group, graph form) stored by lbp_tune, zeros if untuned."""
+    S, G, gf = (ctypes.c_int32() for _ in range(3))
+    _check(lib().lbp_code_tuned(code.ptr, msg, rule, ctypes.byref(S), ctypes.byref(G), ctypes.byref(gf)),
+           "lbp_code_tuned")
+    return S.value, G.value, gf.value
 
 
 def lbp_workspace_size(code: Code, params: lbp_params, num_shots: int) -> int:

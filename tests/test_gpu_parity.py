@@ -304,8 +304,14 @@ def test_autotuner_keeps_results(msg):
     prm = dec.params(**kw)
     s = torch.from_numpy(syn.view(np.int64)).cuda()
     out = dec.alloc(w.shots)
+    assert lbp.lbp_code_tuned(dec.code, msg) == (0, 0, 0)
     lbp.lbp_tune(dec.code, prm, w.shots, s, out.err, out.converged, out.osd, out.iters,
                  dec.workspace(prm, w.shots))
+    S, G, form = lbp.lbp_code_tuned(dec.code, msg)
+    assert S >= 1 and G in (32, 64, 96, 128, 192, 256, 512, 1024) and form in (1, 2, 3)
+    assert lbp.lbp_code_tuned(dec.code, msg, lbp.LBP_RULE_SUM_PRODUCT) == (0, 0, 0)
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_code_tuned(dec.code, 3)
     assert np.array_equal(out.err.cpu().numpy().view(np.uint64), ref["err_words"])
     assert np.array_equal(out.iters.cpu().numpy(), ref["iters"])
     again = dec.decode(s, prm)
