@@ -147,7 +147,7 @@ def roofline_model(w, iters_total, shots):
 # DRAM bytes per shot of K_bp on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture, 131,072 shots, scaled per shot),
 # valid for the kernel sources whose hash is recorded with it.
-KBP_TRAFFIC = {"bytes_per_shot": 1140.5, "source_sha1": "4c7caee9038a"}
+KBP_TRAFFIC = {"bytes_per_shot": 1135.5, "source_sha1": "c5201d0edac9"}
 
 
 def kbp_source_sha1():
@@ -335,9 +335,10 @@ def run_gpu(args):
                         "smem": {"achieved_tbs": smem_bytes / bp_avg_s / 1e12,
                                  "peak_tbs": smem_peak / 1e12,
                                  "frac": smem_bytes / bp_avg_s / smem_peak,
-                                 "note": "binding unit per ncu: shared-memory pipe 87% busy, "
-                                         "37% of load wavefronts bank conflicts"}}
-    line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps, "osd_ms_per_step": osd_ms / args.steps,
+                                 "note": "per ncu: shared-memory pipe 85% busy and instruction issue "
+                                         "77%; 30% of load wavefronts bank conflicts"}}
+    line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps,
+                       "osd_ms_per_step": osd_ms / args.steps,
                        "mean_iters": iters_total / (B * args.steps),
                        "osd_invoke_rate": osd_total / (B * args.steps)}
 
