@@ -147,7 +147,7 @@ def roofline_model(w, iters_total, shots):
 # DRAM bytes per shot of K_bp on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture, 131,072 shots, scaled per shot),
 # valid for the kernel sources whose hash is recorded with it.
-KBP_TRAFFIC = {"bytes_per_shot": 1135.5, "source_sha1": "c5201d0edac9"}
+KBP_TRAFFIC = {"bytes_per_shot": 1135.5, "source_sha1": "e49ad615ca0e"}
 
 
 def kbp_source_sha1():

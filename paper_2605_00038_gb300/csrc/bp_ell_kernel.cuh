@@ -35,9 +35,12 @@
 // memory (the image is L2-resident; the state goes to a per-group slice of the
 // workspace), which is how the d=25 space-time code runs.
 // Lottery: the group's last warp, which has the fewest rounds in both phases,
-// runs lottery_pick's two halves; for the random-check policies it draws c*
-// right after its check-phase rounds (c* depends only on s_hat(i-1), s and the
-// draw), so after the termination test only the column step v* remains.
+// runs it.  For the random-check policies it draws c* right after its
+// check-phase rounds (c* depends only on s_hat(i-1), s and the draw).  The
+// index-image instantiations in shared memory (kTab) draw with a single scan
+// when the code has at most 1024 checks and also prepare c*'s columns then,
+// so after the termination test only lottery_finish's |lambda| comparison
+// remains; the other instantiations run lottery_column after the test.
 // Everything else (groups of G threads per shot, named barriers, s_hat
 // scatter, early termination, outputs, OSD hand-off) is as in bp_kernel.
 #pragma once

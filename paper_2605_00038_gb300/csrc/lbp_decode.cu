@@ -1,12 +1,14 @@
 // lbp_decode / lbp_decode_host: launch planning for K_bp and K_osd.
 //
 // K_bp runs persistent: one CTA per SM, S groups of G threads per CTA, the
-// graph image plus S shots' state in shared memory.  S and G are chosen here
-// from the shared-memory budget (the largest S that fits, then the widest G
-// that keeps S * G <= 1024 threads).  K_osd follows on the same stream and
-// drains the queue K_bp filled; no host round trip separates them.
+// graph image plus S shots' state in shared memory.  S and G come from the
+// shared-memory budget, lbp_tune's stored shape or LBP_BP_SHAPE; a call of
+// at most one shot per SM that runs alone on the device gets one shot per CTA
+// with up to 1024 threads.  K_osd follows on the same stream and drains the
+// queue K_bp filled; no host round trip separates them.
 //
-// With OSD on, K_osd_warp (one warp per shot, sparse-aware) drains the queue
+// With OSD on, K_osd_warp (one warp per shot, sparse-aware; alone on the
+// device with at most one shot per SM, its latency layout) drains the queue
 // first; K_osd (one CTA per shot, dense) then takes the shots it handed over.
 //
 // Workspace (caller-owned device memory), 256-byte aligned sections:
