@@ -226,8 +226,12 @@ size_t lbp_host_workspace_size(const lbp_code *code, const lbp_params *params, i
 
 /* Same as lbp_decode with HOST buffers (same shapes; llr_out and osd_out may
  * be NULL): enqueues the host-to-device copy of the syndromes, the decode and
- * the device-to-host copies of the results on `stream`, using `workspace`
- * (device, lbp_host_workspace_size bytes) for staging.  Pinned host memory
+ * the device-to-host copies of the results, ordered on `stream`, using
+ * `workspace` (device, lbp_host_workspace_size bytes) for staging.  Calls of
+ * at least 262,144 shots run as 2 or 4 consecutive chunks whose copies travel
+ * on two internal streams while the neighbouring chunks decode on `stream`
+ * (events keep the copies after `stream`'s earlier work and `stream`'s later
+ * work after the copies); results are those of one call.  Pinned host memory
  * makes the copies asynchronous; the caller synchronises the stream before
  * reading the outputs. */
 int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_shots,

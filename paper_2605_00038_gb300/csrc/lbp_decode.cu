@@ -19,9 +19,11 @@
 //   osd_mat    u64[grid][m][ceil(n/64)] K_osd dense matrices (when they do
 //                                                     not fit shared memory)
 //   slots      u64[warps][C][ceil(n/64)] K_osd_warp dense-row pools
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_fp16.h>
 
@@ -696,6 +698,36 @@ extern "C" int lbp_decode(const lbp_code *code, const lbp_params *params, int64_
 
 namespace {
 
+// lbp_decode_host pipelines calls of at least 2 * kHostChunkShots shots.
+constexpr int64_t kHostChunkShots = 131072;
+
+// The two copy streams of lbp_decode_host's pipeline, per device, created on
+// first use and kept for the life of the process.
+struct CopyStreams {
+    cudaStream_t in = nullptr, out = nullptr;
+};
+
+bool copy_streams(int dev, CopyStreams *out) {
+    static std::mutex mu;
+    static CopyStreams per_dev[64];
+    if (dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    CopyStreams &c = per_dev[dev];
+    if (!c.in) {
+        cudaStream_t a = nullptr, b = nullptr;
+        if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            if (a) cudaStreamDestroy(a);
+            return false;
+        }
+        c.in = a;
+        c.out = b;
+    }
+    *out = c;
+    return true;
+}
+
 struct HostStage {
     size_t syn, err, conv, osd, iters, decode_ws, total, llr, total_llr;
 };
@@ -747,18 +779,82 @@ extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, i
     uint8_t *d_osd = base + h.osd;
     int32_t *d_iters = reinterpret_cast<int32_t *>(base + h.iters);
     float *d_llr = llr_out ? reinterpret_cast<float *>(base + h.llr) : nullptr;
-    if (cudaMemcpyAsync(d_syn, syndromes, 8ull * wm * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return LBP_ECUDA;
+    // Outputs of shots [s0, s0 + nb) to the host, on stream q.
+    auto d2h = [&](int64_t s0, int64_t nb, cudaStream_t q) {
+        bool ok = cudaMemcpyAsync(err_out + s0 * wn, d_err + s0 * wn, 8ull * wn * nb, cudaMemcpyDeviceToHost,
+                                  q) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(converged + s0, d_conv + s0, static_cast<size_t>(nb), cudaMemcpyDeviceToHost,
+                                   q) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(iters_out + s0, d_iters + s0, 4ull * nb, cudaMemcpyDeviceToHost, q) == cudaSuccess;
+        if (osd_out)
+            ok = ok && cudaMemcpyAsync(osd_out + s0, d_osd + s0, static_cast<size_t>(nb), cudaMemcpyDeviceToHost,
+                                       q) == cudaSuccess;
+        if (llr_out)
+            ok = ok && cudaMemcpyAsync(llr_out + s0 * code->n, d_llr + s0 * code->n, 4ull * code->n * nb,
+                                       cudaMemcpyDeviceToHost, q) == cudaSuccess;
+        return ok;
+    };
+    const int K = B >= 4 * kHostChunkShots ? 4 : (B >= 2 * kHostChunkShots ? 2 : 1);
+    CopyStreams cs;
+    if (K == 1 || !copy_streams(dev, &cs)) {
+        if (cudaMemcpyAsync(d_syn, syndromes, 8ull * wm * B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return LBP_ECUDA;
+        }
+        rc = decode_device(code, params, B, d_syn, d_err, d_conv, d_osd, d_iters, d_llr,
+                           base + h.decode_ws, h.total - h.decode_ws, s);
+        if (rc) return rc;
+        if (!d2h(0, B, s)) { cudaGetLastError(); return LBP_ECUDA; }
+        return LBP_OK;
     }
-    rc = decode_device(code, params, B, d_syn, d_err, d_conv, d_osd, d_iters, d_llr,
-                       base + h.decode_ws, h.total - h.decode_ws, s);
+    // Pipeline over K consecutive chunks: every host-to-device copy is queued
+    // on the input copy stream at once, chunk i decodes on the caller's stream
+    // after its input arrived (shot_offset advanced, so each shot draws as in
+    // one call), and its outputs leave on the output copy stream while the
+    // next chunk decodes.  Events order the copy streams after the caller's
+    // earlier work, and the caller's stream after the last copy.
+    cudaEvent_t ev[2 * 4 + 2] = {};
+    auto release = [&]() {
+        for (cudaEvent_t &e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (cudaEvent_t &e : ev) {
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            release();
+            return LBP_ECUDA;
+        }
+    }
+    cudaEvent_t ev_start = ev[0], ev_end = ev[1], *ev_in = ev + 2, *ev_dec = ev + 2 + K;
+    bool ok = cudaEventRecord(ev_start, s) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(cs.in, ev_start, 0) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(cs.out, ev_start, 0) == cudaSuccess;
+    const int64_t chunk = (B + K - 1) / K;
+    for (int i = 0; ok && i < K; ++i) {
+        const int64_t s0 = i * chunk, nb = std::min<int64_t>(chunk, B - s0);
+        ok = cudaMemcpyAsync(d_syn + s0 * wm, syndromes + s0 * wm, 8ull * wm * nb, cudaMemcpyHostToDevice,
+                             cs.in) == cudaSuccess;
+        ok = ok && cudaEventRecord(ev_in[i], cs.in) == cudaSuccess;
+    }
+    for (int i = 0; ok && i < K; ++i) {
+        const int64_t s0 = i * chunk, nb = std::min<int64_t>(chunk, B - s0);
+        lbp_params p = *params;
+        p.shot_offset += static_cast<uint64_t>(s0);
+        ok = cudaStreamWaitEvent(s, ev_in[i], 0) == cudaSuccess;
+        if (ok) {
+            rc = decode_device(code, &p, nb, d_syn + s0 * wm, d_err + s0 * wn, d_conv + s0, d_osd + s0,
+                               d_iters + s0, d_llr ? d_llr + s0 * code->n : nullptr, base + h.decode_ws,
+                               h.total - h.decode_ws, s);
+            if (rc) break;
+        }
+        ok = ok && cudaEventRecord(ev_dec[i], s) == cudaSuccess;
+        ok = ok && cudaStreamWaitEvent(cs.out, ev_dec[i], 0) == cudaSuccess;
+        ok = ok && d2h(s0, nb, cs.out);
+    }
+    ok = ok && cudaEventRecord(ev_end, cs.out) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(s, ev_end, 0) == cudaSuccess;
+    release();
     if (rc) return rc;
-    bool ok = cudaMemcpyAsync(err_out, d_err, 8ull * wn * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(converged, d_conv, static_cast<size_t>(B), cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(iters_out, d_iters, 4ull * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    if (osd_out) ok = ok && cudaMemcpyAsync(osd_out, d_osd, static_cast<size_t>(B), cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    if (llr_out) ok = ok && cudaMemcpyAsync(llr_out, d_llr, 4ull * code->n * B, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     if (!ok) { cudaGetLastError(); return LBP_ECUDA; }
     return LBP_OK;
 }

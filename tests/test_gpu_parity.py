@@ -395,6 +395,49 @@ def test_host_buffer_entry_point_matches_device():
     dec.close()
 
 
+def _host_decode(dec, prm, syn, n, want_llr):
+    B = syn.shape[0]
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+    hs = pin(syn.shape, torch.int64)
+    hs.numpy()[:] = syn.view(np.int64)
+    out = dict(err=pin((B, (n + 63) // 64), torch.int64), converged=pin(B, torch.uint8),
+               osd=pin(B, torch.uint8), iters=pin(B, torch.int32))
+    if want_llr:
+        out["llr"] = pin((B, n), torch.float32)
+    dec.decode_host(hs, prm, out)
+    out["syndromes"] = hs        # the call reads it asynchronously: keep it alive until synchronised
+    return out
+
+
+@pytest.mark.parametrize("case", ["c2_four_chunks", "bb72_two_chunks_llr"])
+def test_host_buffer_pipeline_matches_device(case):
+    """Calls of at least 2 x 131,072 shots pipeline their copies over 2 or 4
+    chunks on internal streams: outputs identical to the device-buffer path,
+    also when two calls follow each other on the same stream."""
+    if case == "c2_four_chunks":
+        w = workloads.c2_d11_spacetime(shots=4 * 131072 + 777)
+        h, pri, kw, llr = w.h, w.priors, dict(w.decoder, seed=12), False
+    else:
+        hx, _ = bb_code("bb72")
+        h, pri, kw, llr = hx, np.full(hx.n, 0.03), dict(max_iter=50, lottery=1, osd=1, msg=1, seed=13), True
+    B = 4 * 131072 + 777 if case == "c2_four_chunks" else 2 * 131072 + 123
+    _, syn = sampler.sample(h, pri, seed=91, num_shots=B)
+    g = gpu_decode(h, pri, syn, want_llr=llr, **kw)
+    dec = Decoder(h, pri)
+    prm = dec.params(**kw)
+    first = _host_decode(dec, prm, syn, h.n, llr)
+    second = _host_decode(dec, prm, syn, h.n, llr)
+    torch.cuda.synchronize()
+    for out in (first, second):
+        assert np.array_equal(out["err"].numpy().view(np.uint64), g["err_words"])
+        assert np.array_equal(out["converged"].numpy(), g["conv"])
+        assert np.array_equal(out["iters"].numpy(), g["iters"])
+        assert np.array_equal(out["osd"].numpy(), g["osd"])
+        if llr:
+            assert np.array_equal(out["llr"].numpy().view(np.uint32), g["llr"].view(np.uint32))
+    dec.close()
+
+
 def test_bench_launch_config_full_size_sampled():
     """c2 at its full batch (10^6 shots) in the bench's launch configuration:
     sampled shots match the oracle one by one; on every shot the converged or
