@@ -365,9 +365,18 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
         const int v = std::atoi(env);
         if (v > 0 && v <= c->m) C = v;
     } else if (warps_for(C) >= 1) {
+        const int floor_c = c->m < 192 ? c->m : 192;
+        // Up to 15% fewer rows when that fits another warp per SM (the
+        // kernel is latency-bound, so warps are throughput).
+        const int w0 = warps_for(C);
+        for (int c2 = C - 1; c2 >= floor_c && c2 * 20 >= C * 17; --c2) {
+            if (warps_for(c2) > w0) {
+                C = c2;
+                break;
+            }
+        }
         const size_t per_row = static_cast<size_t>(c->sm_count) * warps_for(C) * p.wn * 8u;
         const size_t cap = (static_cast<size_t>(1) << 30) / per_row;
-        const int floor_c = c->m < 192 ? c->m : 192;
         if (static_cast<size_t>(C) > cap) C = cap > static_cast<size_t>(floor_c) ? static_cast<int>(cap) : floor_c;
     }
     p.C = C;
