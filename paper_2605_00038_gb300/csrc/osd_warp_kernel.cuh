@@ -28,6 +28,13 @@
 //    the CSR image of H.  Measured: about 40 changed rows per shot on the d=11
 //    space-time code.  A shot that needs more than C rows goes to the
 //    block-wide kernel K_osd, which computes the same e.
+//  * Shared memory per warp is reused by lifetime, since resident warps set
+//    the throughput of this latency-bound kernel: during the sort only the
+//    keys, the radix buffer and the digit histogram are live, so the
+//    elimination's arrays (pivot columns and rows, row flags, pivot and
+//    syndrome bits, waiting rows) share the buffer's bytes; after the
+//    elimination the keys are dead, so the solution bits and the column ->
+//    pivot index map (rebuilt from the pivot columns) take their place.
 //  * Latency layout (kLat, for batches of at most one shot per SM): one warp
 //    per CTA, whose shared memory also holds the order bits of the shot's
 //    lambda (read once, coalesced) and the first Cs rows of the dense-row
