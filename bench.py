@@ -396,6 +396,31 @@ def run_gpu(args):
             lat["batch_%d" % bs] = {"p50_ms": times[len(times) // 2],
                                     "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
                                     "samples": len(times)}
+        # Batch 1 replayed from a CUDA graph (lbp_graph_*): the same decode
+        # without the per-call cost of issuing its stream operations.  Each
+        # repeat first writes a different shot into the captured buffer.
+        x1 = torch.empty((1, wm), dtype=torch.int64, device=syn_d[0].device)
+        o1 = dec.alloc(1)
+        ws1 = torch.empty(lbp.lbp_workspace_size(dec.code, prms[0], 1) + 256, dtype=torch.uint8,
+                          device=syn_d[0].device)
+        ws1 = ws1[(-ws1.data_ptr()) % 256:]
+        g1 = lbp.lbp_graph_create(dec.code, prms[0], 1, x1, o1.err, o1.converged, o1.osd, o1.iters, None,
+                                  ws1)
+        times = []
+        for r in range(210):
+            x1.copy_(syn_d[0][r:r + 1])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lbp.lbp_graph_launch(g1, stream)
+            b.record(stream)
+            b.synchronize()
+            if r >= 10:
+                times.append(a.elapsed_time(b))
+        g1.close()
+        times.sort()
+        lat["batch_1_graph"] = {"p50_ms": times[len(times) // 2],
+                                "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                                "samples": len(times)}
         lat["batch_%d" % B] = {"p50_ms": line["ms_per_step"], "p99_ms": None}
         line["latency"] = lat
         # Logical error rate of batch 0 (true errors known from the sampler).

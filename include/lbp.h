@@ -319,6 +319,32 @@ int lbp_decode_noalloc(const lbp_code *code, const lbp_params *params, int64_t n
                        const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                        uint8_t *osd_out, int32_t *iters_out, float *llr_out, void *stream);
 
+/* ---- CUDA-graph replay of one decode --------------------------------------
+ *
+ * A decode issues a short chain of stream operations (a memset of its work
+ * counters and the BP and OSD kernels); at small batches the host cost of
+ * issuing them is a visible part of the latency.  lbp_graph_create captures
+ * the chain lbp_decode would issue for these arguments into a CUDA graph
+ * (on a private capturing stream; nothing runs), and lbp_graph_launch
+ * replays it on `stream` with one call.  Buffers, sizes and parameters are
+ * frozen at capture: to decode new shots, write their syndromes into the
+ * same `syndromes` buffer (stream-ordered before the launch); outputs land
+ * in the same output buffers.  Results are those of lbp_decode.  Arguments
+ * as for lbp_decode (device buffers; workspace of lbp_workspace_size bytes,
+ * 256-byte aligned), which must stay allocated while the graph exists.
+ * Errors: LBP_EINVAL (as lbp_decode; also while kernel timing is enabled),
+ * LBP_ENOMEM, LBP_ECUDA. */
+typedef struct lbp_graph lbp_graph;
+int lbp_graph_create(const lbp_code *code, const lbp_params *params, int64_t num_shots,
+                     const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
+                     uint8_t *osd_out, int32_t *iters_out, float *llr_out, void *workspace,
+                     size_t workspace_bytes, lbp_graph **out);
+/* Replay the captured decode on `stream` (a cudaStream_t, NULL = legacy
+ * default).  Replays of one graph must not overlap each other. */
+int lbp_graph_launch(lbp_graph *graph, void *stream);
+/* Release the graph (not its buffers).  Replays already launched finish. */
+int lbp_graph_destroy(lbp_graph *graph);
+
 /* Kernel timing instrumentation, off by default.  While enabled, every
  * decode records a CUDA event pair on its stream around each kernel launch
  * (the BP kernel, K_bp, and the OSD kernel, K_osd); lbp_timing_read waits for

@@ -13,4 +13,7 @@ constexpr int kTimeOsd = 1;
 void *timing_begin(cudaStream_t s);
 void timing_end(void *tok, cudaStream_t s, int kind);
 
+// Whether timing is enabled (lbp_timing_enable).
+bool timing_on();
+
 }  // namespace lbp

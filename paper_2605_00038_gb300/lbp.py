@@ -29,7 +29,8 @@ EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_in
             "lbp_code_rounds", "lbp_code_tuned",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
-            "lbp_server_wait", "lbp_server_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
+            "lbp_server_wait", "lbp_server_destroy", "lbp_graph_create", "lbp_graph_launch",
+            "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
             "lbp_strerror"]
 
 
@@ -86,6 +87,12 @@ def lib():
         L.lbp_decode_host.argtypes = dec
         L.lbp_tune.restype = ctypes.c_int
         L.lbp_tune.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.lbp_graph_create.restype = ctypes.c_int
+        L.lbp_graph_create.argtypes = [vp, P, i64, vp, vp, vp, vp, vp, vp, vp, sz, ctypes.POINTER(vp)]
+        L.lbp_graph_launch.restype = ctypes.c_int
+        L.lbp_graph_launch.argtypes = [vp, vp]
+        L.lbp_graph_destroy.restype = ctypes.c_int
+        L.lbp_graph_destroy.argtypes = [vp]
         L.lbp_server_create.restype = ctypes.c_int
         L.lbp_server_create.argtypes = [sz, ctypes.c_int, ctypes.POINTER(vp)]
         L.lbp_server_configure.restype = ctypes.c_int
@@ -283,6 +290,44 @@ def lbp_timing_read():
     _check(lib().lbp_timing_read(ctypes.byref(bm), ctypes.byref(bl), ctypes.byref(om),
                                  ctypes.byref(ol)), "lbp_timing_read")
     return bm.value, bl.value, om.value, ol.value
+
+
+class Graph:
+    """Owning handle of an lbp_graph (a captured decode); keeps the tensors
+    it was captured with alive."""
+
+    def __init__(self, ptr: int, keep):
+        self.ptr = ctypes.c_void_p(ptr)
+        self._keep = keep
+
+    def close(self):
+        if self.ptr:
+            _check(lib().lbp_graph_destroy(self.ptr), "lbp_graph_destroy")
+            self.ptr = ctypes.c_void_p()
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbp_graph_create(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
+                     osd_out, iters_out, llr_out, workspace) -> Graph:
+    """Capture the decode lbp_decode would run for these device buffers."""
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    out = ctypes.c_void_p()
+    _check(lib().lbp_graph_create(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
+                                  _dptr(err_out), _dptr(converged), _dptr(osd_out), _dptr(iters_out),
+                                  _dptr(llr_out), _dptr(workspace), ws_bytes, ctypes.byref(out)),
+           "lbp_graph_create")
+    return Graph(out.value, (syndromes, err_out, converged, osd_out, iters_out, llr_out, workspace))
+
+
+def lbp_graph_launch(graph: Graph, stream=None):
+    """Replay the captured decode on `stream` (default: torch's current stream)."""
+    _check(lib().lbp_graph_launch(graph.ptr, _stream_handle(stream)), "lbp_graph_launch")
 
 
 class Server:

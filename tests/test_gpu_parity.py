@@ -438,6 +438,37 @@ def test_host_buffer_pipeline_matches_device(case):
     dec.close()
 
 
+@pytest.mark.parametrize("B", [1, 64, 3000])
+def test_graph_replay_matches_decode(B):
+    """lbp_graph_create captures the decode of fixed buffers; replays after
+    writing new syndromes into the captured buffer give lbp_decode's outputs
+    for those syndromes, at a latency-layout size (1, 64) and a large one."""
+    w = workloads.c2_d11_spacetime(shots=3 * B)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed + B, num_shots=3 * B)
+    dec = Decoder(w.h, w.priors)
+    prm = dec.params(**dict(w.decoder, seed=7))
+    allx = torch.from_numpy(syn.view(np.int64)).cuda()
+    x = torch.empty((B, allx.shape[1]), dtype=torch.int64, device="cuda")
+    o = dec.alloc(B, want_llr=True)
+    ws = torch.empty(lbp.lbp_workspace_size(dec.code, prm, B) + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    g = lbp.lbp_graph_create(dec.code, prm, B, x, o.err, o.converged, o.osd, o.iters, o.llr, ws)
+    for r in range(3):
+        x.copy_(allx[r * B:(r + 1) * B])
+        lbp.lbp_graph_launch(g)
+        ref = dec.decode(allx[r * B:(r + 1) * B].contiguous(),
+                         dec.params(**dict(w.decoder, seed=7)), want_llr=True)
+        torch.cuda.synchronize()
+        for a, b in ((o.err, ref.err), (o.converged, ref.converged), (o.iters, ref.iters), (o.osd, ref.osd)):
+            assert torch.equal(a, b)
+        assert torch.equal(o.llr.view(torch.int32), ref.llr.view(torch.int32))
+    g.close()
+    with pytest.raises(lbp.LbpError):
+        lbp.lbp_graph_create(dec.code, dec.params(max_iter=0), B, x, o.err, o.converged, o.osd, o.iters,
+                             None, ws)
+    dec.close()
+
+
 def test_bench_launch_config_full_size_sampled():
     """c2 at its full batch (10^6 shots) in the bench's launch configuration:
     sampled shots match the oracle one by one; on every shot the converged or
