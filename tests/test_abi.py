@@ -78,3 +78,27 @@ def test_decode_rejects_bad_params_without_gpu(L):
         assert L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(p), 1, None, None, None, None, None,
                             None, None, 0, None) == lbp.LBP_EINVAL
     assert L.lbp_workspace_size(ctypes.c_void_p(1), ctypes.byref(bad), 10) == 0
+
+
+def test_graph_server_and_tuned_reject_null_without_gpu(L):
+    """The entry points added for graph replay, the serving policy and the
+    tuned-shape query validate their arguments before any CUDA call."""
+    p = lbp.lbp_params_default()
+    out = ctypes.c_void_p()
+    # lbp_graph_create: NULL code, NULL out, empty batch, NULL buffers.
+    assert L.lbp_graph_create(None, ctypes.byref(p), 1, None, None, None, None, None, None, None, 0,
+                              ctypes.byref(out)) == lbp.LBP_EINVAL
+    assert out.value is None
+    assert L.lbp_graph_create(ctypes.c_void_p(1), ctypes.byref(p), 1, None, None, None, None, None,
+                              None, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_graph_create(ctypes.c_void_p(1), ctypes.byref(p), 0, ctypes.c_void_p(8),
+                              ctypes.c_void_p(8), ctypes.c_void_p(8), None, ctypes.c_void_p(8), None,
+                              ctypes.c_void_p(256), 1 << 20, ctypes.byref(out)) == lbp.LBP_EINVAL
+    assert L.lbp_graph_create(ctypes.c_void_p(1), ctypes.byref(p), 4, None, None, None, None, None,
+                              None, None, 0, ctypes.byref(out)) == lbp.LBP_EINVAL
+    assert L.lbp_graph_launch(None, None) == lbp.LBP_EINVAL
+    assert L.lbp_graph_destroy(None) == lbp.LBP_EINVAL
+    # lbp_server_configure / lbp_code_tuned on NULL handles.
+    assert L.lbp_server_configure(None, 1 << 20, 1) == lbp.LBP_EINVAL
+    g = ctypes.c_int32()
+    assert L.lbp_code_tuned(None, 0, 0, None, ctypes.byref(g), None) == lbp.LBP_EINVAL
