@@ -429,3 +429,35 @@ def test_rejects_weight_one_rows():
     h = SparseH.from_rows([[0], [0, 1]], 2)
     with pytest.raises(ValueError):
         oracle.decode(h, np.full(2, 0.1), np.zeros((1, 2), np.uint8), OracleParams())
+
+
+@pytest.mark.parametrize("prec", [PREC_F64, PREC_F32])
+def test_scale_schedule_closed_form(prec):
+    """The normalisation factor of Alg. 1: f_i = 1 - 2^-(i+1) (adaptive) or the
+    constant 0.625.  On one weight-2 check with equal priors and syndrome 1 the
+    estimate stays zero, so BP runs all I iterations; every V2C message equals
+    mu (lambda - beta = (mu + beta) - beta is exact), each C2V message is
+    -fl(f_i mu), and the final posterior is mu - fl(f_{I-1} mu), exact by
+    Sterbenz's lemma.  numpy's IEEE arithmetic in the same precision gives the
+    expected bits.  In binary32 f_i rounds to 1.0 from i = 24 on, so after 25
+    iterations lambda is exactly 0 (the hard decisions flip to 1)."""
+    h = SparseH.from_rows([[0, 1]], 2)
+    p = 0.2
+    S = np.ones((1, 1), dtype=np.uint8)
+    ft = np.float64 if prec == PREC_F64 else np.float32
+    mu = ft(mu_of(p))
+    for I in (1, 2, 3, 7, 12, 24, 25):
+        r = oracle.decode(h, np.full(2, p), S,
+                          OracleParams(max_iter=I, lottery=False, osd=False, prec=prec), want_llr=True)
+        assert r.converged[0] == 0 and r.iters[0] == I
+        f = ft(1.0 - 2.0 ** -I)                 # f_{I-1}, rounded once to the precision
+        expect = mu - ft(f * mu)
+        assert r.llr[0, 0] == r.llr[0, 1] == float(expect), (I, r.llr[0], expect)
+        if prec == PREC_F32 and I == 25:
+            assert expect == 0.0 and r.err[0].tolist() == [1, 1]
+        else:
+            assert r.err[0].tolist() == [0, 0]
+    r = oracle.decode(h, np.full(2, p), S,
+                      OracleParams(max_iter=3, scale_mode=0, scale_const=0.625, lottery=False, osd=False,
+                                   prec=prec), want_llr=True)
+    assert r.llr[0, 0] == float(mu - ft(ft(0.625) * mu))
