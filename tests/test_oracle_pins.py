@@ -461,3 +461,24 @@ def test_scale_schedule_closed_form(prec):
                       OracleParams(max_iter=3, scale_mode=0, scale_const=0.625, lottery=False, osd=False,
                                    prec=prec), want_llr=True)
     assert r.llr[0, 0] == float(mu - ft(ft(0.625) * mu))
+
+
+@pytest.mark.parametrize("prec", [PREC_F64, PREC_F32])
+def test_lottery_never_runs_at_the_last_iteration(prec):
+    """Reading R7 (Alg. 3 applied for i >= skip, never at i = I - 1): with
+    lottery_skip = I - 1 the lottery has no iteration left, so every output
+    equals the decode without the lottery; one iteration earlier it does act
+    (some shot's outputs change), so the comparison is not vacuous."""
+    hz, _ = rotated_surface(5)
+    h = spacetime(hz, 5)
+    pri = spacetime_priors(hz, 5, 0.02, 0.02)
+    _, syn = sampler.sample(h, pri, seed=17, num_shots=400)
+    S = sampler.unpack(syn, h.m)
+    I = 12
+    base = dict(max_iter=I, osd=False, prec=prec, seed=3)
+    off = oracle.decode(h, pri, S, OracleParams(lottery=False, **base), want_llr=True)
+    last = oracle.decode(h, pri, S, OracleParams(lottery=True, lottery_skip=I - 1, **base), want_llr=True)
+    for k in ("err", "converged", "iters", "llr"):
+        assert np.array_equal(getattr(off, k), getattr(last, k)), k
+    early = oracle.decode(h, pri, S, OracleParams(lottery=True, lottery_skip=I - 2, **base), want_llr=True)
+    assert not np.array_equal(off.llr, early.llr)
