@@ -482,3 +482,37 @@ def test_lottery_never_runs_at_the_last_iteration(prec):
         assert np.array_equal(getattr(off, k), getattr(last, k)), k
     early = oracle.decode(h, pri, S, OracleParams(lottery=True, lottery_skip=I - 2, **base), want_llr=True)
     assert not np.array_equal(off.llr, early.llr)
+
+
+def test_lottery_trajectory_on_one_check_closed_form():
+    """Alg. 3 (proposed rule, skip 0) on one weight-2 check, equal priors,
+    syndrome 1, where BP alone never converges.  By hand: after iteration 0
+    both posteriors are mu - fl(mu/2) > 0; U = {check 0}, both columns count
+    one unsatisfied check and have equal |lambda|, so the lowest column
+    (reading R9) is flipped.  Iteration 1 then reads alpha_0 = lambda_0 - beta_0
+    from the flipped posterior (reading R10), alpha_0 = 0 and alpha_1 = mu,
+    giving (mu - fl(0.75 mu), mu - 0).  Iteration 1's lottery flips column 0
+    again (least |lambda|), and iteration 2 gives the values below.  The
+    expected bits come from numpy float64 doing the same operations."""
+    h = SparseH.from_rows([[0, 1]], 2)
+    p = 0.2
+    S = np.ones((1, 1), dtype=np.uint8)
+    mu = np.float64(mu_of(p))
+
+    def run(I):
+        return oracle.decode(h, np.full(2, p), S,
+                             OracleParams(max_iter=I, lottery=True, lottery_skip=0, osd=False, prec=PREC_F64),
+                             want_llr=True)
+
+    half = mu - np.float64(0.5 * mu)
+    r = run(1)                                             # no lottery at the last iteration
+    assert r.llr[0].tolist() == [half, half]
+    b75 = np.float64(0.75 * mu)
+    r = run(2)
+    assert r.llr[0].tolist() == [mu - b75, mu]             # column 0 was flipped after iteration 0
+    lam0 = -(mu - b75)                                     # iteration 1's flip of column 0
+    a0 = lam0 - (-b75)                                     # alpha_0 = lambda_0 - beta_0 (from iteration 1)
+    a1 = mu - (-0.0)                                       # alpha_1 = lambda_1 - beta_1, beta_1 = -0
+    r = run(3)
+    assert r.llr[0].tolist() == [mu - np.float64(0.875 * a1), mu - np.float64(0.875 * abs(a0))]
+    assert r.converged[0] == 0 and r.err[0].tolist() == [0, 0]
