@@ -136,8 +136,10 @@ def workload(shots):
 
 
 def roofline_model(w, iters_total, shots):
-    """Algorithmic work of K_bp ('Roofline'): per shot-iteration
-    8 E + 2 m + n operations; per shot the syndrome in and results out."""
+    """Algorithmic work of K_bp: per shot-iteration 8 E + 2 m + n operations
+    (per edge the V2C subtract, two minimum compares, sign parity, output
+    select and sign, LLR add and syndrome XOR; per check two scale multiplies;
+    per column the hard decision); per shot the syndrome in and results out."""
     E, m, n = w.h.nnz, w.h.m, w.h.n
     ops = float(iters_total) * (8 * E + 2 * m + n)
     io = shots * (8 * ((m + 63) // 64) + 8 * ((n + 63) // 64) + 1 + 1 + 4)

@@ -67,3 +67,28 @@ def test_two_gloo_ranks_split_shots_and_take_max_time():
     r1 = res[1]
     _, full = sampler.sample(h, pri, seed=5, num_shots=r1[1][1] + shots)
     assert np.array_equal(full[r1[1][1]:], r1[2])
+
+
+def test_clock_summary_and_roofline_helpers():
+    """Host-side bench helpers: the nvidia-smi sample summary (median clock,
+    throttle reasons that were ever active) and the K_bp work model."""
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["unsampled"]
+    cs.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Active"],
+               ["0", "1900", "2070", "950", "0x4", "Not Active", "Active", "Not Active", "Not Active"],
+               ["0", "2070", "2070", "880", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0,
+                 "reasons": ["hw_thermal_slowdown", "sw_power_cap"], "samples": 3}
+    hz, _ = rotated_surface(3)
+    h = spacetime(hz, 3)
+
+    class W:
+        pass
+
+    w = W()
+    w.h = h
+    ops, io = bench.roofline_model(w, iters_total=10, shots=4)
+    assert ops == 10 * (8 * h.nnz + 2 * h.m + h.n)
+    assert io == 4 * (8 * ((h.m + 63) // 64) + 8 * ((h.n + 63) // 64) + 6)
+    assert bench.alu_peak_ops(2070.0) == 152 * 128 * 2070e6
