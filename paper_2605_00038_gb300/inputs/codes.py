@@ -186,6 +186,12 @@ def spacetime(h: SparseH, T: int, boundary: str = "open") -> SparseH:
     return SparseH.from_rows(rows, T * n + nblocks * m)
 
 
+def block_diag(a: SparseH, b: SparseH) -> SparseH:
+    """[[a, 0], [0, b]]: rows of b after a's, columns of b after a's."""
+    rows = [list(r) for r in a.rows()] + [[a.n + q for q in r] for r in b.rows()]
+    return SparseH.from_rows(rows, a.n + b.n)
+
+
 def spacetime_priors(h: SparseH, T: int, p_data: float, p_meas: float,
                      boundary: str = "open") -> np.ndarray:
     nblocks = T if boundary == "cyclic" else T - 1

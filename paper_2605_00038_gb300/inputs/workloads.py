@@ -11,7 +11,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .codes import SparseH, bb_code, rotated_surface, spacetime, spacetime_priors
+from .codes import SparseH, bb_code, block_diag, rotated_surface, spacetime, spacetime_priors
 
 
 @dataclass
@@ -56,6 +56,17 @@ def c5_d25_spacetime(msg: int = 0, shots: int = 1 << 20) -> Workload:
     return Workload("rotated_d25_st25_p0.004", st, spacetime_priors(hz, 25, 0.004, 0.004), shots, 6,
                     dict(max_iter=100, scale_mode=1, lottery=1, lottery_skip=6, osd=0, msg=msg),
                     "rotated surface d=25, 25 rounds space-time H 7800x23113 (nnz 44976), p=0.004")
+
+
+def c5_d25_spacetime_xz(msg: int = 0, shots: int = 1 << 20) -> Workload:
+    """The stress form of the d=25 workload: X and Z space-time matrices on the
+    block diagonal (both error types decoded in one call), 15,600 x 46,226."""
+    hx, hz = rotated_surface(25)
+    st = block_diag(spacetime(hz, 25), spacetime(hx, 25))
+    pri = np.concatenate([spacetime_priors(hz, 25, 0.004, 0.004), spacetime_priors(hx, 25, 0.004, 0.004)])
+    return Workload("rotated_d25_st25_xz_p0.004", st, pri, shots, 7,
+                    dict(max_iter=100, scale_mode=1, lottery=1, lottery_skip=6, osd=0, msg=msg),
+                    "rotated surface d=25, 25 rounds, X and Z space-time H block-diagonal 15600x46226, p=0.004")
 
 
 def serving_codes():

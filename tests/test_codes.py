@@ -173,3 +173,17 @@ def test_sampler_splitmix64_published_outputs():
     # SplitMix64 from state 0: the first three outputs of the published generator.
     assert [sampler.splitmix64_at(0, k) for k in range(3)] == [
         0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_d25_xz_stress_form_sizes():
+    """Reading R5's stress form of the d=25 workload: X and Z space-time
+    matrices block-diagonal, 15,600 x 46,226 with twice the single-type nonzeros;
+    the halves do not touch each other's columns."""
+    from paper_2605_00038_gb300.inputs import workloads
+    w = workloads.c5_d25_spacetime_xz(shots=1)
+    single = workloads.c5_d25_spacetime(shots=1)
+    assert (w.h.m, w.h.n) == (15600, 46226)
+    assert w.h.nnz == 2 * single.h.nnz == 2 * 44976
+    assert w.priors.shape == (46226,)
+    rows = list(w.h.rows())
+    assert max(max(r) for r in rows[:7800]) < 23113 <= min(min(r) for r in rows[7800:])

@@ -134,6 +134,18 @@ def test_c5_d25_spacetime_precisions(msg):
     assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
 
 
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
+def test_c5_d25_xz_stress_form(msg):
+    """Reading R5's stress form of the d=25 workload, X and Z space-time
+    matrices block-diagonal (15,600 x 46,226): message offsets exceed 16 bits,
+    so the 32-bit image is read from global memory; a sample of shots matches
+    the oracle."""
+    w = workloads.c5_d25_spacetime_xz(msg=msg, shots=48)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    kw = dict(w.decoder, max_iter=60, seed=8)
+    assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
+
+
 @pytest.mark.parametrize("policy", [1, 2, 3, 4])
 def test_lottery_baseline_policies(policy):
     """The four baseline sign-flip policies of Sec. III-B, on the bounded-degree
