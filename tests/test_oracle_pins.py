@@ -516,3 +516,92 @@ def test_lottery_trajectory_on_one_check_closed_form():
     r = run(3)
     assert r.llr[0].tolist() == [mu - np.float64(0.875 * a1), mu - np.float64(0.875 * abs(a0))]
     assert r.converged[0] == 0 and r.err[0].tolist() == [0, 0]
+
+
+def _store_i8(x):
+    """Int3.4 from its definition (Sec. VI-C): nearest multiple of 1/16, ties
+    to even, saturated to [-127, 127] / 16."""
+    return float(np.clip(np.rint(16.0 * x), -127.0, 127.0) / 16.0)
+
+
+@pytest.mark.parametrize("prec", [PREC_F16, PREC_I8])
+def test_message_storage_inside_decode_closed_form(prec):
+    """Reduced-precision message storage is applied inside the decode, not
+    only by the rounding helpers (Sec. VI-C; readings R15, R16).
+
+    Same single weight-2 check as the schedule pin: equal priors, syndrome 1,
+    so BP runs all I iterations.  In these modes arithmetic is binary32 and
+    each C2V message is rounded once when stored.  The stored magnitude h of
+    iteration i is store(fl32(f_i mu)); h lies on a grid that is a multiple of
+    binary32's spacing at mu (binary16 keeps 11 bits at an exponent no larger
+    than mu's; Int3.4 has spacing 1/16 and mu >= 1 here), so both
+    lambda = mu - h and the next V2C message lambda + h = mu are exact.  Hence
+    the final posterior is mu - store(fl32(f_{I-1} mu)), with store taken
+    from numpy's IEEE half or from the Int3.4 definition.  The priors make the
+    rounding change the bits, and p = 1e-4 (mu = 9.21 > 127/16) drives Int3.4
+    into saturation once f_i mu > 7.97, so a decode that skipped the storage
+    rounding, or the saturation, fails."""
+    h = SparseH.from_rows([[0, 1]], 2)
+    S = np.ones((1, 1), dtype=np.uint8)
+    changed = saturated = 0
+    for p in (0.2, 0.07, 1e-4):
+        mu = np.float32(mu_of(p))
+        for I in (1, 2, 3, 7, 12):
+            r = oracle.decode(h, np.full(2, p), S,
+                              OracleParams(max_iter=I, lottery=False, osd=False, prec=prec), want_llr=True)
+            assert r.converged[0] == 0 and r.iters[0] == I
+            prod = np.float32(np.float32(1.0 - 2.0 ** -I) * mu)      # fl32(f_{I-1} mu)
+            if prec == PREC_F16:
+                hq = float(np.float16(prod))
+            else:
+                hq = _store_i8(float(prod))
+                saturated += hq == 127.0 / 16.0
+            changed += hq != float(prod)
+            expect = float(mu) - hq                                  # exact (see above)
+            assert expect == float(np.float32(expect))
+            assert r.llr[0, 0] == r.llr[0, 1] == expect, (p, I, r.llr[0], expect)
+    assert changed >= 10
+    if prec == PREC_I8:
+        assert saturated >= 2
+
+
+def test_lottery_reads_previous_iteration_syndrome():
+    """Reading R6: the lottery of iteration i draws from U = s_hat(i-1) xor s
+    (Alg. 3 and the pipelining note of Sec. IV-B), with s_hat(-1) = 0, not from
+    this iteration's s_hat(i).  Hand-worked on the chain c0 = {v0, v1},
+    c1 = {v1, v2}, mu ~ (10, 1, 1), s = (1, 0), skip 0, I = 2, F64:
+
+    iteration 0 (f = 1/2): beta = (-mu1/2, -mu0/2 | +mu2/2, +mu1/2), so
+    lambda ~ (9.5, -3.5, 1.5), e_hat = {v1}, s_hat(0) = (1, 1) != s.
+    Lottery at i = 0: U = s_hat(-1) xor s = {c0}, so c* = c0; v0 and v1 each
+    meet one member of U, and |lambda_1| < |lambda_0| picks v1: lambda_1 -> +3.5.
+    (From s_hat(0) instead, U = {c1}, c* = c1 and v2 would be flipped; the
+    decode then converges at iteration 1 on e_hat = {v1, v2}.)
+    iteration 1 (f = 3/4), from the flipped posterior: alpha = (~10, 8.5 | 3, 1),
+    beta = (-0.75 |alpha_1c0|, -0.75 |alpha_0c0| | 0.75 alpha_2c1, 0.75 alpha_1c1),
+    lambda ~ (3.625, -5.75, 3.25): s_hat = (1, 1) != s, no lottery at I - 1,
+    so the decode ends unconverged with those posteriors.  The expected bits
+    repeat these operations in numpy float64, in the oracle's order of sums."""
+    h = SparseH.from_rows([[0, 1], [1, 2]], 3)
+    target = np.array([10.0, 1.0, 1.0])
+    p = 1.0 / (1.0 + np.exp(target))
+    mu = mu_of(p)
+    S = np.array([[1, 0]], dtype=np.uint8)
+    r = oracle.decode(h, p, S, OracleParams(max_iter=2, lottery=True, lottery_skip=0, osd=False, prec=PREC_F64),
+                      want_llr=True)
+    # iteration 0
+    b00, b10, b11, b21 = -(0.5 * mu[1]), -(0.5 * mu[0]), 0.5 * mu[2], 0.5 * mu[1]
+    lam = np.array([mu[0] + b00, (mu[1] + b10) + b11, mu[2] + b21])
+    assert lam[0] > 0 and lam[1] <= 0 and lam[2] > 0             # e_hat(0) = {v1}, s_hat(0) = (1, 1)
+    assert abs(lam[1]) < abs(lam[0])
+    lam[1] = -lam[1]                                              # the lottery's flip (c* = c0, v* = v1)
+    # iteration 1
+    a00, a10, a11, a21 = lam[0] - b00, lam[1] - b10, lam[1] - b11, lam[2] - b21
+    assert min(a00, a10, a11, a21) > 0
+    b00, b10 = -(0.75 * abs(a10)), -(0.75 * abs(a00))
+    b11, b21 = 0.75 * a21, 0.75 * a11
+    want = [mu[0] + b00, (mu[1] + b10) + b11, mu[2] + b21]
+    assert want[1] <= 0 < min(want[0], want[2])
+    assert r.converged[0] == 0 and r.iters[0] == 2
+    assert r.llr[0].tolist() == want
+    assert r.err[0].tolist() == [0, 1, 0]
