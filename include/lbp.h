@@ -123,7 +123,13 @@ void lbp_params_default(lbp_params *p);
  * pairs of checks into warps (chosen by a deterministic local search over
  * the shared-memory bank conflicts of the posterior gathers).  Results are
  * the same with or without it; LBP_BANK_LAYOUT=0 (read at load) turns it
- * off. */
+ * off.
+ *
+ * Environment switches for experiments are read here, once, and kept in the
+ * code object, so decodes never depend on the environment at call time:
+ * LBP_BANK_LAYOUT, LBP_GRAPH (graph form, see lbp_code_surface),
+ * LBP_BP_SHAPE ("S,G": BP groups per CTA and threads per group),
+ * LBP_OSD_POOL_ROWS and LBP_OSD_LAT (see lbp_workspace_size). */
 int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *priors, lbp_code **out);
 
@@ -167,13 +173,13 @@ int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r
  * changed rows take dense copies from a per-warp pool of C rows, by default
  * max(192, m / 2) (at most m), lowered so that the pools of all warps stay
  * within 1 GiB but never below min(m, 192).  The environment variable
- * LBP_OSD_POOL_ROWS (read at every call) sets C (1..m); a shot that needs
- * more rows is solved by the block-wide OSD kernel instead, with the same
- * result.  Set it identically for lbp_workspace_size and lbp_decode.
+ * LBP_OSD_POOL_ROWS (read when the code is loaded) sets C (1..m); a shot
+ * that needs more rows is solved by the block-wide OSD kernel instead, with
+ * the same result.
  * A call with num_shots at most the SM count runs OSD in its latency layout
  * (one warp per CTA; lambda and the first pool rows that fit in shared
  * memory, the other rows of the same C in the workspace); LBP_OSD_LAT=0
- * turns that off.  The workspace size does not depend on it. */
+ * (read when the code is loaded) turns that off.  The workspace size does not depend on it. */
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).
@@ -294,9 +300,10 @@ int lbp_server_wait(lbp_server *server, int64_t ticket, double *latency_s);
 int lbp_server_destroy(lbp_server *server);
 
 /* Same decode as lbp_decode, for callers that cannot allocate device memory
- * (no cudaMalloc, no allocator callback: e.g. a latency-bound request loop on
- * a pre-sized device, a plugin whose host owns every allocation, a caller
- * inside stream capture).  No workspace argument: scratch comes from a fixed
+ * (no cudaMalloc, no allocator callback): e.g. a latency-bound request loop
+ * on a pre-sized device, where an allocation could stall or synchronise the
+ * device in the middle of a request, or a plugin whose host process owns
+ * every allocation and gives it none.  No workspace argument: scratch comes from a fixed
  * device array of LBP_NOALLOC_SCRATCH_BYTES bytes inside this library, which
  * every GPU that loads the library holds until the process exits.  The call
  * allocates nothing; buffers and their meaning are those of lbp_decode.
@@ -307,9 +314,9 @@ int lbp_server_destroy(lbp_server *server);
  *  - Returns LBP_E2BIG, enqueuing nothing, when lbp_workspace_size(code,
  *    params, num_shots) exceeds LBP_NOALLOC_SCRATCH_BYTES (OSD on a large
  *    code, or very large OSD batches); use lbp_decode with a workspace then.
- *  - The first call on each device looks up the array's device address (with
- *    that device current) and keeps it: make that first call before any
- *    stream capture that should contain a later call.
+ *  - The first call on each device does a one-time set-up: with that device
+ *    current, it looks up the array's device address (cudaGetSymbolAddress)
+ *    and keeps it.  Make that first call before any stream capture begins.
  *  - All calls on a device share the array; the decode clears what must start
  *    at zero on the call's stream, so calls in order on one stream are
  *    independent, but calls that overlap on the GPU (other streams, other host

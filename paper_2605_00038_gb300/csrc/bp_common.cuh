@@ -65,13 +65,22 @@ __device__ __forceinline__ __half2 make_pair(__half a, __half b) { return __halv
 __device__ __forceinline__ char2 make_pair(int8_t a, int8_t b) { return make_char2(a, b); }
 
 // -------------------------------------------------------------- group sync
+//
+// Named barriers over the G threads of one group.  They use the non-.aligned
+// PTX forms (barrier.sync, barrier.red): the .aligned forms (bar.sync,
+// bar.red) require every thread of a warp to execute the barrier together,
+// and the kernels reach these barriers right after code whose trip counts or
+// branches differ between the lanes of a warp (strided loops over checks and
+// columns, lane-0 stores, the lottery warp's scans).  The non-aligned forms
+// count arriving threads one by one, so a warp that has not reconverged
+// still synchronises correctly.
 
 template <int G>
 __device__ __forceinline__ void group_sync(int bar) {
     if (G == 32) {
         __syncwarp();
     } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(G) : "memory");
+        asm volatile("barrier.sync %0, %1;" ::"r"(bar), "r"(G) : "memory");
     }
 }
 
@@ -85,7 +94,7 @@ __device__ __forceinline__ bool group_sync_or(int bar, bool p) {
         asm volatile(
             "{\n\t.reg .pred pi, po;\n\t"
             "setp.ne.u32 pi, %1, 0;\n\t"
-            "bar.red.or.pred po, %2, %3, pi;\n\t"
+            "barrier.red.or.pred po, %2, %3, pi;\n\t"
             "selp.u32 %0, 1, 0, po;\n\t}"
             : "=r"(r)
             : "r"(static_cast<unsigned>(p)), "r"(bar), "r"(G)

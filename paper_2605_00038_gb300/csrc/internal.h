@@ -152,4 +152,10 @@ struct lbp_code {
     // groups per CTA and threads per group.
     int tuned_groups[6], tuned_G[6];   // per (rule, message type), lbp_tune
     int tuned_graph[6];                // graph form chosen by lbp_tune (0 none, 1 image, 2 implicit)
+    // Experiment switches, read from the environment once, by lbp_load_code,
+    // so that decodes of a loaded code never depend on the environment at
+    // call time: LBP_GRAPH (0 unset, 1 table, 2 implicit, 3 round),
+    // LBP_BP_SHAPE "S,G" (0, 0 unset), LBP_OSD_POOL_ROWS (0 unset) and
+    // LBP_OSD_LAT (0: latency layout off).
+    int env_graph, env_S, env_G, env_pool_rows, env_osd_lat;
 };

@@ -7,6 +7,7 @@
 // memory once per CTA.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -296,6 +297,35 @@ extern "C" const char *lbp_strerror(int code) {
     }
 }
 
+namespace {
+
+// The experiment switches of lbp_code, read once here (see internal.h).
+void read_env_switches(lbp_code *c) {
+    c->env_graph = 0;
+    if (const char *g = std::getenv("LBP_GRAPH")) {
+        if (!std::strcmp(g, "table")) c->env_graph = 1;
+        else if (!std::strcmp(g, "implicit")) c->env_graph = 2;
+        else if (!std::strcmp(g, "round")) c->env_graph = 3;
+    }
+    c->env_S = c->env_G = 0;
+    if (const char *sh = std::getenv("LBP_BP_SHAPE")) {
+        int S = 0, G = 0;
+        if (std::sscanf(sh, "%d,%d", &S, &G) == 2 && S > 0 && G > 0) {
+            c->env_S = S;
+            c->env_G = G;
+        }
+    }
+    c->env_pool_rows = 0;
+    if (const char *pr = std::getenv("LBP_OSD_POOL_ROWS")) {
+        const int v = std::atoi(pr);
+        if (v > 0) c->env_pool_rows = v;
+    }
+    const char *lat = std::getenv("LBP_OSD_LAT");
+    c->env_osd_lat = (lat && !std::strcmp(lat, "0")) ? 0 : 1;
+}
+
+}  // namespace
+
 extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                              const double *priors, lbp_code **out) {
     if (!out) return LBP_EINVAL;
@@ -343,6 +373,7 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
 
     lbp_code *c = new (std::nothrow) lbp_code();
     if (!c) return LBP_ENOMEM;
+    read_env_switches(c);
     std::memset(c, 0, sizeof(*c));
     c->m = m; c->n = n; c->nnz = nnz;
     c->max_row_deg = maxdeg; c->max_col_deg = maxcol;

@@ -2,7 +2,8 @@
 //
 // K_bp runs persistent: one CTA per SM, S groups of G threads per CTA, the
 // graph image plus S shots' state in shared memory.  S and G come from the
-// shared-memory budget, lbp_tune's stored shape or LBP_BP_SHAPE; a call of
+// shared-memory budget, lbp_tune's stored shape or LBP_BP_SHAPE (read when
+// the code was loaded, like every environment switch here); a call of
 // at most one shot per SM that runs alone on the device gets one shot per CTA
 // with up to 1024 threads.  K_osd follows on the same stream and drains the
 // queue K_bp filled; no host round trip separates them.
@@ -107,11 +108,8 @@ int validate_params(const lbp_params *p) {
 int graph_form(const lbp_code *c, int mi, int req_graph, size_t state_bytes) {
     auto ok = [&](int f) { return f == 1 || (f == 2 && c->surface) || (f == 3 && c->round); };
     if (req_graph >= 1 && req_graph <= 3) return ok(req_graph) ? req_graph : -1;
-    if (const char *env = std::getenv("LBP_GRAPH")) {
-        if (!std::strcmp(env, "table")) return 1;
-        if (!std::strcmp(env, "implicit") && ok(2)) return 2;
-        if (!std::strcmp(env, "round") && ok(3)) return 3;
-    }
+    if (c->env_graph == 1) return 1;
+    if (c->env_graph >= 2 && ok(c->env_graph)) return c->env_graph;
     if (c->tuned_graph[mi] > 0 && ok(c->tuned_graph[mi])) return c->tuned_graph[mi];
     (void)state_bytes;
     return 1;
@@ -166,9 +164,8 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
             }
             int s_req = req_S, g_req = req_G;
             if (!g_req) {
-                if (const char *env = std::getenv("LBP_BP_SHAPE")) {
-                    if (std::sscanf(env, "%d,%d", &s_req, &g_req) != 2) s_req = g_req = 0;
-                }
+                s_req = c->env_S;
+                g_req = c->env_G;
             }
             if (g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 || g_req == 256 || g_req == 512 ||
                 g_req == 1024) {
@@ -258,9 +255,8 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     // Explicit shape (lbp_tune candidates), then the LBP_BP_SHAPE override "S,G".
     int s_req = req_S, g_req = req_G;
     if (!g_req) {
-        if (const char *env = std::getenv("LBP_BP_SHAPE")) {
-            if (std::sscanf(env, "%d,%d", &s_req, &g_req) != 2) s_req = g_req = 0;
-        }
+        s_req = c->env_S;
+        g_req = c->env_G;
     }
     const bool g_ok = g_req == 32 || g_req == 64 || g_req == 96 || g_req == 128 || g_req == 192 ||
                       g_req == 256 || (p.ell && (g_req == 512 || g_req == 1024));
@@ -361,9 +357,8 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
     // p = 0.003) would otherwise send a quarter of their OSD shots to K_osd.
     int C = c->m / 2 > 192 ? c->m / 2 : 192;
     if (C > c->m) C = c->m;
-    if (const char *env = std::getenv("LBP_OSD_POOL_ROWS")) {
-        const int v = std::atoi(env);
-        if (v > 0 && v <= c->m) C = v;
+    if (c->env_pool_rows > 0) {
+        if (c->env_pool_rows <= c->m) C = c->env_pool_rows;
     } else if (warps_for(C) >= 1) {
         const int floor_c = c->m < 192 ? c->m : 192;
         // Up to 15% fewer rows when that fits another warp per SM (the
@@ -400,9 +395,7 @@ void plan_osd_warp(const lbp_code *c, int64_t num_shots, OsdWarpPlan *out) {
 // overflow to K_osd.  LBP_OSD_LAT=0 turns it off.
 bool plan_osd_lat(const lbp_code *c, int64_t num_shots, const OsdWarpPlan &wp, OsdWarpPlan *out) {
     if (!wp.ok || num_shots > c->sm_count) return false;
-    if (const char *env = std::getenv("LBP_OSD_LAT")) {
-        if (!std::strcmp(env, "0")) return false;
-    }
+    if (!c->env_osd_lat) return false;
     OsdWarpPlan p = wp;
     const size_t budget = static_cast<size_t>(c->smem_optin) - p.image;
     const uint32_t lbb = align16u(4u * static_cast<uint32_t>(c->n));

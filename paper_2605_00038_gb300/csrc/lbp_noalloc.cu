@@ -1,19 +1,20 @@
 // lbp_decode_noalloc: the decode of lbp_decode for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc or an allocator: code that runs where a
-// device allocation may stall or synchronise at the wrong moment (a
-// latency-bound request loop on a pre-sized device, a plugin whose host
-// process owns every allocation, a caller inside stream capture).  This entry
-// point takes its scratch from a fixed array in device memory that the
-// library defines, so the caller passes only inputs and outputs.
+// Some callers cannot call cudaMalloc or an allocator: a latency-bound request
+// loop on a pre-sized device, where an allocation could stall or synchronise
+// the device in the middle of a request, or a plugin whose host process owns
+// every allocation and hands it none.  This entry point takes its scratch
+// from a fixed array in device memory that the library defines, so the
+// caller passes only inputs and outputs.
 //
 // The array is a file-scope __device__ variable of kNoAllocScratchBytes bytes:
 // every GPU that loads this library holds it until the process exits.  Host
 // code cannot use the array's name as a device address (it is a host-side
-// stand-in), so the first call on a device looks the address up with
-// cudaGetSymbolAddress, with that device current, and keeps it; the decode
-// kernels receive that pointer.  Every call on a device shares the array and
+// stand-in), so the first call on a device does a one-time set-up: it looks
+// the address up with cudaGetSymbolAddress, with that device current, and
+// keeps it; the decode kernels receive that pointer.  That first call should
+// come before any stream capture begins.  Every call on a device shares the array and
 // it keeps the last call's contents: the decode path clears what must start at
 // zero (its shot and queue counters) on the call's stream before the kernels
 // run, so consecutive calls on one stream are independent, but calls that

@@ -1,8 +1,9 @@
 """lbp_decode_noalloc: the decode for callers that cannot allocate device memory.
 
-Such callers (a request loop on a pre-sized device, a host that owns every
-allocation, code inside stream capture) pass only inputs and outputs; the
-library's fixed device scratch array replaces the caller-provided workspace.
+Such callers (a latency-bound request loop on a pre-sized device, where an
+allocation could stall it mid-request, or a plugin whose host process owns
+every allocation) pass only inputs and outputs; the library's fixed device
+scratch array replaces the caller-provided workspace.
 These tests call it through the C ABI and compare it with lbp_decode on the
 same inputs, twice in a row, with the same tolerance as the other parity
 tests (bit-identical decisions, LLRs to 1e-5 relative).  The file sorts last
