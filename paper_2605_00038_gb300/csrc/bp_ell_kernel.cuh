@@ -33,7 +33,13 @@
 // Placement: the graph image and each group's state sit in shared memory when
 // they fit (kGraphSmem, kStateSmem); otherwise they are read from global
 // memory (the image is L2-resident; the state goes to a per-group slice of the
-// workspace), which is how the d=25 space-time code runs.
+// workspace).  A state slightly too large for shared memory (the d=25
+// space-time code with binary32 messages) is split (kSplit): the posteriors,
+// syndrome words and the first ks message slots stay in shared memory, the
+// other slots go to the workspace.  The check phase moves those slots as
+// coalesced pairs; the column phase gathers them, which for a space-time
+// matrix touches only the measurement columns, whose messages of one round
+// block are contiguous.
 // Lottery: the group's last warp, which has the fewest rounds in both phases,
 // runs it.  For the random-check policies it draws c* right after its
 // check-phase rounds (c* depends only on s_hat(i-1), s and the draw).  The
@@ -76,6 +82,11 @@ struct BpEllArgs {
     uint32_t state_bytes;
     uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
     uint8_t *gstate;          // per-group state slices when not in shared memory
+    // Split state (kSplit): message slots [0, ks) live in shared memory with
+    // the rest of the shot's state, slots [ks, DC) in a per-group workspace
+    // slice of gbeta_bytes at gstate.
+    int32_t ks;
+    uint32_t gbeta_bytes;
     uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
     SurfaceDesc surf;         // implicit graph (SurfaceGraph)
     RoundDesc rnd;            // round-periodic graph (RoundGraph)
@@ -140,10 +151,11 @@ __device__ __forceinline__ void check_update_sp(const float (&al)[DC], uint32_t 
 }
 
 template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename GraphT,
-          int kRule = LBP_RULE_MIN_SUM>
+          int kRule = LBP_RULE_MIN_SUM, bool kSplit = false>
 __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
     static_assert(GraphT::kImage || !kGraphSmem, "an implicit graph has no image to stage");
+    static_assert(!kSplit || (kStateSmem && !kGraphSmem), "a split state keeps its shared part beside a global image");
     using PairT = typename Pair<MsgT>::type;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
@@ -177,6 +189,13 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
         : reinterpret_cast<volatile uint32_t *>(smem + image_smem + 16 * grp);
     MsgT *beta = reinterpret_cast<MsgT *>(st + a.off_beta);
     PairT *beta2 = reinterpret_cast<PairT *>(beta);
+    // Message slots [ks, DC) of a split state: gbeta[(k - ks) * R + c].
+    const int ks = kSplit ? a.ks : DC;
+    const uint32_t ksR = static_cast<uint32_t>(ks) * static_cast<uint32_t>(R);
+    MsgT *gbeta = kSplit ? reinterpret_cast<MsgT *>(a.gstate + (static_cast<size_t>(blockIdx.x) * groups + grp) *
+                                                                  a.gbeta_bytes)
+                         : nullptr;
+    PairT *gbeta2 = reinterpret_cast<PairT *>(gbeta);
     float *lam = reinterpret_cast<float *>(st + a.off_lam);
     float2 *lam2 = reinterpret_cast<float2 *>(lam);
     uint32_t *s_w = reinterpret_cast<uint32_t *>(st + a.off_s);
@@ -239,7 +258,8 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 } else {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
-                        const PairT bb = beta2[((k * R) >> 1) + pr];
+                        const PairT bb = (kSplit && k >= ks) ? gbeta2[(((k - ks) * R) >> 1) + pr]
+                                                             : beta2[((k * R) >> 1) + pr];
                         al0[k] = __fsub_rn(lam[v0[k]], Msg<MsgT>::load(pair_lo<MsgT>(bb)));
                         al1[k] = __fsub_rn(lam[v1[k]], Msg<MsgT>::load(pair_hi<MsgT>(bb)));
                     }
@@ -254,7 +274,10 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                     check_update<MsgT, DC>(al1, (sw >> ((c & 31) + 1)) & 1u, f, o1);
                 }
                 #pragma unroll
-                for (int k = 0; k < DC; ++k) beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
+                for (int k = 0; k < DC; ++k) {
+                    if (kSplit && k >= ks) gbeta2[(((k - ks) * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
+                    else beta2[((k * R) >> 1) + pr] = make_pair(o0[k], o1[k]);
+                }
             }
             if (lot && early && lw) {
                 if constexpr (kTab) {
@@ -280,8 +303,15 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
                 float acc0 = mm.x, acc1 = mm.y;
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
-                    acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[e0[k]]));
-                    acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[e1[k]]));
+                    if (kSplit) {
+                        const MsgT m0 = e0[k] >= ksR ? gbeta[e0[k] - ksR] : beta[e0[k]];
+                        const MsgT m1 = e1[k] >= ksR ? gbeta[e1[k] - ksR] : beta[e1[k]];
+                        acc0 = __fadd_rn(acc0, Msg<MsgT>::load(m0));
+                        acc1 = __fadd_rn(acc1, Msg<MsgT>::load(m1));
+                    } else {
+                        acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[e0[k]]));
+                        acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[e1[k]]));
+                    }
                 }
                 lam2[q] = make_float2(acc0, acc1);
                 if (acc0 <= 0.0f || acc1 <= 0.0f) {

@@ -6,9 +6,9 @@
 
 namespace lbp {
 
-template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename GraphT>
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename GraphT, bool SP = false>
 int launch_graph_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, GraphT, kRule>;
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, GraphT, kRule, SP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -18,9 +18,10 @@ int launch_graph_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) 
     return LBP_OK;
 }
 
-template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t>
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename IdxT = uint16_t,
+          bool SP = false>
 int launch_ell_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    return launch_graph_one<MsgT, kRule, G, DC, DV, GS, SS, EllGraph<IdxT, DC, DV>>(s, a, st);
+    return launch_graph_one<MsgT, kRule, G, DC, DV, GS, SS, EllGraph<IdxT, DC, DV>, SP>(s, a, st);
 }
 
 // Implicit surface-code graph (Table III): no image; state in shared memory
@@ -67,6 +68,11 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
             return LBP_ENOSYS;
         }
         if (s.G == 512) return launch_ell_one<MsgT, kRule, 512, DC, DV, false, false, uint32_t>(s, a, st);
+        return LBP_ENOSYS;
+    }
+    if (s.split) {
+        // One shot per CTA: the shared part of a split state nearly fills it.
+        if (s.G == 1024) return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, true, uint16_t, true>(s, a, st);
         return LBP_ENOSYS;
     }
     if (s.state_smem) {

@@ -14,6 +14,7 @@ struct LaunchShape {
     bool graph_smem, state_smem, idx32;
     bool surface;            // implicit surface-code graph (no index image)
     bool round;              // round-periodic graph (one round's index image)
+    bool split;              // split state: ks message slots in shared memory, the rest in the workspace
 };
 
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);

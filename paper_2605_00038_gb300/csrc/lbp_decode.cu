@@ -53,6 +53,9 @@ int tuned_slot(int msg, int rule) {
 struct BpPlan {
     bool ell = false, graph_smem = true, state_smem = true, idx32 = false, surface = false, round = false;
     bool tab = false;            // index-image form with the bank-aware stride and pair table
+    bool split = false;          // split state: ks message slots in shared memory, the rest in the workspace
+    int ks = 0;
+    uint32_t gbeta_bytes = 0;    // per-group workspace slice of a split state's other slots
     int groups = 0, G = 0, grid = 0;
     uint32_t state_bytes = 0, off_beta = 0, off_lam = 0, off_s = 0, off_shat = 0, off_misc = 0;
     size_t smem = 0;
@@ -123,9 +126,9 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
     // Bounded-degree ELL kernel when the code has an ELL image that fits.
     // Message rows: R = Mp + 2 words, or the bank-aware stride of the
     // index-image form (always in shared memory) when the code has one.
-    auto state_layout = [&](int R) {
+    auto state_layout = [&](int R, int slots = 0) {
         uint32_t o = 0;
-        p.off_beta = o; o = align16u(o + static_cast<uint32_t>(msg_bytes(msg)) * c->ell.DC * R);
+        p.off_beta = o; o = align16u(o + static_cast<uint32_t>(msg_bytes(msg)) * (slots ? slots : c->ell.DC) * R);
         p.off_lam = o;  o = align16u(o + 4u * (c->ell.Np + 2));
         p.off_s = o;    o = align16u(o + 4u * W32);
         p.off_shat = o; o = align16u(o + 12u * W32);
@@ -198,6 +201,36 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
         // memory when one group's fits, else in the workspace.
         p.graph_smem = false;
         p.state_smem = off <= budget0;
+        if (!req_G && c->env_G) {
+            req_S = c->env_S;
+            req_G = c->env_G;
+        }
+        // Split state: when one shot's state does not fit, the largest number
+        // of message slots that fits stays in shared memory with the
+        // posteriors and syndrome words (one shot per CTA, 1024 threads), the
+        // other slots go to a per-group workspace slice.  An explicit request
+        // for 256 or 512 threads keeps the whole state in the workspace.
+        if (!p.state_smem && !p.idx32 && req_G != 256 && req_G != 512) {
+            for (int ks = c->ell.DC - 1; ks >= 1; --ks) {
+                const uint32_t o = state_layout(c->ell.Mp + 2, ks);
+                if (o <= budget0) {
+                    p.split = true;
+                    p.ks = ks;
+                    p.gbeta_bytes = static_cast<uint32_t>(
+                        align256(static_cast<size_t>(msg_bytes(msg)) * (c->ell.DC - ks) * (c->ell.Mp + 2)));
+                    p.state_smem = true;
+                    p.groups = 1;
+                    p.G = 1024;
+                    p.smem = o;
+                    const int64_t need = num_shots;
+                    p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
+                    if (p.grid < 1) p.grid = 1;
+                    *out = p;
+                    return LBP_OK;
+                }
+            }
+            off = state_layout(c->ell.Mp + 2);
+        }
         int G = 1024, S = 1;
         if (p.state_smem) {
             S = static_cast<int>(budget0 / off);
@@ -421,11 +454,13 @@ WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, con
     WsLayout w;
     size_t off = 0;
     w.counters = off; off = align256(off + 256);
-    if (bp && !bp->state_smem) {
+    if (bp && (!bp->state_smem || bp->split)) {
         // Sized for every launch shape (at most 1024 / 256 groups per CTA, one
-        // CTA per SM), so lbp_tune's candidates and any tuned shape fit.
+        // CTA per SM), so lbp_tune's candidates and any tuned shape fit; a
+        // split state needs the slice of its workspace slots per group.
         w.gstate = off;
-        off = align256(off + static_cast<size_t>(c->sm_count) * 4 * bp->state_bytes);
+        const size_t slice = bp->split ? bp->gbeta_bytes : bp->state_bytes;
+        off = align256(off + static_cast<size_t>(c->sm_count) * 4 * slice);
     }
     if (prm->osd) {
         w.osd_list = off; off = align256(off + 4ull * num_shots);
@@ -552,7 +587,9 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.llr = a.llr; e.counters = a.counters; e.osd_list = a.osd_list; e.osd_llr = a.osd_llr;
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
-        e.gstate = bp.state_smem ? nullptr : base + w.gstate;
+        e.gstate = (bp.state_smem && !bp.split) ? nullptr : base + w.gstate;
+        e.ks = bp.split ? bp.ks : 0;
+        e.gbeta_bytes = bp.gbeta_bytes;
         const int R = bp.tab ? c->tab_R : c->ell.Mp + 2;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(R) + 1);
         e.tab_R = bp.tab ? c->tab_R : 0;
@@ -565,7 +602,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             e.img.bytes = c->rnd.bytes;
         }
         const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32,
-                              bp.surface, bp.round};
+                              bp.surface, bp.round, bp.split};
         const bool sp = prm->rule == LBP_RULE_SUM_PRODUCT;
         switch (prm->msg) {
             case LBP_MSG_F32:

@@ -126,12 +126,31 @@ def test_precisions_on_d7_spacetime(msg):
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
 def test_c5_d25_spacetime_precisions(msg):
     """d=25, 25 rounds (7,800 x 23,113): the graph image exceeds shared memory,
-    so the kernel reads it from global memory; FP32 state lives in the
-    workspace, FP16 / INT8 state in shared memory."""
+    so the kernel reads it from global memory; FP32 state is split between
+    shared memory and the workspace, FP16 / INT8 state sits in shared memory."""
     w = workloads.c5_d25_spacetime(msg=msg, shots=300)
     _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
     kw = dict(w.decoder, seed=8)
     assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
+
+
+@pytest.mark.parametrize("policy", [0, 1, 4])
+def test_d25_split_state_equals_workspace_state(policy, monkeypatch):
+    """FP32 messages at d=25 do not fit shared memory beside the posteriors,
+    so by default the state is split: the first message slots stay in shared
+    memory, the rest go to the workspace.  Forcing the whole state into the
+    workspace (two 512-thread groups per CTA) must give the same bits, and
+    both must match the oracle."""
+    w = workloads.c5_d25_spacetime(msg=lbp.LBP_MSG_F32, shots=160)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed + policy, num_shots=w.shots)
+    kw = dict(w.decoder, max_iter=50, lottery_policy=policy, seed=11)
+    split = gpu_decode(w.h, w.priors, syn, **kw)
+    monkeypatch.setenv("LBP_BP_SHAPE", "2,512")
+    whole = gpu_decode(w.h, w.priors, syn, **kw)
+    for k in ("err", "conv", "iters", "osd"):
+        assert np.array_equal(split[k], whole[k]), k
+    assert np.array_equal(split["llr"].view(np.uint32), whole["llr"].view(np.uint32))
+    assert_parity(split, oracle_decode(w.h, w.priors, syn, **kw))
 
 
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
