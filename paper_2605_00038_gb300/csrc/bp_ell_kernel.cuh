@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
     // The bank-aware layout exists only for the index image staged in shared
     // memory; every other instantiation keeps R = Mp + 2 and no pair table.
     constexpr bool kTab = kGraphSmem && GraphT::kEll;
+    // Index image read from global memory: prefetch its words one trip ahead.
+    constexpr bool kPf = !kGraphSmem && GraphT::kEll;
     const int Mp = a.img.Mp, Np = a.img.Np, R = (kTab && a.tab_R > 0) ? a.tab_R : Mp + 2;
     const uint16_t *ptab =
         (kTab && a.off_ptab != 0u) ? reinterpret_cast<const uint16_t *>(smem + a.off_ptab) : nullptr;
@@ -243,12 +245,24 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             uint32_t u2pre = 0;
             LotteryPrep lp;          // index-image instantiations in shared memory only
             // ---- C2V, two adjacent checks per thread ---------------------------
+            // With the index image in global memory (L2), each trip's index
+            // words are loaded one trip ahead, so their latency overlaps the
+            // previous pair's work.
+            typename GraphT::IP pfc[DC];
+            if constexpr (kPf) {
+                if (t < mpairs) gr.cols2_raw(t, pfc);
+            }
             for (int ip = t; ip < mpairs; ip += G) {
                 const int pr = (kTab && ptab) ? static_cast<int>(ptab[ip]) : ip;
                 const int c = 2 * pr;
                 float al0[DC], al1[DC];
                 uint32_t v0[DC], v1[DC];
-                gr.cols2(pr, v0, v1);
+                if constexpr (kPf) {
+                    GraphT::template unpack<DC>(pfc, v0, v1);
+                    if (ip + G < mpairs) gr.cols2_raw(ip + G, pfc);
+                } else {
+                    gr.cols2(pr, v0, v1);
+                }
                 if (it == 0) {
                     #pragma unroll
                     for (int k = 0; k < DC; ++k) {
@@ -296,10 +310,28 @@ __global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
             group_sync<G>(bar);
             // ---- LLR update, hard decision, syndrome scatter: column pairs ------
             uint32_t *sh_cur = shat + cur * W32;
+            typename GraphT::IP pfe[DV];
+            float2 pfm = make_float2(0.0f, 0.0f);
+            if constexpr (kPf) {
+                if (t < npairs) {
+                    gr.ents2_raw(t, pfe);
+                    pfm = gr.mu2_ldg(t);
+                }
+            }
             for (int q = t; q < npairs; q += G) {
                 uint32_t e0[DV], e1[DV];
-                gr.ents2(q, e0, e1);
-                const float2 mm = gr.mu2(q);
+                float2 mm;
+                if constexpr (kPf) {
+                    GraphT::template unpack<DV>(pfe, e0, e1);
+                    mm = pfm;
+                    if (q + G < npairs) {
+                        gr.ents2_raw(q + G, pfe);
+                        pfm = gr.mu2_ldg(q + G);
+                    }
+                } else {
+                    gr.ents2(q, e0, e1);
+                    mm = gr.mu2(q);
+                }
                 float acc0 = mm.x, acc1 = mm.y;
                 #pragma unroll
                 for (int k = 0; k < DV; ++k) {

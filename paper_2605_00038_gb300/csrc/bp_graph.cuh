@@ -90,6 +90,26 @@ struct EllGraph {
             y[k] = Idx<IdxT>::hi(e);
         }
     }
+    // Prefetch form for an image in global memory: the raw paired index words
+    // of checks 2 pr, 2 pr + 1 (columns 2 q, 2 q + 1), loaded through the
+    // read-only path one loop trip ahead of their use, and their unpacking.
+    __device__ __forceinline__ void cols2_raw(int pr, IP (&w)[DC]) const {
+        #pragma unroll
+        for (int k = 0; k < DC; ++k) w[k] = __ldg(cidx2 + k * mpairs + pr);
+    }
+    __device__ __forceinline__ void ents2_raw(int q, IP (&w)[DV]) const {
+        #pragma unroll
+        for (int k = 0; k < DV; ++k) w[k] = __ldg(vent2 + k * npairs + q);
+    }
+    __device__ __forceinline__ float2 mu2_ldg(int q) const { return __ldg(mu2_ + q); }
+    template <int N>
+    static __device__ __forceinline__ void unpack(const IP (&w)[N], uint32_t (&x)[N], uint32_t (&y)[N]) {
+        #pragma unroll
+        for (int k = 0; k < N; ++k) {
+            x[k] = Idx<IdxT>::lo(w[k]);
+            y[k] = Idx<IdxT>::hi(w[k]);
+        }
+    }
     __device__ __forceinline__ uint32_t col(int k, int c) const { return cidx[k * Mp + c]; }
     __device__ __forceinline__ uint32_t ent(int k, int v) const { return vent[k * Np + v]; }
     __device__ __forceinline__ uint32_t orig(uint32_t v) const { return v; }
@@ -100,6 +120,7 @@ struct EllGraph {
 template <int DC, int DV>
 struct SurfaceGraph {
     static_assert(DC == 6 && DV == 2, "surface-code space-time matrices have DC = 6, DV = 2");
+    using IP = uint32_t;     // no index words to prefetch
     static constexpr bool kImage = false;
     static constexpr bool kEll = false;
     SurfaceDesc s;
@@ -222,6 +243,7 @@ struct SurfaceGraph {
 template <int DC, int DV>
 struct RoundGraph {
     static_assert(DV >= 2, "a measurement column has two checks");
+    using IP = uint32_t;     // no index words to prefetch
     static constexpr bool kImage = true;     // the round image is staged like an index image
     static constexpr bool kEll = false;
     RoundDesc r;
