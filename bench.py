@@ -1,18 +1,24 @@
 #!/usr/bin/env python3
-"""Throughput benchmark of the Lottery BP + OSD-0 decoder on GB300.
+"""Throughput benchmark of the Lottery BP decoder on GB300.
 
 One step = one pass of the whole decoding path (BP with the lottery on every
-shot, OSD-0 on the shots BP leaves unconverged) over one batch of seeded
-synthetic syndromes of the rotated d=11 surface code with 11 noisy rounds
-(space-time H 660 x 1931, nnz 3620), p_data = p_meas = 0.003, 10^6 shots,
-max 100 iterations, binary32 messages.
+shot, early termination, hard decisions; this workload runs without OSD, as
+configured) over one batch of seeded synthetic syndromes of the rotated d=25
+surface code with 25 noisy rounds (space-time H 7,800 x 23,113, nnz 44,976),
+p_data = p_meas = 0.004, max 100 iterations, binary32 messages.  A step
+decodes 2^18 shots; four rotating batches of 2^18 make up the 2^20 shots of
+the configuration (each 258 MB of syndromes, larger than L2).
 
 Prints one JSON line (rank 0).  `value` is decoded shots per second over all
 ranks with inputs resident in HBM; `e2e` is the same through the host-buffer
-entry point with the copies inside the timed region.  `--impl reference`
-times the CPU oracle instead (on a bounded sample of the same workload).
-Under torchrun each rank decodes its own shots (weak scaling; no data-path
-collective).
+entry point with the copies inside the timed region.  Further legs (rank 0,
+N = 1): the precision sweep of this workload (FP16 / INT8 messages, logical
+error rates against the FP64 oracle), the rotated d=11 space-time workload
+with Lottery BP + OSD-0, the BB [[144,12,12]] code with FP16 messages and
+OSD-0, serving, matched LER, the lottery design space and the check-node
+rule.  `--impl reference` times the CPU oracle instead (on a bounded sample
+of the same workload).  Under torchrun each rank decodes its own shots (weak
+scaling; no data-path collective).
 """
 from __future__ import annotations
 
@@ -33,7 +39,7 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "decoded shots/sec and p99 decode latency at matched logical error rate; HBM GB/s"
 UNIT = "shots/s"
-N_BATCHES = 3        # rotating input batches: 3 x 88 MB of syndromes > 129 MB L2
+N_BATCHES = 4        # rotating input batches of 2^18 shots: 4 x 258 MB of syndromes, each > 129 MB L2
 
 
 def parse():
@@ -42,10 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--shots", type=int, default=1_000_000, help="shots per step per rank")
+    ap.add_argument("--shots", type=int, default=1 << 18, help="shots per step per rank")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
-    ap.add_argument("--cpu-sample", type=int, default=20_000, help="oracle shots for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=6144, help="oracle shots for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=192, help="oracle shots per step of --impl reference")
     ap.add_argument("--no-tune", action="store_true", help="skip lbp_tune (default launch shape)")
     ap.add_argument("--serving-only", action="store_true", help="print the serving and matched-LER results only")
     return ap.parse_args()
@@ -132,7 +139,20 @@ def job_value(world: int, shots: int, steps: int, elapsed_ms_per_rank, dist=None
 
 def workload(shots):
     from paper_2605_00038_gb300.inputs import workloads
-    return workloads.c2_d11_spacetime(shots=shots, osd=1)
+    return workloads.c5_d25_spacetime(msg=0, shots=shots)
+
+
+def state_bytes_per_iteration(h, msg_bytes):
+    """Algorithmic bytes of one shot-iteration: the state that persists between
+    iterations, read and written once: E messages of msg_bytes and n binary32
+    posteriors, B_it = 2 (E b + 4 n)."""
+    return 2 * (h.nnz * msg_bytes + 4 * h.n)
+
+
+def io_bytes_per_shot(h):
+    """Per shot: syndrome in, estimate out (packed 64-bit words), the
+    converged flag, the OSD status byte and the iteration count."""
+    return 8 * ((h.m + 63) // 64) + 8 * ((h.n + 63) // 64) + 1 + 1 + 4
 
 
 def roofline_model(w, iters_total, shots):
@@ -142,20 +162,22 @@ def roofline_model(w, iters_total, shots):
     per column the hard decision); per shot the syndrome in and results out."""
     E, m, n = w.h.nnz, w.h.m, w.h.n
     ops = float(iters_total) * (8 * E + 2 * m + n)
-    io = shots * (8 * ((m + 63) // 64) + 8 * ((n + 63) // 64) + 1 + 1 + 4)
+    io = shots * io_bytes_per_shot(w.h)
     return ops, io
 
 
-# DRAM bytes per shot of K_bp on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture, 131,072 shots, scaled per shot),
-# valid for the kernel sources whose hash is recorded with it.
-KBP_TRAFFIC = {"bytes_per_shot": 1135.5, "source_sha1": "e49ad615ca0e"}
+# DRAM bytes of K_bp per shot-iteration on the d=25 workload (FP32 messages):
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
+# 4,096-shot launch, divided by the shot-iterations it ran; the traffic of a
+# full launch scales with its shot-iterations.  Valid for the kernel sources
+# whose hash is recorded with it (None until captured).
+KBP_TRAFFIC = {"bytes_per_shot_iteration": None, "source_sha1": None}
 
 
 def kbp_source_sha1():
     import hashlib
     h = hashlib.sha1()
-    for f in ("bp_ell_kernel.cuh", "bp_common.cuh", "bp_graph.cuh"):
+    for f in ("bp_ell_kernel.cuh", "bp_common.cuh", "bp_graph.cuh", "bp_lottery.cuh"):
         h.update((ROOT / "paper_2605_00038_gb300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:12]
 
@@ -165,7 +187,44 @@ def alu_peak_ops(sm_mhz):
     return 152 * 4 * 32 * sm_mhz * 1e6
 
 
+def hbm_peak_gbs():
+    """(peak GB/s, basis): the measured copy bandwidth of the GB300s
+    when MEASURED_PEAKS.json is present, else the recipe's fallback."""
+    f = ROOT / "MEASURED_PEAKS.json"
+    try:
+        v = float(json.loads(f.read_text())["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def histogram(iters_tensors):
+    """Iteration histogram (Fig. 6) over the given per-shot iteration counts:
+    {iterations: shots}, non-zero entries only."""
+    import torch
+    tot = None
+    for t in iters_tensors:
+        c = torch.bincount(t.to(torch.int64))
+        if tot is None:
+            tot = c
+        else:
+            if c.numel() > tot.numel():
+                c, tot = tot, c
+            tot[: c.numel()] += c
+    nz = torch.nonzero(tot).flatten().tolist()
+    vals = tot[nz].tolist()
+    return {str(k): int(v) for k, v in zip(nz, vals)}
+
+
 # ------------------------------------------------------------- reference arm
+
+def oracle_params_for(w, oracle, prec=None):
+    d = w.decoder
+    return oracle.OracleParams(max_iter=d["max_iter"], scale_mode=d.get("scale_mode", 1),
+                               scale_const=d.get("scale_const", 0.625), lottery=bool(d.get("lottery", 1)),
+                               lottery_skip=d.get("lottery_skip", 6), osd=bool(d.get("osd", 0)),
+                               prec=oracle.PREC_F64 if prec is None else prec, seed=w.seed)
+
 
 def run_reference(args):
     world, rank, _ = dist_setup()
@@ -175,16 +234,15 @@ def run_reference(args):
     from paper_2605_00038_gb300.inputs import sampler
     w = workload(args.shots)
     cores = os.cpu_count() or 1
-    sample = max(1, min(args.cpu_sample, w.shots))
-    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=sample)
+    sample = max(1, min(args.ref_sample, w.shots))
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=sample * (args.steps + 1))
     S = sampler.unpack(syn, w.h.m)
-    prm = oracle.OracleParams(max_iter=100, lottery=True, lottery_skip=6, osd=True,
-                              prec=oracle.PREC_F64, seed=w.seed)
+    prm = oracle_params_for(w, oracle)
     for _ in range(args.warmup):
-        oracle.decode(w.h, w.priors, S[: max(1, sample // 20)], prm, nthreads=cores)
+        oracle.decode(w.h, w.priors, S[: max(1, sample // 8)], prm, nthreads=cores)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.decode(w.h, w.priors, S, prm, nthreads=cores)
+    for k in range(args.steps):
+        oracle.decode(w.h, w.priors, S[k * sample:(k + 1) * sample], prm, nthreads=cores)
     dt = time.perf_counter() - t0
     v = sample * args.steps / dt
     line = {
@@ -192,10 +250,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "shots_per_step": sample, "decoder": "lottery_bp+osd0",
-                   "max_iter": 100, "parallelism": "cpu threads"},
+        "config": {"workload": w.name, "shots_per_step": sample, "decoder": "lottery_bp",
+                   "max_iter": w.decoder["max_iter"], "parallelism": "cpu threads"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d shots of %s per step (FP64 oracle, %d threads)"
+                         "sample": "%d distinct shots of %s per step (FP64 oracle, %d threads)"
                                    % (sample, w.name, cores)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -203,28 +261,6 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-
-def logical_failures(w, err_words, est_words, conv, osd):
-    """Logical failure per shot: the residual's data part, summed over rounds,
-    hits a logical operator; or BP did not converge and OSD did not apply."""
-    import torch
-    from paper_2605_00038_gb300.inputs.codes import logical_operators, rotated_surface
-    hz, hx = rotated_surface(11)
-    L = torch.from_numpy(logical_operators(hz, hx).astype(np.float32)).cuda()
-    T, nq = 11, hz.n
-    fails = 0
-    B = err_words.shape[0]
-    shifts = torch.arange(64, device="cuda", dtype=torch.int64)
-    for lo in range(0, B, 50_000):
-        r = torch.bitwise_xor(err_words[lo:lo + 50_000], est_words[lo:lo + 50_000])
-        bits = torch.bitwise_and(torch.bitwise_right_shift(r.unsqueeze(-1), shifts), 1)
-        bits = bits.reshape(r.shape[0], -1)[:, : w.h.n]
-        data = bits[:, : T * nq].reshape(-1, T, nq).sum(1).remainder(2).float()
-        hit = (data @ L.T).remainder(2).sum(1) > 0
-        bad = (conv[lo:lo + 50_000] == 0) & (osd[lo:lo + 50_000] != 1)
-        fails += int((hit | bad).sum().item())
-    return fails
-
 
 def run_gpu(args):
     import torch
@@ -236,7 +272,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2605_00038_gb300 import lbp
+    from paper_2605_00038_gb300 import evaluate, lbp
     from paper_2605_00038_gb300.decoder import Decoder
     from paper_2605_00038_gb300.inputs import sampler
 
@@ -258,19 +294,19 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step(k):
-        lbp.lbp_decode(dec.code, prms[k % N_BATCHES], B, syn_d[k % N_BATCHES], outs[k % N_BATCHES].err,
-                       outs[k % N_BATCHES].converged, outs[k % N_BATCHES].osd,
-                       outs[k % N_BATCHES].iters, None, ws, stream)
+        o = outs[k % N_BATCHES]
+        lbp.lbp_decode(dec.code, prms[k % N_BATCHES], B, syn_d[k % N_BATCHES], o.err, o.converged, o.osd,
+                       o.iters, None, ws, stream)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # Launch-shape autotuning on the first batch (outside the timed region).
+    # Launch-shape autotuning on part of the first batch (outside the timed region).
     launch = None
     if not args.no_tune:
-        tb = min(B, 131072)
+        tb = min(B, 16384)
         dec.tune(syn_d[0][:tb].contiguous(), prms[0], stream)
         S_t, G_t, gf_t = lbp.lbp_code_tuned(dec.code, prms[0].msg, prms[0].rule)
         launch = {"groups_per_cta": S_t, "threads_per_shot": G_t,
@@ -294,55 +330,61 @@ def run_gpu(args):
     lbp.lbp_timing_enable(False)
     max_ms, value = job_value(world, B, args.steps, elapsed_ms, dist)
 
-    # Work actually done in the timed steps (iterations, OSD invocations).
+    # Work actually done in the timed steps (iterations per batch decoded).
     iters_total = 0
-    osd_total = 0
+    unconverged = 0
     for k in range(args.steps):
         o = outs[k % N_BATCHES]
         iters_total += int(o.iters.sum().item())
-        osd_total += int((o.osd != 0).sum().item())
+        unconverged += int((o.converged == 0).sum().item())
+    hist = histogram([outs[k].iters for k in range(min(args.steps, N_BATCHES))])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "code": "rotated surface d=11, 11 rounds, H_st 660x1931 nnz 3620",
-                   "noise": "iid p_data=p_meas=0.003", "shots_per_step_per_rank": B,
-                   "decoder": "lottery_bp(skip 6, adaptive scale, I=100) + osd0",
-                   "msg": "f32", "l2": "3 rotating input batches (%d MB syndromes) > L2" % (
-                       N_BATCHES * B * wm * 8 // 2 ** 20),
+        "config": {"workload": w.name,
+                   "code": "rotated surface d=25, 25 noisy rounds, space-time H %dx%d nnz %d"
+                           % (w.h.m, w.h.n, w.h.nnz),
+                   "noise": "iid p_data=p_meas=0.004", "shots_per_step_per_rank": B,
+                   "configuration_shots": N_BATCHES * B,
+                   "decoder": "lottery_bp(proposed rule, skip 6, adaptive scale, I=100), no OSD",
+                   "msg": "f32",
+                   "l2": "%d rotating input batches of %d MB syndromes, each > L2" % (
+                       N_BATCHES, B * wm * 8 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single"},
         "clocks": clocks.summary(),
         "gpu_launches": int(bp_n + osd_n),
     }
     sm_mhz = line["clocks"]["sm_mhz"] or 2070.0
-    ops, io = roofline_model(w, iters_total / args.steps, B)
+    iters_per_step = iters_total / args.steps
     bp_avg_s = bp_ms / max(bp_n, 1) / 1e3
-    peak = alu_peak_ops(sm_mhz)
-    traffic = (KBP_TRAFFIC["bytes_per_shot"] * B
-               if kbp_source_sha1() == KBP_TRAFFIC["source_sha1"] else None)
-    # Shared-memory view: per shot-iteration the state the algorithm must move
-    # (read lambda and beta, write beta on each edge; read beta per edge and
-    # write lambda per column), E (4 + 3b) + 8 n bytes, against
-    # 152 SMs x 128 B/clock.
-    E, n = w.h.nnz, w.h.n
-    smem_bytes = (iters_total / args.steps) * (E * (4 + 3 * 4) + 8 * n)
-    smem_peak = 152 * 128 * sm_mhz * 1e6
-    line["roofline"] = {"bound": "alu", "achieved": ops / bp_avg_s / 1e12, "peak": peak / 1e12,
-                        "unit": "Tops/s", "frac": (ops / bp_avg_s) / peak, "traffic": traffic,
-                        "kernel": "bp_ell_kernel", "avg_launch_ms": bp_avg_s * 1e3,
-                        "ops_per_launch": ops, "io_bytes_per_launch": io,
-                        "dram_gbs_from_traffic": (traffic / bp_avg_s / 1e9) if traffic else None,
-                        "peak_basis": "152 SMs x 128 lanes x median SM clock %.0f MHz (derived)" % sm_mhz,
-                        "smem": {"achieved_tbs": smem_bytes / bp_avg_s / 1e12,
-                                 "peak_tbs": smem_peak / 1e12,
-                                 "frac": smem_bytes / bp_avg_s / smem_peak,
-                                 "note": "per ncu: shared-memory pipe 85% busy and instruction issue "
-                                         "77%; 30% of load wavefronts bank conflicts"}}
+    b_it = state_bytes_per_iteration(w.h, 4)
+    alg_bytes = iters_per_step * b_it + B * io_bytes_per_shot(w.h)
+    peak_gbs, peak_basis = hbm_peak_gbs()
+    traffic = None
+    if KBP_TRAFFIC["bytes_per_shot_iteration"] and kbp_source_sha1() == KBP_TRAFFIC["source_sha1"]:
+        traffic = KBP_TRAFFIC["bytes_per_shot_iteration"] * iters_per_step
+    ops, _ = roofline_model(w, iters_per_step, B)
+    line["roofline"] = {
+        "bound": "hbm", "achieved": alg_bytes / bp_avg_s / 1e9, "peak": peak_gbs, "unit": "GB/s",
+        "frac": alg_bytes / bp_avg_s / 1e9 / peak_gbs, "traffic": traffic,
+        "kernel": "bp_ell_kernel", "avg_launch_ms": bp_avg_s * 1e3,
+        "bytes_per_shot_iteration": b_it, "shot_iterations_per_launch": iters_per_step,
+        "algorithmic_bytes_per_launch": alg_bytes, "peak_basis": peak_basis,
+        "dram_gbs_from_traffic": (traffic / bp_avg_s / 1e9) if traffic else None,
+        "note": "algorithmic bytes = state read and written once per shot-iteration, 2 (E 4 + 4 n), "
+                "plus I/O; the posteriors, syndrome words and four of six message slots stay in "
+                "shared memory, the other two slots in an L2-resident workspace slice, so DRAM "
+                "carries far less than the algorithmic bytes (traffic)",
+        "alu": {"achieved_tops": ops / bp_avg_s / 1e12, "peak_tops": alu_peak_ops(sm_mhz) / 1e12,
+                "frac": ops / bp_avg_s / alu_peak_ops(sm_mhz),
+                "peak_basis": "152 SMs x 128 lanes x median SM clock %.0f MHz (derived)" % sm_mhz}}
     line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps,
                        "osd_ms_per_step": osd_ms / args.steps,
                        "mean_iters": iters_total / (B * args.steps),
-                       "osd_invoke_rate": osd_total / (B * args.steps)}
+                       "unconverged_rate": unconverged / (B * args.steps),
+                       "iteration_histogram": hist}
 
     # End to end through the host-buffer entry point (pinned memory).
     if not args.no_e2e:
@@ -374,89 +416,332 @@ def run_gpu(args):
                        "d2h_bytes_per_step": B * (wn * 8 + 1 + 1 + 4)}
 
     if not args.no_extras and rank == 0:
-        # Per-batch latency at small batch sizes (outside the timed region):
-        # each repeat decodes different shots of batch 0, so the quantiles are
-        # over the workload's shots (converged and OSD-bound alike), not over
-        # timing jitter of one batch.
-        lat = {}
-        for bs, reps in ((1, 210), (64, 210), (4096, 60)):
-            o = dec.alloc(bs)
-            wsb = dec.workspace(prms[0], bs)
-            times = []
-            for r in range(reps):
-                lo = (r * bs) % max(1, B - bs + 1)
-                sub = syn_d[0][lo:lo + bs].contiguous()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                lbp.lbp_decode(dec.code, prms[0], bs, sub, o.err, o.converged, o.osd, o.iters, None,
-                               wsb, stream)
-                b.record(stream)
-                b.synchronize()
-                if r >= 10:
-                    times.append(a.elapsed_time(b))
-            times.sort()
-            lat["batch_%d" % bs] = {"p50_ms": times[len(times) // 2],
-                                    "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
-                                    "samples": len(times)}
-        # Batch 1 replayed from a CUDA graph (lbp_graph_*): the same decode
-        # without the per-call cost of issuing its stream operations.  Each
-        # repeat first writes a different shot into the captured buffer.
-        x1 = torch.empty((1, wm), dtype=torch.int64, device=syn_d[0].device)
-        o1 = dec.alloc(1)
-        ws1 = torch.empty(lbp.lbp_workspace_size(dec.code, prms[0], 1) + 256, dtype=torch.uint8,
-                          device=syn_d[0].device)
-        ws1 = ws1[(-ws1.data_ptr()) % 256:]
-        g1 = lbp.lbp_graph_create(dec.code, prms[0], 1, x1, o1.err, o1.converged, o1.osd, o1.iters, None,
-                                  ws1)
-        times = []
-        for r in range(210):
-            x1.copy_(syn_d[0][r:r + 1])
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            lbp.lbp_graph_launch(g1, stream)
-            b.record(stream)
-            b.synchronize()
-            if r >= 10:
-                times.append(a.elapsed_time(b))
-        g1.close()
-        times.sort()
-        lat["batch_1_graph"] = {"p50_ms": times[len(times) // 2],
-                                "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
-                                "samples": len(times)}
-        lat["batch_%d" % B] = {"p50_ms": line["ms_per_step"], "p99_ms": None}
-        line["latency"] = lat
+        # Per-batch latency (outside the timed region): each repeat decodes
+        # different shots of batch 0.
+        line["latency"] = latency_sweep(dec, prms[0], syn_d[0], ((1, 30), (64, 12), (4096, 5)), stream)
+        line["latency"]["batch_%d" % B] = {"p50_ms": line["ms_per_step"], "p99_ms": None}
         # Logical error rate of batch 0 (true errors known from the sampler).
         o = outs[0]
         step(0)
         torch.cuda.synchronize()
-        fails = logical_failures(w, torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err,
-                                 o.converged, o.osd)
-        line["quality"] = {"ler": fails / B, "shots": B, "logical_failures": fails}
+        spec = evaluate.surface_spec(25, 25, w.h.n)
+        f = evaluate.logical_failures(spec, torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err,
+                                      o.converged, o.osd)
+        k = int(f.sum().item())
+        line["quality"] = {"ler": k / B, "ler_ci95": evaluate.wilson(k, B), "shots": B, "logical_failures": k,
+                           "note": "BP alone (no OSD in this configuration): an unconverged shot counts as a "
+                                   "logical failure"}
 
     if not args.no_extras and rank == 0 and world == 1:
+        del outs, ws
+        dec.close()
+        torch.cuda.empty_cache()
+        line["precision_d25"] = run_c5_precision(syn_h[0], err_h[0], args)
+        line["d11_spacetime_osd"] = run_c2_leg(args)
+        line["bb144_osd_fp16"] = run_c3_leg()
         line["serving"] = run_serving()
         line["serving_one_launch_fifo"] = run_serving(policy=(0, False))
         line["matched_ler"] = run_matched()
-        line["precision"] = run_precision()
+        line["precision_d7"] = run_precision()
         line["lottery_design_space"] = run_policies()
         line["check_rule"] = run_sum_product()
+    else:
+        dec.close()
     if not args.no_extras and rank == 0 and world == 1:
         import oracle
         cores = os.cpu_count() or 1
         S = sampler.unpack(syn_h[0][: args.cpu_sample], w.h.m)
-        prm = oracle.OracleParams(max_iter=100, lottery=True, lottery_skip=6, osd=True,
-                                  prec=oracle.PREC_F64, seed=w.seed, shot_offset=0)
         t0 = time.perf_counter()
-        oracle.decode(w.h, w.priors, S, prm, nthreads=cores)
+        oracle.decode(w.h, w.priors, S, oracle_params_for(w, oracle), nthreads=cores)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": S.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%d shots of %s (FP64 oracle, %d threads, %.1f s)"
                                           % (S.shape[0], w.name, cores, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    dec.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def latency_sweep(dec, prm, syn_d, sizes, stream):
+    """Per-batch latency quantiles (CUDA events around lbp_decode), each repeat
+    on different shots of syn_d; the first two repeats are warm-up."""
+    import torch
+    from paper_2605_00038_gb300 import lbp
+    lat = {}
+    B = syn_d.shape[0]
+    for bs, reps in sizes:
+        o = dec.alloc(bs)
+        wsb = dec.workspace(prm, bs)
+        times = []
+        for r in range(reps + 2):
+            lo = (r * bs) % max(1, B - bs + 1)
+            sub = syn_d[lo:lo + bs].contiguous()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lbp.lbp_decode(dec.code, prm, bs, sub, o.err, o.converged, o.osd, o.iters, None, wsb, stream)
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                times.append(a.elapsed_time(b))
+        times.sort()
+        lat["batch_%d" % bs] = {"p50_ms": times[len(times) // 2],
+                                "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                                "samples": len(times)}
+    return lat
+
+
+def run_c5_precision(syn0, err0, args, timed_shots: int = 1 << 18, oracle_shots: int = 4096):
+    """Precision sweep of the d=25 workload (BASELINE's fifth configuration):
+    FP32 / FP16 / INT8 messages on the same shots, each timed on one batch of
+    2^18 shots (tuned launch shape), with its logical error rate (BP alone, an
+    unconverged shot fails) and the paired comparison with the FP64 oracle on
+    the first `oracle_shots` shots.  Then the same decoder on the unrotated
+    d=25 space-time code (Table III, 15,000 x 44,425) at the same noise, where
+    BP converges far more often: the rotated code's weight-2 boundary checks
+    make degenerate pairs that stall BP (shown at d=11 too)."""
+    import torch
+    import oracle
+    from paper_2605_00038_gb300 import evaluate
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+    from paper_2605_00038_gb300.inputs.codes import spacetime, spacetime_priors, unrotated_surface
+
+    w = workloads.c5_d25_spacetime(msg=0, shots=timed_shots)
+    spec = evaluate.surface_spec(25, 25, w.h.n)
+    x = torch.from_numpy(syn0[:timed_shots].view(np.int64)).cuda()
+    true_d = torch.from_numpy(err0[:timed_shots].view(np.int64)).cuda()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.decode(w.h, w.priors, sampler.unpack(syn0[:oracle_shots], w.h.m),
+                      oracle_params_for(w, oracle), nthreads=cores)
+    t_or = time.perf_counter() - t0
+    fo = evaluate.logical_failures(spec, true_d[:oracle_shots].cpu(),
+                                   torch.from_numpy(sampler.pack(r.err).view(np.int64)),
+                                   torch.from_numpy(r.converged), torch.from_numpy(r.osd_used)).numpy()
+    ko = int(fo.sum())
+    out = {"workload": w.name, "timed_shots": timed_shots, "oracle_shots": oracle_shots,
+           "fp64_oracle": {"ler": ko / oracle_shots, "ler_ci95": evaluate.wilson(ko, oracle_shots),
+                           "unconverged_rate": float(1.0 - r.converged.mean()),
+                           "seconds": t_or, "threads": cores}}
+    dec = Decoder(w.h, w.priors)
+    for msg, name in ((0, "fp32"), (1, "fp16"), (2, "int8")):
+        prm = dec.params(**dict(w.decoder, msg=msg), seed=w.seed)
+        dec.tune(x[:16384].contiguous(), prm)
+        dec.decode(x[:4096].contiguous(), prm)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        res = dec.decode(x, prm)
+        a1.record()
+        torch.cuda.synchronize()
+        t = a0.elapsed_time(a1) / 1e3
+        it = float(res.iters.float().mean().item())
+        f = evaluate.logical_failures(spec, true_d, res.err, res.converged, res.osd).cpu().numpy()
+        k = int(f.sum())
+        fs = f[:oracle_shots]
+        S_t, G_t, gf_t = lbp_tuned(dec, prm)
+        out[name] = {"shots_per_s": timed_shots / t, "mean_iters": it,
+                     "unconverged_rate": float((res.converged == 0).float().mean().item()),
+                     "state_bytes_per_shot_iteration": state_bytes_per_iteration(w.h, {0: 4, 1: 2, 2: 1}[msg]),
+                     "launch": {"groups_per_cta": S_t, "threads_per_shot": G_t, "graph": gf_t},
+                     "ler": k / timed_shots, "ler_ci95": evaluate.wilson(k, timed_shots),
+                     "ler_subset": float(fs.mean()), "gap_vs_fp64_subset": float(fs.mean() - fo.mean()),
+                     "mcnemar_p_vs_fp64": evaluate.mcnemar_p(int((fs & ~fo).sum()), int((fo & ~fs).sum()))}
+    dec.close()
+    # The paper's own family (Table III): unrotated d=25, 25 rounds, same noise.
+    _, hz = unrotated_surface(25)
+    st = spacetime(hz, 25)
+    pri = spacetime_priors(hz, 25, 0.004, 0.004)
+    n_u = 1 << 14
+    _, su = sampler.sample(st, pri, seed=w.seed, num_shots=n_u)
+    xu = torch.from_numpy(su.view(np.int64)).cuda()
+    du = Decoder(st, pri)
+    unrot = {"shape": [st.m, st.n, st.nnz], "shots": n_u}
+    for I in (100, 300):
+        for lot in (0, 1):
+            prm = du.params(max_iter=I, lottery=lot, osd=0, msg=0, seed=w.seed)
+            res = du.decode(xu, prm)
+            torch.cuda.synchronize()
+            unrot["%s_I%d" % ("lottery" if lot else "plain", I)] = {
+                "unconverged_rate": float((res.converged == 0).float().mean().item()),
+                "mean_iters": float(res.iters.float().mean().item())}
+    du.close()
+    out["unrotated_d25_st25_p0.004"] = unrot
+    return out
+
+
+def lbp_tuned(dec, prm):
+    from paper_2605_00038_gb300 import lbp
+    return lbp.lbp_code_tuned(dec.code, prm.msg, prm.rule)
+
+
+def run_c2_leg(args, shots: int = 1_000_000, steps: int = 5, warmup: int = 3):
+    """The rotated d=11 space-time workload (BASELINE's second configuration):
+    Lottery BP + OSD-0, FP32 messages, 10^6 shots per step, three rotating
+    batches (88 MB of syndromes each), tuned launch shape; shots/s device
+    resident and end to end, kernel times, OSD invoke rate, iteration
+    histogram, small-batch latency, logical error rate."""
+    import torch
+    from paper_2605_00038_gb300 import evaluate, lbp
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+
+    w = workloads.c2_d11_spacetime(shots=shots, osd=1)
+    B = w.shots
+    nb = 3
+    dec = Decoder(w.h, w.priors)
+    wm, wn = (w.h.m + 63) // 64, (w.h.n + 63) // 64
+    syn_h, err_h, syn_d, prms = [], [], [], []
+    for k in range(nb):
+        e, s = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=B, shot_offset=k * B)
+        err_h.append(e)
+        syn_h.append(s)
+        syn_d.append(torch.from_numpy(s.view(np.int64)).cuda())
+        prms.append(dec.params(**w.decoder, seed=w.seed, shot_offset=k * B))
+    outs = [dec.alloc(B) for _ in range(nb)]
+    ws = dec.workspace(prms[0], B)
+    stream = torch.cuda.current_stream()
+    dec.tune(syn_d[0][:131072].contiguous(), prms[0], stream)
+
+    def step(k):
+        o = outs[k % nb]
+        lbp.lbp_decode(dec.code, prms[k % nb], B, syn_d[k % nb], o.err, o.converged, o.osd, o.iters, None, ws,
+                       stream)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    lbp.lbp_timing_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bp_ms, bp_n, osd_ms, osd_n = lbp.lbp_timing_read()
+    lbp.lbp_timing_enable(False)
+    t = e0.elapsed_time(e1) / 1e3
+    iters = sum(int(outs[k % nb].iters.sum().item()) for k in range(steps))
+    osd_total = sum(int((outs[k % nb].osd != 0).sum().item()) for k in range(steps))
+    S_t, G_t, gf_t = lbp_tuned(dec, prms[0])
+    out = {"workload": w.name, "shots_per_step": B, "steps": steps, "shots_per_s": B * steps / t,
+           "ms_per_step": 1e3 * t / steps, "bp_ms_per_step": bp_ms / steps, "osd_ms_per_step": osd_ms / steps,
+           "bp_launch": {"groups_per_cta": S_t, "threads_per_shot": G_t, "graph": gf_t},
+           "mean_iters": iters / (B * steps), "osd_invoke_rate": osd_total / (B * steps),
+           "iteration_histogram": histogram([outs[k].iters for k in range(nb)])}
+    # ALU and shared-memory views of K_bp (the state stays in shared memory).
+    ops, _ = roofline_model(w, iters / steps, B)
+    bp_avg_s = bp_ms / max(bp_n, 1) / 1e3
+    out["roofline_alu"] = {"achieved_tops": ops / bp_avg_s / 1e12, "frac": ops / bp_avg_s / alu_peak_ops(2070.0),
+                           "algorithmic_state_tbs": (iters / steps) * state_bytes_per_iteration(w.h, 4)
+                                                    / bp_avg_s / 1e12}
+    # End to end through the host-buffer entry point.
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+    hsyn = pin(syn_h[0].shape, torch.int64)
+    hsyn.numpy()[:] = syn_h[0].view(np.int64)
+    ho = dict(err=pin((B, wn), torch.int64), converged=pin(B, torch.uint8), osd=pin(B, torch.uint8),
+              iters=pin(B, torch.int32))
+    hws = dec.workspace(prms[0], B, host=True)
+    lbp.lbp_decode_host(dec.code, prms[0], B, hsyn, ho["err"], ho["converged"], ho["osd"], ho["iters"], None,
+                        hws, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(steps):
+        lbp.lbp_decode_host(dec.code, prms[0], B, hsyn, ho["err"], ho["converged"], ho["osd"], ho["iters"],
+                            None, hws, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["e2e_shots_per_s"] = B * steps / (e0.elapsed_time(e1) / 1e3)
+    # Small-batch latency, each repeat on different shots; batch 1 replayed
+    # from a CUDA graph too.
+    out["latency"] = latency_sweep(dec, prms[0], syn_d[0], ((1, 200), (64, 200), (4096, 50)), stream)
+    x1 = torch.empty((1, wm), dtype=torch.int64, device="cuda")
+    o1 = dec.alloc(1)
+    ws1 = torch.empty(lbp.lbp_workspace_size(dec.code, prms[0], 1) + 256, dtype=torch.uint8, device="cuda")
+    ws1 = ws1[(-ws1.data_ptr()) % 256:]
+    g1 = lbp.lbp_graph_create(dec.code, prms[0], 1, x1, o1.err, o1.converged, o1.osd, o1.iters, None, ws1)
+    times = []
+    for r in range(210):
+        x1.copy_(syn_d[0][r:r + 1])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lbp.lbp_graph_launch(g1, stream)
+        b.record(stream)
+        b.synchronize()
+        if r >= 10:
+            times.append(a.elapsed_time(b))
+    g1.close()
+    times.sort()
+    out["latency"]["batch_1_graph"] = {"p50_ms": times[len(times) // 2],
+                                       "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                                       "samples": len(times)}
+    step(0)
+    torch.cuda.synchronize()
+    o = outs[0]
+    f = evaluate.logical_failures(evaluate.surface_spec(11, 11, w.h.n),
+                                  torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err, o.converged, o.osd)
+    k = int(f.sum().item())
+    out["ler"] = k / B
+    out["ler_ci95"] = evaluate.wilson(k, B)
+    dec.close()
+    return out
+
+
+def run_c3_leg(shots: int = 1_000_000, oracle_shots: int = 100_000):
+    """BB [[144,12,12]] code capacity (BASELINE's third configuration):
+    Lottery BP + OSD-0 with FP16 messages, p in {0.01, 0.03, 0.05}, 10^6 shots
+    each (tuned launch shape): shots/s, OSD invoke rate, mean iterations,
+    logical error rate with its Wilson interval, and the paired comparison
+    with the FP64 oracle on the first `oracle_shots` shots."""
+    import torch
+    import oracle
+    from paper_2605_00038_gb300 import evaluate
+    from paper_2605_00038_gb300.decoder import Decoder
+    from paper_2605_00038_gb300.inputs import sampler, workloads
+
+    spec = evaluate.bb_spec("bb144")
+    cores = os.cpu_count() or 1
+    out = {}
+    for p in (0.01, 0.03, 0.05):
+        w = workloads.c3_bb144(p, shots=shots)
+        e, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=shots)
+        x = torch.from_numpy(syn.view(np.int64)).cuda()
+        true_d = torch.from_numpy(e.view(np.int64)).cuda()
+        dec = Decoder(w.h, w.priors)
+        prm = dec.params(**w.decoder, seed=w.seed)
+        dec.tune(x[:131072].contiguous(), prm)
+        dec.decode(x, prm)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        res = dec.decode(x, prm)
+        a1.record()
+        torch.cuda.synchronize()
+        t = a0.elapsed_time(a1) / 1e3
+        f = evaluate.logical_failures(spec, true_d, res.err, res.converged, res.osd).cpu().numpy()
+        k = int(f.sum())
+        t0 = time.perf_counter()
+        r = oracle.decode(w.h, w.priors, sampler.unpack(syn[:oracle_shots], w.h.m), oracle_params_for(w, oracle),
+                          nthreads=cores)
+        t_or = time.perf_counter() - t0
+        fo = evaluate.logical_failures(spec, true_d[:oracle_shots].cpu(),
+                                       torch.from_numpy(sampler.pack(r.err).view(np.int64)),
+                                       torch.from_numpy(r.converged), torch.from_numpy(r.osd_used)).numpy()
+        fs = f[:oracle_shots]
+        S_t, G_t, gf_t = lbp_tuned(dec, prm)
+        out["p%g" % p] = {
+            "workload": w.name, "shots": shots, "shots_per_s": shots / t,
+            "launch": {"groups_per_cta": S_t, "threads_per_shot": G_t, "graph": gf_t},
+            "osd_invoke_rate": float((res.osd != 0).float().mean().item()),
+            "mean_iters": float(res.iters.float().mean().item()),
+            "ler": k / shots, "ler_ci95": evaluate.wilson(k, shots),
+            "fp64_oracle_subset": {"shots": oracle_shots, "ler": float(fo.mean()),
+                                   "shots_per_s": oracle_shots / t_or, "threads": cores},
+            "gap_vs_fp64_subset": float(fs.mean() - fo.mean()),
+            "mcnemar_p_vs_fp64": evaluate.mcnemar_p(int((fs & ~fo).sum()), int((fo & ~fs).sum()))}
+        dec.close()
+    return out
 
 
 def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11, policy=None):
@@ -651,7 +936,7 @@ def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int =
     """Precision gap: Lottery BP + OSD-0 on the rotated d=7 surface code, 7
     noisy rounds, p = 0.012, with FP32 / FP16 / INT8 messages (2^20 shots
     each, identical shots), against the FP64 oracle on the first 2^15 shots.
-    Then throughput of the d=25, 25-round code (7,800 x 23,113) per precision."""
+    Then the d=27 space-time matrix in the form whose size Table II prints."""
     import torch
     import oracle
     from paper_2605_00038_gb300 import evaluate
@@ -691,30 +976,6 @@ def run_precision(shots: int = 1 << 20, oracle_shots: int = 1 << 15, seed: int =
                      "osd_invoke_rate": float((res.osd != 0).float().mean().item()),
                      "mean_iters": float(res.iters.float().mean().item())}
     dec.close()
-    # d=25 throughput per precision (no OSD, as configured).
-    c5 = {}
-    for msg, name in ((0, "fp32"), (1, "fp16"), (2, "int8")):
-        w = workloads.c5_d25_spacetime(msg=msg, shots=1 << 17)
-        _, s5 = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
-        d5 = Decoder(w.h, w.priors)
-        prm = d5.params(**w.decoder)
-        s5d = torch.from_numpy(s5.view(np.int64)).cuda()
-        d5.tune(s5d[:16384].contiguous(), prm)
-        d5.decode(s5d, prm)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        res = d5.decode(s5d, prm)
-        a1.record()
-        torch.cuda.synchronize()
-        t = a0.elapsed_time(a1) / 1e3
-        it = float(res.iters.float().mean().item())
-        bpm = {0: 4, 1: 2, 2: 1}[msg]
-        c5[name] = {"shots_per_s": w.shots / t, "mean_iters": it,
-                    "unconverged": float((res.converged == 0).float().mean().item()),
-                    "state_gbs": w.shots * it * 2 * (w.h.nnz * bpm + 4 * w.h.n) / t / 1e9}
-        d5.close()
-    out["d25_throughput"] = c5
     # d=27 in the form of Table II (unrotated code, cyclic boundary, 18,954 x
     # 56,889): the paper's simulator ran out of GPU memory here.
     from paper_2605_00038_gb300.inputs.codes import unrotated_surface
@@ -857,7 +1118,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         print(json.dumps({"serving": run_serving(), "matched_ler": run_matched(),
-                          "precision": run_precision(), "lottery_design_space": run_policies(),
+                          "precision_d7": run_precision(), "lottery_design_space": run_policies(),
                           "check_rule": run_sum_product()}),
               flush=True)
         return

@@ -527,3 +527,38 @@ def test_bench_launch_config_full_size_sampled():
         shat = torch.remainder(e @ Hd.T, 2)
         bad = (shat != s).any(1).cpu().numpy() & ok[lo:lo + 100_000]
         assert not bad.any()
+
+
+def test_bench_headline_launch_config_sampled():
+    """The d=25 workload at the benchmark's batch (2^18 shots, a quarter of
+    the configuration's 2^20) in the benchmark's launch configuration
+    (lbp_tune on the first 16,384 shots, then one decode): sampled shots match
+    the oracle one by one (decisions, flags, iteration counts), and every
+    converged shot reproduces its syndrome (H e_hat = s, on the GPU)."""
+    w = workloads.c5_d25_spacetime(msg=lbp.LBP_MSG_F32, shots=1 << 18)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    dec = Decoder(w.h, w.priors)
+    prm = dec.params(**w.decoder, seed=w.seed)
+    x = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec.tune(x[:16384].contiguous(), prm)
+    out = dec.decode(x, prm)
+    torch.cuda.synchronize()
+    conv = out.converged.cpu().numpy()
+    iters = out.iters.cpu().numpy()
+    err = sampler.unpack(out.err.cpu().numpy().view(np.uint64), w.h.n)
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(w.shots, size=40, replace=False))
+    pick = np.unique(np.concatenate([pick, np.nonzero(conv == 1)[0][:16]]))
+    for b in pick:
+        r = oracle_decode(w.h, w.priors, syn[b:b + 1], shot_offset=int(b), **dict(w.decoder, seed=w.seed))
+        assert conv[b] == r.converged[0] and iters[b] == r.iters[0], b
+        assert np.array_equal(err[b], r.err[0]), b
+    idx = np.nonzero(conv == 1)[0]
+    assert idx.size > 100
+    Hd = torch.from_numpy(w.h.to_dense().astype(np.float32)).cuda()
+    for lo in range(0, idx.size, 2048):
+        sel = idx[lo:lo + 2048]
+        e = torch.from_numpy(err[sel].astype(np.float32)).cuda()
+        s = torch.from_numpy(sampler.unpack(syn[sel], w.h.m).astype(np.float32)).cuda()
+        assert torch.equal(torch.remainder(e @ Hd.T, 2), s)
+    dec.close()

@@ -92,3 +92,19 @@ def test_clock_summary_and_roofline_helpers():
     assert ops == 10 * (8 * h.nnz + 2 * h.m + h.n)
     assert io == 4 * (8 * ((h.m + 63) // 64) + 8 * ((h.n + 63) // 64) + 6)
     assert bench.alu_peak_ops(2070.0) == 152 * 128 * 2070e6
+
+
+def test_roofline_bytes_and_iteration_histogram():
+    """The HBM roofline's numerator: B_it = 2 (E b + 4 n) bytes per
+    shot-iteration, 544,712 / 364,808 / 274,856 for the d=25 space-time code
+    with FP32 / FP16 / INT8 messages (E = 44,976, n = 23,113); and the
+    iteration histogram helper (Fig. 6) counts shots per iteration count."""
+    from paper_2605_00038_gb300.inputs import workloads
+    h = workloads.c5_d25_spacetime(shots=1).h
+    assert (h.m, h.n, h.nnz) == (7800, 23113, 44976)
+    assert [bench.state_bytes_per_iteration(h, b) for b in (4, 2, 1)] == [544712, 364808, 274856]
+    assert bench.io_bytes_per_shot(h) == 8 * 122 + 8 * 362 + 6
+    a = torch.tensor([3, 1, 3, 100], dtype=torch.int32)
+    b = torch.tensor([100, 100, 7], dtype=torch.int32)
+    assert bench.histogram([a, b]) == {"1": 1, "3": 2, "7": 1, "100": 3}
+    assert bench.histogram([b, a]) == {"1": 1, "3": 2, "7": 1, "100": 3}
