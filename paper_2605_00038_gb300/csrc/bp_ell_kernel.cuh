@@ -150,9 +150,11 @@ __device__ __forceinline__ void check_update_sp(const float (&al)[DC], uint32_t 
     }
 }
 
+// A split state runs one shot per CTA, so its block is exactly G threads and
+// the register budget follows G (64 per thread at 1024, 80 at 768, 128 at 512).
 template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename GraphT,
           int kRule = LBP_RULE_MIN_SUM, bool kSplit = false>
-__global__ void __launch_bounds__(1024, 1) bp_ell_kernel(const BpEllArgs a) {
+__global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
     static_assert(GraphT::kImage || !kGraphSmem, "an implicit graph has no image to stage");
     static_assert(!kSplit || (kStateSmem && !kGraphSmem), "a split state keeps its shared part beside a global image");

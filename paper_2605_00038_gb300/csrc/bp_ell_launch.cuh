@@ -72,8 +72,12 @@ int launch_ell_g(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     }
     if (s.split) {
         // One shot per CTA: the shared part of a split state nearly fills it.
-        if (s.G == 1024) return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, true, uint16_t, true>(s, a, st);
-        return LBP_ENOSYS;
+        switch (s.G) {
+            case 512: return launch_ell_one<MsgT, kRule, 512, DC, DV, false, true, uint16_t, true>(s, a, st);
+            case 768: return launch_ell_one<MsgT, kRule, 768, DC, DV, false, true, uint16_t, true>(s, a, st);
+            case 1024: return launch_ell_one<MsgT, kRule, 1024, DC, DV, false, true, uint16_t, true>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
     }
     if (s.state_smem) {
         switch (s.G) {

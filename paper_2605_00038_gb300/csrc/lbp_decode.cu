@@ -21,6 +21,8 @@
 //                                                     not fit shared memory)
 //   slots      u64[warps][C][ceil(n/64)] K_osd_warp dense-row pools
 #include <algorithm>
+#include <utility>
+#include <vector>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -201,16 +203,24 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
         // memory when one group's fits, else in the workspace.
         p.graph_smem = false;
         p.state_smem = off <= budget0;
+        // The requested shape, else LBP_BP_SHAPE, else lbp_tune's stored one.
         if (!req_G && c->env_G) {
             req_S = c->env_S;
             req_G = c->env_G;
         }
+        if (!req_G && c->tuned_G[mi] > 0 && c->tuned_graph[mi] == 1) {
+            req_S = c->tuned_groups[mi];
+            req_G = c->tuned_G[mi];
+        }
         // Split state: when one shot's state does not fit, the largest number
         // of message slots that fits stays in shared memory with the
-        // posteriors and syndrome words (one shot per CTA, 1024 threads), the
-        // other slots go to a per-group workspace slice.  An explicit request
-        // for 256 or 512 threads keeps the whole state in the workspace.
-        if (!p.state_smem && !p.idx32 && req_G != 256 && req_G != 512) {
+        // posteriors and syndrome words (one shot per CTA of 512, 768 or 1024
+        // threads: the tuned or requested width, else 1024), the other slots
+        // go to a per-group workspace slice.  A request for several groups
+        // (S > 1) or for 256 threads keeps the whole state in the workspace.
+        const int s_eff = req_G > 0 ? std::min(req_S > 0 ? req_S : 1, 1024 / req_G) : 1;
+        const bool split_req = req_G == 0 || (s_eff <= 1 && (req_G == 512 || req_G == 768 || req_G == 1024));
+        if (!p.state_smem && !p.idx32 && split_req) {
             for (int ks = c->ell.DC - 1; ks >= 1; --ks) {
                 const uint32_t o = state_layout(c->ell.Mp + 2, ks);
                 if (o <= budget0) {
@@ -221,6 +231,7 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
                     p.state_smem = true;
                     p.groups = 1;
                     p.G = 1024;
+                    if (req_G == 512 || req_G == 768) p.G = req_G;
                     p.smem = o;
                     const int64_t need = num_shots;
                     p.grid = static_cast<int>(need < c->sm_count ? need : c->sm_count);
@@ -923,19 +934,26 @@ extern "C" int lbp_tune(lbp_code *code, const lbp_params *params, int64_t num_sh
     code->tuned_G[mi] = 0;
     code->tuned_groups[mi] = 0;
     code->tuned_graph[mi] = 0;
-    const int Gs[] = {32, 64, 96, 128, 192, 256, 512, 1024};
+    const int Gs[] = {32, 64, 96, 128, 192, 256, 512, 768, 1024};
     float best = -1.0f;
     int best_S = 0, best_G = 0, best_graph = 0;
     // Candidates: every thread count, with the index image and, for a
     // recognised surface code, with the implicit graph.
+    std::vector<std::pair<int, int>> seen;           // (S, G) already timed for this graph form
     for (int graph = 1; graph <= 3; ++graph) {
         if (graph == 2 && !code->surface) continue;
         if (graph == 3 && !code->round) continue;
-        for (int G : Gs) {
+        seen.clear();
+        for (int cand = 0; cand < 2 * static_cast<int>(sizeof(Gs) / sizeof(Gs[0])); ++cand) {
+            // Each width with as many groups as fit, then with one group per CTA.
+            const int G = Gs[cand % (sizeof(Gs) / sizeof(Gs[0]))];
+            const int S_req = cand < static_cast<int>(sizeof(Gs) / sizeof(Gs[0])) ? 1024 : 1;
             BpPlan probe;
-            if (plan_bp(code, params->msg, params->rule, num_shots, &probe, 1024, G, graph) != LBP_OK) continue;
+            if (plan_bp(code, params->msg, params->rule, num_shots, &probe, S_req, G, graph) != LBP_OK) continue;
             if (probe.G != G) continue;                    // shape not available for this code
             const int S = probe.groups;
+            if (std::find(seen.begin(), seen.end(), std::make_pair(S, G)) != seen.end()) continue;
+            seen.emplace_back(S, G);
             float ms = 0.0f, warm = 0.0f;
             rc = lbp::decode_device_shaped(code, params, num_shots, syndromes, err_out, converged, osd_out,
                                            iters_out, nullptr, workspace, workspace_bytes, s, S, G, &warm,
