@@ -373,8 +373,8 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
 
     lbp_code *c = new (std::nothrow) lbp_code();
     if (!c) return LBP_ENOMEM;
-    read_env_switches(c);
     std::memset(c, 0, sizeof(*c));
+    read_env_switches(c);
     c->m = m; c->n = n; c->nnz = nnz;
     c->max_row_deg = maxdeg; c->max_col_deg = maxcol;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LBP_ECUDA; }
