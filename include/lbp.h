@@ -133,6 +133,14 @@ void lbp_params_default(lbp_params *p);
 int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *priors, lbp_code **out);
 
+/* The environment switches lbp_load_code read for this code: graph form
+ * (0 unset, 1 table, 2 implicit, 3 round), BP launch shape (groups per CTA and
+ * threads per group, 0 unset), OSD pool rows (0 unset) and the OSD latency
+ * layout (1 on, 0 off).  Any output pointer may be NULL.  Errors: LBP_EINVAL
+ * (code NULL). */
+int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int32_t *G,
+                     int32_t *pool_rows, int32_t *osd_latency);
+
 /* Release a code object (synchronous; no call using it may be in flight). */
 int lbp_free_code(lbp_code *code);
 

@@ -326,6 +326,17 @@ void read_env_switches(lbp_code *c) {
 
 }  // namespace
 
+extern "C" int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int32_t *G,
+                                int32_t *pool_rows, int32_t *osd_latency) {
+    if (!code) return LBP_EINVAL;
+    if (graph) *graph = code->env_graph;
+    if (groups) *groups = code->env_S;
+    if (G) *G = code->env_G;
+    if (pool_rows) *pool_rows = code->env_pool_rows;
+    if (osd_latency) *osd_latency = code->env_osd_lat;
+    return LBP_OK;
+}
+
 extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                              const double *priors, lbp_code **out) {
     if (!out) return LBP_EINVAL;

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from .inputs.codes import SparseH, bb_code, logical_operators, rotated_surface
+from .inputs.codes import SparseH, bb_code, logical_operators, rotated_surface, unrotated_surface
 
 
 @dataclass
@@ -28,6 +28,13 @@ class LogicalSpec:
 
 def surface_spec(d: int, rounds: int, n_total: int) -> LogicalSpec:
     hz, hx = rotated_surface(d)
+    return LogicalSpec(logical_operators(hz, hx), rounds, hz.n, n_total)
+
+
+def unrotated_surface_spec(d: int, rounds: int, n_total: int) -> LogicalSpec:
+    """Logical operators for X errors detected by the unrotated code's Z
+    checks (Table III's H_Z rows), per round of a space-time matrix."""
+    hx, hz = unrotated_surface(d)
     return LogicalSpec(logical_operators(hz, hx), rounds, hz.n, n_total)
 
 

@@ -39,3 +39,29 @@ def test_wilson_and_mcnemar():
     assert evaluate.mcnemar_p(0, 0) == 1.0
     assert evaluate.mcnemar_p(10, 10) > 0.5
     assert evaluate.mcnemar_p(0, 20) < 1e-5
+
+
+def test_unrotated_spec_scores_logicals_and_stabilizers():
+    """Unrotated surface code (Table III rows): one logical operator L, which
+    commutes with the X stabilizers; a residual that is an X logical (no Z
+    check sees it, and it is not a product of X stabilizers) fails, a
+    residual equal to an X stabilizer (a row of H_X) does not."""
+    from paper_2605_00038_gb300.inputs.codes import unrotated_surface
+    d, T = 5, 3
+    hx, hz = unrotated_surface(d)
+    st = spacetime(hz, T)
+    spec = evaluate.unrotated_surface_spec(d, T, st.n)
+    assert spec.L.shape == (1, hz.n)
+    L = spec.L[0]
+    assert not (hx.to_dense().astype(int) @ L % 2).any()
+    xl = logical_operators(hx, hz)[0]                  # an X logical: in ker(H_Z), not in rowspace(H_X)
+    assert not (hz.to_dense().astype(int) @ xl % 2).any() and int(L.astype(int) @ xl) % 2 == 1
+    true = np.zeros((2, st.n), np.uint8)
+    true[0, 2 * hz.n: 3 * hz.n] = xl
+    true[1, hz.n: 2 * hz.n] = hx.to_dense()[3]
+    z = np.zeros_like(true)
+    ones = np.ones(2, np.uint8)
+    f = evaluate.logical_failures(spec, torch.from_numpy(sampler.pack(true).view(np.int64)),
+                                  torch.from_numpy(sampler.pack(z).view(np.int64)),
+                                  torch.from_numpy(ones), torch.from_numpy(np.zeros(2, np.uint8)))
+    assert f.tolist() == [True, False]

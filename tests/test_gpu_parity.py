@@ -562,3 +562,24 @@ def test_bench_headline_launch_config_sampled():
         s = torch.from_numpy(sampler.unpack(syn[sel], w.h.m).astype(np.float32)).cuda()
         assert torch.equal(torch.remainder(e @ Hd.T, 2), s)
     dec.close()
+
+
+def test_environment_switches_read_at_load(monkeypatch):
+    """The experiment switches are read once, when a code is loaded, and kept
+    in the code object: a later change of the environment does not affect it."""
+    h, pri = workloads.c1_d3_code_capacity().h, np.full(9, 0.05)
+    for k in ("LBP_GRAPH", "LBP_BP_SHAPE", "LBP_OSD_POOL_ROWS", "LBP_OSD_LAT"):
+        monkeypatch.delenv(k, raising=False)
+    plain = Decoder(h, pri)
+    assert lbp.lbp_code_options(plain.code) == (0, 0, 0, 0, 1)
+    monkeypatch.setenv("LBP_GRAPH", "round")
+    monkeypatch.setenv("LBP_BP_SHAPE", "3,256")
+    monkeypatch.setenv("LBP_OSD_POOL_ROWS", "7")
+    monkeypatch.setenv("LBP_OSD_LAT", "0")
+    dec = Decoder(h, pri)
+    assert lbp.lbp_code_options(dec.code) == (3, 3, 256, 7, 0)
+    assert lbp.lbp_code_options(plain.code) == (0, 0, 0, 0, 1)
+    monkeypatch.setenv("LBP_GRAPH", "implicit")
+    assert lbp.lbp_code_options(dec.code)[0] == 3
+    dec.close()
+    plain.close()

@@ -53,10 +53,13 @@ def test_c1_ler_matches_fp64_oracle_over_1e6_shots():
     assert abs(fg.mean() - fo.mean()) <= 0.05 * fo.mean()
 
 
-def test_bb144_ler_matches_fp64_oracle():
-    w = workloads.c3_bb144(0.05, shots=100_000)
+def test_bb144_ler_matches_fp64_oracle_over_1e6_shots():
+    """BB [[144,12,12]] at p = 0.05 (BASELINE's third configuration), Lottery
+    BP + OSD-0: FP32 GPU against the FP64 oracle on the same 10^6 shots."""
+    w = workloads.c3_bb144(0.05, shots=1_000_000)
     kw = dict(w.decoder, msg=lbp.LBP_MSG_F32, seed=3)
     fg, fo = _paired(w, evaluate.bb_spec("bb144"), w.shots, **kw)
     b, c = int((fg & ~fo).sum()), int((fo & ~fg).sum())
-    assert fg.sum() > 100
+    assert fg.sum() > 1000
     assert evaluate.mcnemar_p(b, c) > 0.01, (fg.sum(), fo.sum(), b, c)
+    assert abs(fg.mean() - fo.mean()) <= 0.05 * fo.mean()
