@@ -198,6 +198,34 @@ def hbm_peak_gbs():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def smem_bytes_per_iteration(h, msg_bytes):
+    """On-chip bytes one shot-iteration must move: per edge the posterior and
+    message read, the message written (check phase) and read again (column
+    phase), E (4 + 3 b); per column the posterior written and the prior read,
+    8 n."""
+    return h.nnz * (4 + 3 * msg_bytes) + 8 * h.n
+
+
+def smem_peak(stream=None, reps: int = 3):
+    """(bytes/s, clock summary) of the shared-memory load bandwidth probe
+    (lbp_probe_smem), the best of `reps` timed launches, with the SM clock
+    sampled while it ran."""
+    from paper_2605_00038_gb300 import lbp
+    import torch
+    cs = ClockSampler(torch.cuda.current_device())
+    cs.start()
+    best = 0.0
+    t_end = time.perf_counter() + 0.5
+    while True:
+        for _ in range(reps):
+            b, ms = lbp.lbp_probe_smem(4096, stream)
+            best = max(best, b / (ms / 1e3))
+        if time.perf_counter() >= t_end:
+            break
+    cs.stop()
+    return best, cs.summary()
+
+
 def histogram(iters_tensors):
     """Iteration histogram (Fig. 6) over the given per-shot iteration counts:
     {iterations: shots}, non-zero entries only."""
@@ -380,6 +408,13 @@ def run_gpu(args):
         "alu": {"achieved_tops": ops / bp_avg_s / 1e12, "peak_tops": alu_peak_ops(sm_mhz) / 1e12,
                 "frac": ops / bp_avg_s / alu_peak_ops(sm_mhz),
                 "peak_basis": "152 SMs x 128 lanes x median SM clock %.0f MHz (derived)" % sm_mhz}}
+    smem_bps, smem_clk = smem_peak(stream)
+    smem_alg = iters_per_step * smem_bytes_per_iteration(w.h, 4)
+    line["roofline"]["smem"] = {"achieved_tbs": smem_alg / bp_avg_s / 1e12, "peak_tbs": smem_bps / 1e12,
+                                "frac": smem_alg / bp_avg_s / smem_bps,
+                                "bytes_per_shot_iteration": smem_bytes_per_iteration(w.h, 4),
+                                "peak_basis": "measured by lbp_probe_smem (conflict-free 16-byte loads), "
+                                              "SM clock %s MHz while it ran" % smem_clk.get("sm_mhz")}
     line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps,
                        "osd_ms_per_step": osd_ms / args.steps,
                        "mean_iters": iters_total / (B * args.steps),
@@ -633,9 +668,13 @@ def run_c2_leg(args, shots: int = 1_000_000, steps: int = 5, warmup: int = 3):
     # ALU and shared-memory views of K_bp (the state stays in shared memory).
     ops, _ = roofline_model(w, iters / steps, B)
     bp_avg_s = bp_ms / max(bp_n, 1) / 1e3
+    smem_bps, _ = smem_peak()
     out["roofline_alu"] = {"achieved_tops": ops / bp_avg_s / 1e12, "frac": ops / bp_avg_s / alu_peak_ops(2070.0),
                            "algorithmic_state_tbs": (iters / steps) * state_bytes_per_iteration(w.h, 4)
                                                     / bp_avg_s / 1e12}
+    out["roofline_smem"] = {"achieved_tbs": (iters / steps) * smem_bytes_per_iteration(w.h, 4) / bp_avg_s / 1e12,
+                            "peak_tbs": smem_bps / 1e12,
+                            "frac": (iters / steps) * smem_bytes_per_iteration(w.h, 4) / bp_avg_s / smem_bps}
     # End to end through the host-buffer entry point.
     pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
     hsyn = pin(syn_h[0].shape, torch.int64)
@@ -850,85 +889,134 @@ def dec_priors(dec):
     return dec.priors
 
 
-def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21):
-    """Matched-LER head-to-head on identical shots of the rotated d=7 surface
-    code, 7 noisy rounds, p = 0.012: (A) plain NMS BP + OSD-0, FP32 messages,
-    one batched lbp_decode; (B) Lottery BP + OSD-0, INT8 (Int3.4) messages, served in
-    4096-shot requests through lbp_server, with the proposed flip rule and
-    with the worst-check / least-reliable-column rule of Sec. III-B.  Logical
-    error rates with Wilson 95% intervals and the paired McNemar test against
-    (A), throughput and p50 / p99 request latency."""
+def _served(dec, prms, hs, hbuf, load, rng):
+    """Serve the requests (lo, B, params) through one lbp_server: capacity with
+    all queued, then open-loop Poisson arrivals at `load` x that capacity.
+    Returns (capacity shots/s, open-loop dict, request latencies of the
+    capacity run)."""
+    import torch
+    from paper_2605_00038_gb300 import lbp
+    herr, hconv, hosd, hit = hbuf
+    srv = lbp.lbp_server_create(8 << 30, 16)
+
+    def submit(lo, B, prm):
+        return lbp.lbp_server_submit(srv, dec.code, prm, B, hs[lo:lo + B], herr[lo:lo + B], hconv[lo:lo + B],
+                                     hosd[lo:lo + B], hit[lo:lo + B])
+
+    lo0, B0, p0 = prms[0]
+    lbp.lbp_server_wait(srv, submit(lo0, B0, p0))
+    total = sum(B for _, B, _ in prms)
+    t0 = time.perf_counter()
+    tks = [submit(lo, B, prm) for lo, B, prm in prms]
+    for t in tks:
+        lbp.lbp_server_wait(srv, t)
+    span = time.perf_counter() - t0
+    cap = total / span
+    rate = load * len(prms) / span
+    gaps = rng.exponential(1.0 / rate, size=len(prms))
+    sent = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for j, (lo, B, prm) in enumerate(prms):
+        t_next += gaps[j]
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            time.sleep(min(0.0005, t_next - now))
+        sent.append(submit(lo, B, prm))
+    lats = [lbp.lbp_server_wait(srv, t) for t in sent]
+    span2 = time.perf_counter() - t_start
+    srv.close()
+    q = lambda x: float(np.quantile(np.asarray(lats), x) * 1e3)
+    return cap, {"load": load, "offered_requests_per_s": rate, "requests": len(prms),
+                 "shots_per_s": total / span2, "p50_ms": q(0.5), "p99_ms": q(0.99)}
+
+
+def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load: float = 0.8):
+    """Matched-LER head-to-head on identical shots: (A) plain NMS BP + OSD-0
+    with FP32 messages against Lottery BP + OSD-0 with INT8 (Int3.4) messages
+    and the paper's rule (Alg. 3), on the code families the paper evaluates
+    (the BB [[144,12,12]] code at p = 0.05, code capacity; the unrotated
+    surface code's space-time matrix, Table III rows, d = 7, 7 rounds,
+    p = 0.01) and on the rotated d = 7 space-time code (p = 0.012), where the
+    worst-check / least-reliable-column rule of Sec. III-B is added.  Every
+    arm is timed the same two ways: one device-resident lbp_decode of all
+    shots, and served through lbp_server from host buffers in 4096-shot
+    requests (capacity with every request queued; then open-loop Poisson
+    arrivals at 80% of that arm's own capacity, whose p50 / p99 request
+    latency is not queueing).  LER with Wilson intervals and the paired
+    McNemar test of each Lottery arm against (A)."""
     import torch
     from paper_2605_00038_gb300 import evaluate, lbp
     from paper_2605_00038_gb300.decoder import Decoder
     from paper_2605_00038_gb300.inputs import sampler
-    from paper_2605_00038_gb300.inputs.codes import rotated_surface, spacetime, spacetime_priors
+    from paper_2605_00038_gb300.inputs.codes import (bb_code, rotated_surface, spacetime, spacetime_priors,
+                                                     unrotated_surface)
 
-    d, p = 7, 0.012
-    hz, _ = rotated_surface(d)
-    h = spacetime(hz, d)
-    pri = spacetime_priors(hz, d, p, p)
-    e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
-    spec = evaluate.surface_spec(d, d, h.n)
-    true_d = torch.from_numpy(e.view(np.int64)).cuda()
-    dec = Decoder(h, pri)
-    # Arm A: plain BP + OSD-0, FP32, batched.
-    pa = dec.params(max_iter=100, lottery=0, osd=1, msg=0, seed=seed)
-    sd = torch.from_numpy(syn.view(np.int64)).cuda()
-    dec.decode(sd, pa)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    ra = dec.decode(sd, pa)
-    ev1.record()
-    torch.cuda.synchronize()
-    ta = ev0.elapsed_time(ev1) / 1e3
-    fa = evaluate.logical_failures(spec, true_d, ra.err, ra.converged, ra.osd)
-    ka = int(fa.sum().item())
-    out = {
-        "workload": "rotated_d7_st7_p0.012", "shots": shots,
-        "plain_bp_osd_fp32_batched": {
-            "ler": ka / shots, "ler_ci95": evaluate.wilson(ka, shots), "shots_per_s": shots / ta,
-            "latency_ms": ta * 1e3, "osd_invoke_rate": float((ra.osd != 0).float().mean().item()),
-            "mean_iters": float(ra.iters.float().mean().item())},
-    }
-    # Arms B: Lottery BP + OSD-0, INT8, served.
-    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
-    hs = pin(syn.shape, torch.int64)
-    hs.numpy()[:] = syn.view(np.int64)
-    wn = (h.n + 63) // 64
-    herr, hconv, hosd, hit = pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8), pin(shots, torch.int32)
-    for key, policy in (("lottery_bp_osd_int8_served", lbp.LBP_LOTTERY_PROPOSED),
-                        ("lottery_worst_unreliable_bp_osd_int8_served", lbp.LBP_LOTTERY_WORST_UNRELIABLE)):
-        srv = lbp.lbp_server_create(8 << 30, 16)
-        reqs = []
-        for lo in range(0, shots, request):
-            B = min(request, shots - lo)
-            prm = dec.params(max_iter=100, lottery=1, lottery_policy=policy, osd=1, msg=2, seed=seed,
-                             shot_offset=lo)
-            reqs.append((lo, B, prm))
-        lbp.lbp_server_wait(srv, lbp.lbp_server_submit(srv, dec.code, reqs[0][2], reqs[0][1], hs[:reqs[0][1]],
-                                                       herr[:reqs[0][1]], hconv[:reqs[0][1]],
-                                                       hosd[:reqs[0][1]], hit[:reqs[0][1]]))
-        t0 = time.perf_counter()
-        tks = [lbp.lbp_server_submit(srv, dec.code, prm, B, hs[lo:lo + B], herr[lo:lo + B], hconv[lo:lo + B],
-                                     hosd[lo:lo + B], hit[lo:lo + B]) for lo, B, prm in reqs]
-        lats = [lbp.lbp_server_wait(srv, t) for t in tks]
-        tb = time.perf_counter() - t0
-        srv.close()
-        fb = evaluate.logical_failures(spec, true_d, herr.cuda(), hconv.cuda(), hosd.cuda())
-        kb = int(fb.sum().item())
-        only_a = int((fa & ~fb).sum().item())
-        only_b = int((fb & ~fa).sum().item())
-        out[key] = {
-            "policy": policy, "ler": kb / shots, "ler_ci95": evaluate.wilson(kb, shots),
-            "shots_per_s": shots / tb, "request_shots": request,
-            "p50_ms": float(np.quantile(lats, 0.5) * 1e3), "p99_ms": float(np.quantile(lats, 0.99) * 1e3),
-            "osd_invoke_rate": float((hosd != 0).float().mean().item()),
-            "mean_iters": float(hit.float().mean().item()),
-            "ler_relative_difference": (kb - ka) / max(ka, 1), "mcnemar_discordant": [only_a, only_b],
-            "mcnemar_p": evaluate.mcnemar_p(only_a, only_b)}
-    dec.close()
+    fams = []
+    hx, _ = bb_code("bb144")
+    fams.append(("bb144_cc_p0.05", hx, np.full(hx.n, 0.05), evaluate.bb_spec("bb144")))
+    _, uz = unrotated_surface(7)
+    ust = spacetime(uz, 7)
+    fams.append(("unrotated_d7_st7_p0.01", ust, spacetime_priors(uz, 7, 0.01, 0.01),
+                 evaluate.unrotated_surface_spec(7, 7, ust.n)))
+    rz, _ = rotated_surface(7)
+    rst = spacetime(rz, 7)
+    fams.append(("rotated_d7_st7_p0.012", rst, spacetime_priors(rz, 7, 0.012, 0.012),
+                 evaluate.surface_spec(7, 7, rst.n)))
+    rng = np.random.default_rng(seed)
+    out = {"shots": shots, "request_shots": request, "open_loop_load": load, "families": {}}
+    for name, h, pri, spec in fams:
+        e, syn = sampler.sample(h, pri, seed=seed, num_shots=shots)
+        true_d = torch.from_numpy(e.view(np.int64)).cuda()
+        sd = torch.from_numpy(syn.view(np.int64)).cuda()
+        dec = Decoder(h, pri)
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory()
+        hs = pin(syn.shape, torch.int64)
+        hs.numpy()[:] = syn.view(np.int64)
+        wn = (h.n + 63) // 64
+        hbuf = (pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8),
+                pin(shots, torch.int32))
+        arms = [("plain_bp_osd_fp32", dict(lottery=0, msg=0, lottery_policy=0)),
+                ("lottery_alg3_bp_osd_int8", dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_PROPOSED))]
+        if name.startswith("rotated"):
+            arms.append(("lottery_worst_unreliable_bp_osd_int8",
+                         dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE)))
+        fam = {"shape": [h.m, h.n, h.nnz]}
+        fa = None
+        for arm, kw in arms:
+            prm = dec.params(max_iter=100, osd=1, seed=seed, **kw)
+            dec.decode(sd[:4096].contiguous(), prm)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            r = dec.decode(sd, prm)
+            a1.record()
+            torch.cuda.synchronize()
+            tb = a0.elapsed_time(a1) / 1e3
+            f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+            k = int(f.sum().item())
+            reqs = [(lo, min(request, shots - lo), dec.params(max_iter=100, osd=1, seed=seed, shot_offset=lo, **kw))
+                    for lo in range(0, shots, request)]
+            cap, ol = _served(dec, reqs, hs, hbuf, load, rng)
+            same = bool(torch.equal(hbuf[0].cuda(), r.err) and torch.equal(hbuf[1].cuda(), r.converged))
+            res = {"ler": k / shots, "ler_ci95": evaluate.wilson(k, shots), "logical_failures": k,
+                   "batched_shots_per_s": shots / tb, "served_capacity_shots_per_s": cap, "served_open_loop": ol,
+                   "served_equals_batched": same,
+                   "osd_invoke_rate": float((r.osd != 0).float().mean().item()),
+                   "mean_iters": float(r.iters.float().mean().item())}
+            if fa is None:
+                fa, ka = f, k
+            else:
+                only_a = int((fa & ~f).sum().item())
+                only_b = int((f & ~fa).sum().item())
+                res.update({"ler_relative_difference": (k - ka) / max(ka, 1),
+                            "mcnemar_discordant": [only_a, only_b],
+                            "mcnemar_p": evaluate.mcnemar_p(only_a, only_b)})
+            fam[arm] = res
+        out["families"][name] = fam
+        dec.close()
     return out
 
 

@@ -369,6 +369,15 @@ int lbp_graph_destroy(lbp_graph *graph);
 int lbp_timing_enable(int on);
 int lbp_timing_read(double *bp_ms, int64_t *bp_launches, double *osd_ms, int64_t *osd_launches);
 
+/* Shared-memory load bandwidth probe for the on-chip roofline: two CTAs of
+ * 1024 threads per SM read conflict-free 16-byte words from shared memory,
+ * `trips` loop trips of eight loads per thread; the second of two launches
+ * is timed with CUDA events on `stream` (synchronous: returns after it).
+ * *bytes = bytes loaded by that launch, *ms = its duration.  Not part of the
+ * paper's method; it measures the device.  Errors: LBP_EINVAL (trips outside
+ * [1, 2^20], NULL outputs), LBP_ENOMEM, LBP_ECUDA. */
+int lbp_probe_smem(int32_t trips, double *bytes, float *ms, void *stream);
+
 /* Static text for an LBP_* code. */
 const char *lbp_strerror(int code);
 

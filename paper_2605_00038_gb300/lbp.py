@@ -30,7 +30,7 @@ EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_in
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
             "lbp_server_wait", "lbp_server_destroy", "lbp_graph_create", "lbp_graph_launch",
-            "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read",
+            "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_probe_smem",
             "lbp_strerror"]
 
 
@@ -76,6 +76,8 @@ def lib():
         L.lbp_code_tuned.argtypes = [vp, i32, i32, vp, vp, vp]
         L.lbp_code_options.restype = ctypes.c_int
         L.lbp_code_options.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.lbp_probe_smem.restype = ctypes.c_int
+        L.lbp_probe_smem.argtypes = [i32, vp, vp, vp]
         L.lbp_code_rounds.restype = ctypes.c_int
         L.lbp_code_rounds.argtypes = [vp, vp, vp, vp, vp]
         L.lbp_workspace_size.restype = sz
@@ -213,6 +215,13 @@ def lbp_code_options(code: Code):
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().lbp_code_options(code.ptr, *[ctypes.byref(x) for x in v]), "lbp_code_options")
     return tuple(x.value for x in v)
+
+
+def lbp_probe_smem(trips: int = 4096, stream=None):
+    """(bytes loaded, milliseconds) of the shared-memory bandwidth probe."""
+    b, ms = ctypes.c_double(), ctypes.c_float()
+    _check(lib().lbp_probe_smem(trips, ctypes.byref(b), ctypes.byref(ms), _stream_handle(stream)), "lbp_probe_smem")
+    return b.value, ms.value
 
 
 def lbp_workspace_size(code: Code, params: lbp_params, num_shots: int) -> int:
