@@ -253,6 +253,43 @@ int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_
                     uint8_t *osd_out, int32_t *iters_out, float *llr_out,
                     void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---- One launch for several codes -------------------------------------------
+ *
+ * A merged decode: the shots of several requests, of different codes, share
+ * one persistent BP launch.  Every group of threads claims the next shot of
+ * the combined work list, finds the request it belongs to and decodes it with
+ * that request's code (its index image read from global memory, where the
+ * L2 keeps it), parameters and buffers; OSD-0 then runs per request on the
+ * shots BP left unconverged.  Each request's results are exactly those of
+ * lbp_decode on the same arguments.  All requests must use the same message
+ * type, the min-sum rule, and codes whose bounded-degree image has 16-bit
+ * indices and the same degree bounds (every surface-code space-time matrix
+ * shares one bound, every BB code another), on the current device.  The paper
+ * has one decoder per code; this is the GPU service's batching. */
+typedef struct {
+    const lbp_code *code;
+    lbp_params params;
+    int64_t  num_shots;
+    const uint64_t *syndromes;   /* device, [B][ceil(m/64)] */
+    uint64_t *err_out;           /* device, [B][ceil(n/64)] */
+    uint8_t  *converged;         /* device, [B] */
+    uint8_t  *osd_out;           /* device, [B], may be NULL */
+    int32_t  *iters_out;         /* device, [B] */
+} lbp_batch_item;
+
+/* Device workspace bytes lbp_decode_batch needs for these items (0 when the
+ * items cannot share a launch or an argument is invalid).  Only the codes,
+ * parameters and shot counts are read, not the buffer pointers. */
+size_t lbp_batch_workspace_size(const lbp_batch_item *items, int32_t n_items);
+
+/* Decode n_items (1..64) requests in one BP launch on `stream` (asynchronous;
+ * the item array itself is copied before the call returns).  workspace:
+ * lbp_batch_workspace_size bytes, 256-byte aligned, caller-owned.  Errors:
+ * LBP_EINVAL (arguments), LBP_ENOSYS (the items cannot share a launch),
+ * LBP_ENOMEM (workspace too small), LBP_ECUDA. */
+int lbp_decode_batch(const lbp_batch_item *items, int32_t n_items, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
 /* ---- Serving: continuous batching on one device ---------------------------
  *
  * A server owns a device arena (one cudaMalloc of arena_bytes at creation),
@@ -288,6 +325,16 @@ int lbp_server_create(size_t arena_bytes, int max_inflight, lbp_server **out);
  * whole SMs; otherwise it runs the throughput layouts.
  * Errors: LBP_EINVAL (chunk_work < 0, priority not 0 or 1). */
 int lbp_server_configure(lbp_server *server, int64_t chunk_work, int priority);
+
+/* Merged launches: with max_items > 0, whenever an in-flight slot is free
+ * the scheduler takes the oldest waiting request and up to max_items - 1
+ * later ones that can share its launch (lbp_decode_batch's conditions) and
+ * that fit the arena together, and decodes them with one BP launch on the
+ * slot's stream; requests that cannot be merged run as before.  0 (the
+ * default) keeps one launch chain per request.  Results do not depend on it.
+ * Applies to requests admitted after the call.  Errors: LBP_EINVAL
+ * (max_items outside [0, 64]). */
+int lbp_server_set_batching(lbp_server *server, int32_t max_items);
 
 /* Queue a decode (buffers as for lbp_decode_host, osd_out may be NULL) and
  * return its ticket.  LBP_E2BIG if the request can never fit the arena. */

@@ -95,6 +95,14 @@ struct BpEllArgs {
     // row stride in words and the image offset of the check-pair table.
     int32_t tab_R;
     uint32_t off_ptab;
+    // Merged launch (kMulti): the launch's arguments hold the claim counter
+    // (counters[0]), the total shot count (num_shots), the largest state
+    // (state_bytes) and the items; each item is a whole BpEllArgs of its own
+    // code, parameters and buffers, whose shots are the launch's work indices
+    // [first, first + num_shots).
+    const BpEllArgs *items;
+    int32_t n_items;
+    int64_t first;
 };
 
 // Exclusive minima and signed outputs of one check (DC slots).
@@ -152,12 +160,20 @@ __device__ __forceinline__ void check_update_sp(const float (&al)[DC], uint32_t 
 
 // A split state runs one shot per CTA, so its block is exactly G threads and
 // the register budget follows G (64 per thread at 1024, 80 at 768, 128 at 512).
+// A merged launch (kMulti) decodes the shots of several codes of the same
+// degree bounds: each group claims the next work index, finds its item (a
+// binary search over the items' first indices) and decodes that shot with the
+// item's image (read from global memory, L2-resident), parameters and
+// buffers; every code-dependent value is rebound per shot, and the group's
+// shared-memory state is sized for the largest code.
 template <typename MsgT, int G, int DC, int DV, bool kGraphSmem, bool kStateSmem, typename GraphT,
-          int kRule = LBP_RULE_MIN_SUM, bool kSplit = false>
+          int kRule = LBP_RULE_MIN_SUM, bool kSplit = false, bool kMulti = false>
 __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEllArgs a) {
     static_assert(DC >= 2 && DC <= 8 && DV <= 8, "bounded degrees");
     static_assert(GraphT::kImage || !kGraphSmem, "an implicit graph has no image to stage");
     static_assert(!kSplit || (kStateSmem && !kGraphSmem), "a split state keeps its shared part beside a global image");
+    static_assert(!kMulti || (GraphT::kEll && !kGraphSmem && kStateSmem && !kSplit),
+                  "a merged launch reads its images from global memory and keeps its states in shared memory");
     using PairT = typename Pair<MsgT>::type;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
@@ -166,17 +182,15 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
         const int words = static_cast<int>(a.img.bytes >> 4);
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
     }
-    const int m = a.m, n = a.n, I = a.max_iter;
+    // The shot's item in a merged launch; LBP_ARG(f) is the argument f of the
+    // shot being decoded (the launch's own arguments otherwise).
+    const BpEllArgs *item = nullptr;
+#define LBP_ARG(f) (kMulti ? item->f : a.f)
     // The bank-aware layout exists only for the index image staged in shared
     // memory; every other instantiation keeps R = Mp + 2 and no pair table.
     constexpr bool kTab = kGraphSmem && GraphT::kEll;
     // Index image read from global memory: prefetch its words one trip ahead.
     constexpr bool kPf = !kGraphSmem && GraphT::kEll;
-    const int Mp = a.img.Mp, Np = a.img.Np, R = (kTab && a.tab_R > 0) ? a.tab_R : Mp + 2;
-    const uint16_t *ptab =
-        (kTab && a.off_ptab != 0u) ? reinterpret_cast<const uint16_t *>(smem + a.off_ptab) : nullptr;
-    const int mpairs = Mp >> 1, npairs = Np >> 1;
-    const GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.rnd, a.mu_tab, m, n);
     const uint32_t image_smem = kGraphSmem ? a.img.bytes : 0u;
 
     const int grp = threadIdx.x / G;
@@ -184,44 +198,86 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
     const int lane = threadIdx.x & 31;
     const int bar = grp + 1;
     const int groups = blockDim.x / G;
+    // A merged launch keeps the groups' shot slots ahead of their states.
+    const uint32_t misc_smem = kMulti ? 16u * static_cast<uint32_t>(groups) : 0u;
     uint8_t *st = kStateSmem
-        ? smem + image_smem + static_cast<size_t>(grp) * a.state_bytes
+        ? smem + image_smem + misc_smem + static_cast<size_t>(grp) * a.state_bytes
         : a.gstate + (static_cast<size_t>(blockIdx.x) * groups + grp) * a.state_bytes;
     // The group's shot counter slot always lives in shared memory.
-    volatile uint32_t *misc = kStateSmem
+    volatile uint32_t *misc = (kStateSmem && !kMulti)
         ? reinterpret_cast<volatile uint32_t *>(st + a.off_misc)
         : reinterpret_cast<volatile uint32_t *>(smem + image_smem + 16 * grp);
-    MsgT *beta = reinterpret_cast<MsgT *>(st + a.off_beta);
-    PairT *beta2 = reinterpret_cast<PairT *>(beta);
     // Message slots [ks, DC) of a split state: gbeta[(k - ks) * R + c].
-    const int ks = kSplit ? a.ks : DC;
-    const uint32_t ksR = static_cast<uint32_t>(ks) * static_cast<uint32_t>(R);
     MsgT *gbeta = kSplit ? reinterpret_cast<MsgT *>(a.gstate + (static_cast<size_t>(blockIdx.x) * groups + grp) *
                                                                   a.gbeta_bytes)
                          : nullptr;
     PairT *gbeta2 = reinterpret_cast<PairT *>(gbeta);
-    float *lam = reinterpret_cast<float *>(st + a.off_lam);
-    float2 *lam2 = reinterpret_cast<float2 *>(lam);
-    uint32_t *s_w = reinterpret_cast<uint32_t *>(st + a.off_s);
-    uint32_t *shat = reinterpret_cast<uint32_t *>(st + a.off_shat);
-    if (t == 0) {
-        beta[Mp] = Msg<MsgT>::store(0.0f);                // column-side padding message
-        lam[n] = __int_as_float(0x7f800000);              // check-side padding column
+
+    // Code-dependent values: bound once, or per shot in a merged launch.
+    int m, n, I, Mp, Np, R, mpairs, npairs, ks, W32, wm64, wn64;
+    uint32_t ksR, last_mask;
+    const uint16_t *ptab;
+    MsgT *beta;
+    PairT *beta2;
+    float *lam;
+    float2 *lam2;
+    uint32_t *s_w, *shat;
+    GraphT gr(a.img, kGraphSmem ? smem : a.image, a.surf, a.rnd, a.mu_tab, a.m, a.n);
+    auto bind = [&]() {
+        m = LBP_ARG(m);
+        n = LBP_ARG(n);
+        I = LBP_ARG(max_iter);
+        Mp = LBP_ARG(img.Mp);
+        Np = LBP_ARG(img.Np);
+        R = (kTab && a.tab_R > 0) ? a.tab_R : Mp + 2;
+        ptab = (kTab && a.off_ptab != 0u) ? reinterpret_cast<const uint16_t *>(smem + a.off_ptab) : nullptr;
+        mpairs = Mp >> 1;
+        npairs = Np >> 1;
+        if constexpr (kMulti) gr = GraphT(item->img, item->image, item->surf, item->rnd, item->mu_tab, m, n);
+        beta = reinterpret_cast<MsgT *>(st + LBP_ARG(off_beta));
+        beta2 = reinterpret_cast<PairT *>(beta);
+        ks = kSplit ? a.ks : DC;
+        ksR = static_cast<uint32_t>(ks) * static_cast<uint32_t>(R);
+        lam = reinterpret_cast<float *>(st + LBP_ARG(off_lam));
+        lam2 = reinterpret_cast<float2 *>(lam);
+        s_w = reinterpret_cast<uint32_t *>(st + LBP_ARG(off_s));
+        shat = reinterpret_cast<uint32_t *>(st + LBP_ARG(off_shat));
+        W32 = (m + 31) >> 5;
+        wm64 = (m + 63) >> 6;
+        wn64 = (n + 63) >> 6;
+        last_mask = (m & 31) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
+    };
+    if constexpr (!kMulti) {
+        bind();
+        if (t == 0) {
+            beta[Mp] = Msg<MsgT>::store(0.0f);                // column-side padding message
+            lam[n] = __int_as_float(0x7f800000);              // check-side padding column
+        }
     }
     __syncthreads();
-
-    const int W32 = (m + 31) >> 5;
-    const int wm64 = (m + 63) >> 6;
-    const int wn64 = (n + 63) >> 6;
-    const uint32_t last_mask = (m & 31) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
 
     while (true) {
         if (t == 0) misc[0] = atomicAdd(&a.counters[0], 1u);
         group_sync<G>(bar);
-        const uint32_t b = misc[0];
+        uint32_t b = misc[0];
         if (static_cast<int64_t>(b) >= a.num_shots) break;
+        if constexpr (kMulti) {
+            int lo = 0, hi = a.n_items - 1;              // last item with first <= b
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.items[mid].first <= static_cast<int64_t>(b)) lo = mid;
+                else hi = mid - 1;
+            }
+            item = a.items + lo;
+            b -= static_cast<uint32_t>(item->first);
+            bind();
+            if (t == 0) {
+                beta[Mp] = Msg<MsgT>::store(0.0f);
+                lam[n] = __int_as_float(0x7f800000);
+            }
+        }
 
-        const uint32_t *syn32 = reinterpret_cast<const uint32_t *>(a.syn + static_cast<size_t>(b) * wm64);
+        const uint32_t *syn32 = reinterpret_cast<const uint32_t *>(LBP_ARG(syn) + static_cast<size_t>(b) * wm64);
         for (int w = t; w < W32; w += G) {
             uint32_t x = __ldg(syn32 + w);
             if (w == W32 - 1) x &= last_mask;
@@ -236,13 +292,13 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
         bool converged = false;
         int it = 0;
         for (; it < I; ++it) {
-            const float f = scale_at(a.scale_mode, a.scale_const, it);
-            const bool lot = a.lottery && it >= a.lottery_skip && it < I - 1;
+            const float f = scale_at(LBP_ARG(scale_mode), LBP_ARG(scale_const), it);
+            const bool lot = LBP_ARG(lottery) && it >= LBP_ARG(lottery_skip) && it < I - 1;
             // The group's last warp (the least loaded in both phases) runs the
             // lottery; a random check is drawn while the other warps finish
             // their check-phase rounds.
             const bool lw = t >= G - 32;
-            const bool early = lottery_random_check(a.policy);
+            const bool early = lottery_random_check(LBP_ARG(policy));
             int cpre = -1;
             uint32_t u2pre = 0;
             LotteryPrep lp;          // index-image instantiations in shared memory only
@@ -301,12 +357,12 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     // the |lambda| comparison remains.
                     uint32_t u2 = 0;
                     const uint32_t *sp = shat + prev * W32;
-                    const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it,
-                                                          a.policy, lam, u2);
-                    lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, a.policy, m, R, a.magic);
+                    const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
+                                                          LBP_ARG(policy), lam, u2);
+                    lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, LBP_ARG(policy), m, R, LBP_ARG(magic));
                 } else {
-                    cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, a.seed, a.shot_offset + b, it,
-                                             a.policy, lam, u2pre);
+                    cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
+                                             LBP_ARG(policy), lam, u2pre);
                 }
             }
             group_sync<G>(bar);
@@ -355,7 +411,7 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                         for (int h = 0; h < 2; ++h) {
                             if ((h == 0 ? acc0 : acc1) <= 0.0f) {
                                 const unsigned o = h == 0 ? e0[k] : e1[k];
-                                const unsigned r = o - __umulhi(o, a.magic) * static_cast<unsigned>(R);
+                                const unsigned r = o - __umulhi(o, LBP_ARG(magic)) * static_cast<unsigned>(R);
                                 if (r < static_cast<unsigned>(m)) atomicXor(&sh_cur[r >> 5], 1u << (r & 31));
                             }
                         }
@@ -378,18 +434,18 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     if constexpr (kTab) {
                         if (!early) {
                             uint32_t u2 = 0;
-                            const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b,
-                                                                  it, a.policy, lam, u2);
-                            lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, a.policy, m, R, a.magic);
+                            const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b,
+                                                                  it, LBP_ARG(policy), lam, u2);
+                            lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, LBP_ARG(policy), m, R, LBP_ARG(magic));
                         }
                         const int vs = lottery_finish(lp, lam);
                         if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
                     } else {
                         if (!early)
-                            cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, a.seed, a.shot_offset + b, it, a.policy,
+                            cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it, LBP_ARG(policy),
                                                      lam, u2pre);
-                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, a.policy, lam, m, R,
-                                                              a.magic);
+                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, LBP_ARG(policy), lam, m, R,
+                                                              LBP_ARG(magic));
                         if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
                     }
                 }
@@ -402,35 +458,36 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
         {
             const int nw = G / 32;
             const int gw = t >> 5;
-            uint32_t *err32 = reinterpret_cast<uint32_t *>(a.err + static_cast<size_t>(b) * wn64);
+            uint32_t *err32 = reinterpret_cast<uint32_t *>(LBP_ARG(err) + static_cast<size_t>(b) * wn64);
             for (int w = gw; w < 2 * wn64; w += nw) {
                 const int v = w * 32 + lane;
                 const bool e = (v < n) && (lam[v] <= 0.0f);
                 const unsigned bits = __ballot_sync(0xffffffffu, e);
                 if (lane == 0) err32[w] = bits;
             }
-            if (a.llr) {
-                float *dst = a.llr + static_cast<size_t>(b) * n;
+            if (LBP_ARG(llr)) {
+                float *dst = LBP_ARG(llr) + static_cast<size_t>(b) * n;
                 for (int v = t; v < n; v += G) dst[v] = lam[v];
             }
             if (t == 0) {
-                a.conv[b] = converged ? 1 : 0;
-                a.iters[b] = converged ? it + 1 : I;
-                if (a.osd_out) a.osd_out[b] = LBP_OSD_NOT_RUN;
+                LBP_ARG(conv)[b] = converged ? 1 : 0;
+                LBP_ARG(iters)[b] = converged ? it + 1 : I;
+                if (LBP_ARG(osd_out)) LBP_ARG(osd_out)[b] = LBP_OSD_NOT_RUN;
             }
-            if (!converged && a.osd) {
+            if (!converged && LBP_ARG(osd)) {
                 if (t == 0) {
-                    const uint32_t slot = atomicAdd(&a.counters[1], 1u);
-                    a.osd_list[slot] = b;
+                    const uint32_t slot = atomicAdd(&LBP_ARG(counters)[1], 1u);
+                    LBP_ARG(osd_list)[slot] = b;
                     misc[1] = slot;
                 }
                 group_sync<G>(bar);
-                float *dst = a.osd_llr + static_cast<size_t>(misc[1]) * n;
+                float *dst = LBP_ARG(osd_llr) + static_cast<size_t>(misc[1]) * n;
                 for (int v = t; v < n; v += G) dst[v] = lam[v];
             }
         }
         group_sync<G>(bar);
     }
+#undef LBP_ARG
 }
 
 }  // namespace lbp

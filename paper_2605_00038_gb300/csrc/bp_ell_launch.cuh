@@ -6,9 +6,10 @@
 
 namespace lbp {
 
-template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename GraphT, bool SP = false>
+template <typename MsgT, int kRule, int G, int DC, int DV, bool GS, bool SS, typename GraphT, bool SP = false,
+          bool MU = false>
 int launch_graph_one(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
-    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, GraphT, kRule, SP>;
+    auto k = bp_ell_kernel<MsgT, G, DC, DV, GS, SS, GraphT, kRule, SP, MU>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(s.smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -117,8 +118,30 @@ int launch_round(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
     return LBP_ENOSYS;
 }
 
+// Merged launch over a work list of codes with the same degree bounds (min-sum
+// rule; 16-bit images read from global memory, states in shared memory).
+template <typename MsgT, int kRule, int DC, int DV>
+int launch_multi(const LaunchShape &s, const BpEllArgs &a, cudaStream_t st) {
+    if constexpr (kRule != LBP_RULE_MIN_SUM) {
+        return LBP_ENOSYS;
+    } else {
+        using GR = EllGraph<uint16_t, DC, DV>;
+        switch (s.G) {
+            case 64: return launch_graph_one<MsgT, kRule, 64, DC, DV, false, true, GR, false, true>(s, a, st);
+            case 128: return launch_graph_one<MsgT, kRule, 128, DC, DV, false, true, GR, false, true>(s, a, st);
+            case 192: return launch_graph_one<MsgT, kRule, 192, DC, DV, false, true, GR, false, true>(s, a, st);
+            default: return LBP_ENOSYS;
+        }
+    }
+}
+
 template <typename MsgT, int kRule>
 int launch_ell(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st) {
+    if (s.multi) {
+        if (DC == 6 && DV == 2) return launch_multi<MsgT, kRule, 6, 2>(s, a, st);
+        if (DC == 6 && DV == 3) return launch_multi<MsgT, kRule, 6, 3>(s, a, st);
+        return LBP_ENOSYS;
+    }
     if (s.round) return DC == 6 && DV == 2 ? launch_round<MsgT, kRule>(s, a, st) : LBP_ENOSYS;
     if (s.surface) return launch_surface<MsgT, kRule>(s, a, st);
     if (DC == 6 && DV == 2) return launch_ell_g<MsgT, kRule, 6, 2>(s, a, st);

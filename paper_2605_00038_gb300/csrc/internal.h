@@ -116,6 +116,10 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
                          void *ws, size_t ws_bytes, cudaStream_t stream, int groups, int G,
                          float *bp_ms, int graph = 0, bool alone = true);
 
+// Device workspace bytes of a merged launch of these items (0 if they cannot
+// share one); the buffer pointers are not looked at.
+size_t batch_workspace_size(const lbp_batch_item *items, int n_items);
+
 }  // namespace lbp
 
 struct lbp_code {

@@ -15,6 +15,7 @@ struct LaunchShape {
     bool surface;            // implicit surface-code graph (no index image)
     bool round;              // round-periodic graph (one round's index image)
     bool split;              // split state: ks message slots in shared memory, the rest in the workspace
+    bool multi;              // merged launch over the items of a work list
 };
 
 int launch_bp_ell_f32(const LaunchShape &s, const BpEllArgs &a, int DC, int DV, cudaStream_t st);

@@ -525,6 +525,72 @@ int check_launch() {
     return e == cudaSuccess ? LBP_OK : LBP_ECUDA;
 }
 
+// K_osd_warp then K_osd on the OSD queue that K_bp filled (counters[1]
+// shots in osd_list / osd_llr), for one code: shared by lbp_decode and by
+// each item of a merged launch.
+int launch_osd(const lbp_code *c, int64_t B, const uint64_t *syn, uint64_t *err, uint8_t *osd_out,
+               unsigned int *counters, uint8_t *base, const WsLayout &w, const OsdPlan &op, OsdWarpPlan wp,
+               uint32_t *osd_list, float *osd_llr, cudaStream_t stream, bool alone) {
+    int rc = LBP_OK;
+    if (wp.ok) {
+        OsdWarpPlan lp;
+        if (alone && plan_osd_lat(c, B, wp, &lp)) wp = lp;
+        OsdWarpArgs ow;
+        std::memset(&ow, 0, sizeof(ow));
+        ow.image = c->d_image;
+        ow.img = c->img;
+        ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.C = wp.C;
+        ow.syn = syn; ow.err = err; ow.osd_out = osd_out;
+        ow.counters = counters;
+        ow.osd_list = osd_list; ow.osd_llr = osd_llr;
+        ow.overflow = reinterpret_cast<uint32_t *>(base + w.overflow);
+        ow.slots = reinterpret_cast<uint64_t *>(base + w.slots);
+        ow.image_bytes = wp.image;
+        ow.region_bytes = wp.region;
+        ow.off_keys = wp.off_keys; ow.off_rflag = wp.off_rflag; ow.off_pivk = wp.off_pivk;
+        ow.off_tmp = wp.off_tmp; ow.off_hist = wp.off_hist;
+        ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
+        ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
+        ow.off_lb = wp.off_lb; ow.off_pool = wp.off_pool; ow.Cs = wp.Cs;
+        rc = wp.lat ? set_smem(osd_warp_kernel<1, true>, wp.smem)
+                    : set_smem(osd_warp_kernel<kOsdMaxWarps, false>, wp.smem);
+        if (rc) return rc;
+        void *tw = timing_begin(stream);
+        if (wp.lat) {
+            osd_warp_kernel<1, true><<<wp.grid, 32, wp.smem, stream>>>(ow);
+        } else {
+            osd_warp_kernel<kOsdMaxWarps, false><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
+        }
+        timing_end(tw, stream, kTimeOsd);
+        rc = check_launch();
+        if (rc) return rc;
+    }
+    OsdArgs o;
+    std::memset(&o, 0, sizeof(o));
+    o.m = c->m; o.n = c->n;
+    o.row_ptr = c->d_row_ptr; o.col_idx = c->d_col_idx;
+    o.syn = syn; o.err = err; o.osd_out = osd_out;
+    o.counters = counters;
+    o.count_slot = wp.ok ? 2 : 1;
+    o.qmap = wp.ok ? reinterpret_cast<const uint32_t *>(base + w.overflow) : nullptr;
+    o.osd_list = osd_list; o.osd_llr = osd_llr;
+    o.gmat = op.smem_mat ? nullptr : reinterpret_cast<uint64_t *>(base + w.osd_mat);
+    o.n_pad = op.n_pad; o.wn = op.wn;
+    o.off_keys = op.off_keys; o.off_inv = op.off_inv; o.off_flags = op.off_flags;
+    o.off_piv = op.off_piv; o.off_ebits = op.off_ebits; o.off_mat = op.off_mat;
+    rc = set_smem(op.smem_mat ? osd_kernel<true> : osd_kernel<false>, op.smem);
+    if (rc) return rc;
+    void *to = timing_begin(stream);
+    if (op.smem_mat) {
+        osd_kernel<true><<<op.grid, 1024, op.smem, stream>>>(o);
+    } else {
+        osd_kernel<false><<<op.grid, 1024, op.smem, stream>>>(o);
+    }
+    timing_end(to, stream, kTimeOsd);
+    rc = check_launch();
+    return rc;
+}
+
 }  // namespace
 
 namespace lbp {
@@ -613,7 +679,7 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
             e.img.bytes = c->rnd.bytes;
         }
         const LaunchShape shp{bp.grid, bp.groups, bp.G, bp.smem, bp.graph_smem, bp.state_smem, bp.idx32,
-                              bp.surface, bp.round, bp.split};
+                              bp.surface, bp.round, bp.split, false};
         const bool sp = prm->rule == LBP_RULE_SUM_PRODUCT;
         switch (prm->msg) {
             case LBP_MSG_F32:
@@ -644,64 +710,8 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     if (rc) return rc;
     rc = check_launch();
     if (rc) return rc;
-    if (prm->osd) {
-        if (wp.ok) {
-            OsdWarpPlan lp;
-            if (alone && plan_osd_lat(c, B, wp, &lp)) wp = lp;
-            OsdWarpArgs ow;
-            std::memset(&ow, 0, sizeof(ow));
-            ow.image = c->d_image;
-            ow.img = c->img;
-            ow.m = c->m; ow.n = c->n; ow.wn = wp.wn; ow.C = wp.C;
-            ow.syn = syn; ow.err = err; ow.osd_out = osd_out;
-            ow.counters = counters;
-            ow.osd_list = a.osd_list; ow.osd_llr = a.osd_llr;
-            ow.overflow = reinterpret_cast<uint32_t *>(base + w.overflow);
-            ow.slots = reinterpret_cast<uint64_t *>(base + w.slots);
-            ow.image_bytes = wp.image;
-            ow.region_bytes = wp.region;
-            ow.off_keys = wp.off_keys; ow.off_rflag = wp.off_rflag; ow.off_pivk = wp.off_pivk;
-            ow.off_tmp = wp.off_tmp; ow.off_hist = wp.off_hist;
-            ow.off_pivb = wp.off_pivb; ow.off_saug = wp.off_saug; ow.off_x = wp.off_x;
-            ow.off_pcol = wp.off_pcol; ow.off_prow = wp.off_prow; ow.off_pend = wp.off_pend;
-            ow.off_lb = wp.off_lb; ow.off_pool = wp.off_pool; ow.Cs = wp.Cs;
-            rc = wp.lat ? set_smem(osd_warp_kernel<1, true>, wp.smem)
-                        : set_smem(osd_warp_kernel<kOsdMaxWarps, false>, wp.smem);
-            if (rc) return rc;
-            void *tw = timing_begin(stream);
-            if (wp.lat) {
-                osd_warp_kernel<1, true><<<wp.grid, 32, wp.smem, stream>>>(ow);
-            } else {
-                osd_warp_kernel<kOsdMaxWarps, false><<<wp.grid, wp.warps * 32, wp.smem, stream>>>(ow);
-            }
-            timing_end(tw, stream, kTimeOsd);
-            rc = check_launch();
-            if (rc) return rc;
-        }
-        OsdArgs o;
-        std::memset(&o, 0, sizeof(o));
-        o.m = c->m; o.n = c->n;
-        o.row_ptr = c->d_row_ptr; o.col_idx = c->d_col_idx;
-        o.syn = syn; o.err = err; o.osd_out = osd_out;
-        o.counters = counters;
-        o.count_slot = wp.ok ? 2 : 1;
-        o.qmap = wp.ok ? reinterpret_cast<const uint32_t *>(base + w.overflow) : nullptr;
-        o.osd_list = a.osd_list; o.osd_llr = a.osd_llr;
-        o.gmat = op.smem_mat ? nullptr : reinterpret_cast<uint64_t *>(base + w.osd_mat);
-        o.n_pad = op.n_pad; o.wn = op.wn;
-        o.off_keys = op.off_keys; o.off_inv = op.off_inv; o.off_flags = op.off_flags;
-        o.off_piv = op.off_piv; o.off_ebits = op.off_ebits; o.off_mat = op.off_mat;
-        rc = set_smem(op.smem_mat ? osd_kernel<true> : osd_kernel<false>, op.smem);
-        if (rc) return rc;
-        void *to = timing_begin(stream);
-        if (op.smem_mat) {
-            osd_kernel<true><<<op.grid, 1024, op.smem, stream>>>(o);
-        } else {
-            osd_kernel<false><<<op.grid, 1024, op.smem, stream>>>(o);
-        }
-        timing_end(to, stream, kTimeOsd);
-        rc = check_launch();
-    }
+    if (prm->osd) rc = launch_osd(c, B, syn, err, osd_out, counters, base, w, op, wp,
+                                  a.osd_list, a.osd_llr, stream, alone);
     return rc;
 }
 
@@ -907,6 +917,188 @@ extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, i
     if (rc) return rc;
     if (!ok) { cudaGetLastError(); return LBP_ECUDA; }
     return LBP_OK;
+}
+
+// ---- Merged launch: one BP launch over the shots of several requests ------
+
+namespace {
+
+constexpr int kMaxBatchItems = 64;
+
+struct BatchPlan {
+    int n = 0, msg = 0, DC = 0, DV = 0, S = 0, G = 0, grid = 0;
+    int64_t total = 0;
+    size_t smem = 0;
+    uint32_t state_bytes = 0;
+    size_t off_items = 0, total_ws = 0;
+    size_t item_off[kMaxBatchItems];
+    WsLayout w[kMaxBatchItems];
+    OsdPlan op[kMaxBatchItems];
+    OsdWarpPlan wp[kMaxBatchItems];
+    uint32_t off_lam[kMaxBatchItems], off_s[kMaxBatchItems], off_shat[kMaxBatchItems];
+};
+
+// Plan a merged launch: every item valid and of one message type, the
+// min-sum rule, a 16-bit index image and the same degree bounds; the
+// groups' states sized for the largest code; workspace = the launch's
+// counters, the device copy of the item array, then each item's own
+// lbp_decode workspace (its OSD counters, queue and pools).
+int plan_batch(const lbp_batch_item *items, int n, BatchPlan *P, bool size_only = false) {
+    if (!items || n < 1 || n > kMaxBatchItems) return LBP_EINVAL;
+    P->n = n;
+    P->msg = items[0].params.msg;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
+    uint32_t maxst = 16;
+    for (int i = 0; i < n; ++i) {
+        const lbp_batch_item &it = items[i];
+        const int rc = check_common(it.code, &it.params, it.num_shots);
+        if (rc) return rc;
+        if (!size_only && it.num_shots > 0 && (!it.syndromes || !it.err_out || !it.converged || !it.iters_out))
+            return LBP_EINVAL;
+        if (it.code->device != dev) return LBP_EINVAL;
+        const lbp_code *c = it.code;
+        if (it.params.msg != P->msg || it.params.rule != LBP_RULE_MIN_SUM) return LBP_ENOSYS;
+        if (!c->d_ell || c->ell.idx_bytes != 2) return LBP_ENOSYS;
+        if (i == 0) { P->DC = c->ell.DC; P->DV = c->ell.DV; }
+        if (c->ell.DC != P->DC || c->ell.DV != P->DV) return LBP_ENOSYS;
+        const int W32 = (c->m + 31) / 32;
+        const int R = c->ell.Mp + 2;
+        uint32_t o = align16u(static_cast<uint32_t>(msg_bytes(P->msg)) * P->DC * R);
+        P->off_lam[i] = o;  o = align16u(o + 4u * (c->ell.Np + 2));
+        P->off_s[i] = o;    o = align16u(o + 4u * W32);
+        P->off_shat[i] = o; o = align16u(o + 12u * W32);
+        if (o > maxst) maxst = o;
+        P->total += it.num_shots;
+    }
+    if (P->total > (1ll << 31)) return LBP_EINVAL;
+    const lbp_code *c0 = items[0].code;
+    P->state_bytes = maxst;
+    // Groups per CTA: as many states (plus their 16-byte shot slots) as fit,
+    // at most 15 named barriers; threads per group: the widest of 192, 128, 64
+    // that keeps the CTA at 1024 threads or fewer.
+    const size_t budget = static_cast<size_t>(c0->smem_optin);
+    int S = static_cast<int>(budget / (static_cast<size_t>(maxst) + 16));
+    if (S < 1) return LBP_ENOSYS;
+    if (S > 15) S = 15;
+    int G = 192;
+    while (G > 64 && S * G > 1024) G = G == 192 ? 128 : 64;
+    if (S * G > 1024) S = 1024 / G;
+    P->S = S;
+    P->G = G;
+    P->smem = static_cast<size_t>(S) * (16 + maxst);
+    const int64_t need = (P->total + S - 1) / S;
+    P->grid = static_cast<int>(need < c0->sm_count ? need : c0->sm_count);
+    if (P->grid < 1) P->grid = 1;
+    size_t off = align256(256);
+    P->off_items = off;
+    off = align256(off + sizeof(BpEllArgs) * n);
+    for (int i = 0; i < n; ++i) {
+        const lbp_batch_item &it = items[i];
+        if (it.params.osd) {
+            int rc = plan_osd(it.code, it.num_shots, &P->op[i]);
+            if (rc) return rc;
+            plan_osd_warp(it.code, it.num_shots, &P->wp[i]);
+        }
+        P->w[i] = layout(it.code, &it.params, it.num_shots, it.params.osd ? &P->op[i] : nullptr,
+                         it.params.osd ? &P->wp[i] : nullptr, nullptr);
+        P->item_off[i] = off;
+        off = align256(off + P->w[i].total);
+    }
+    P->total_ws = off;
+    return LBP_OK;
+}
+
+}  // namespace
+
+namespace lbp {
+
+size_t batch_workspace_size(const lbp_batch_item *items, int n_items) {
+    BatchPlan P;
+    if (plan_batch(items, n_items, &P, true)) return 0;
+    return P.total_ws;
+}
+
+}  // namespace lbp
+
+extern "C" size_t lbp_batch_workspace_size(const lbp_batch_item *items, int32_t n_items) {
+    return lbp::batch_workspace_size(items, n_items);
+}
+
+extern "C" int lbp_decode_batch(const lbp_batch_item *items, int32_t n_items, void *workspace,
+                                size_t workspace_bytes, void *stream) {
+    BatchPlan P;
+    int rc = plan_batch(items, n_items, &P);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < P.total_ws) return LBP_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return LBP_EINVAL;
+    if (P.total == 0) return LBP_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    unsigned int *counters = reinterpret_cast<unsigned int *>(base);
+    if (cudaMemsetAsync(counters, 0, 256, st) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
+    std::vector<BpEllArgs> h(static_cast<size_t>(n_items));
+    int64_t first = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const lbp_batch_item &it = items[i];
+        const lbp_code *c = it.code;
+        uint8_t *ib = base + P.item_off[i];
+        unsigned int *ictr = reinterpret_cast<unsigned int *>(ib + P.w[i].counters);
+        if (cudaMemsetAsync(ictr, 0, 256, st) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
+        BpEllArgs &e = h[i];
+        std::memset(&e, 0, sizeof(e));
+        e.image = c->d_ell;
+        e.img = c->ell;
+        e.m = c->m; e.n = c->n;
+        e.max_iter = it.params.max_iter; e.scale_mode = it.params.scale_mode; e.scale_const = it.params.scale_const;
+        e.lottery = it.params.lottery; e.lottery_skip = it.params.lottery_skip; e.osd = it.params.osd;
+        e.policy = it.params.lottery_policy; e.rule = it.params.rule;
+        e.seed = it.params.seed; e.shot_offset = it.params.shot_offset;
+        e.num_shots = it.num_shots;
+        e.syn = it.syndromes; e.err = it.err_out; e.conv = it.converged; e.osd_out = it.osd_out;
+        e.iters = it.iters_out; e.llr = nullptr;
+        e.counters = ictr;
+        e.osd_list = it.params.osd ? reinterpret_cast<uint32_t *>(ib + P.w[i].osd_list) : nullptr;
+        e.osd_llr = it.params.osd ? reinterpret_cast<float *>(ib + P.w[i].osd_llr) : nullptr;
+        e.state_bytes = P.state_bytes;
+        e.off_beta = 0; e.off_lam = P.off_lam[i]; e.off_s = P.off_s[i]; e.off_shat = P.off_shat[i];
+        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
+        e.first = first;
+        first += it.num_shots;
+    }
+    BpEllArgs *d_items = reinterpret_cast<BpEllArgs *>(base + P.off_items);
+    // Pageable source: the call returns once the array is staged for the copy.
+    if (cudaMemcpyAsync(d_items, h.data(), sizeof(BpEllArgs) * h.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return LBP_ECUDA;
+    }
+    BpEllArgs a = h[0];                       // item 0's image and sizes, for the kernel's prologue
+    a.counters = counters;
+    a.num_shots = P.total;
+    a.state_bytes = P.state_bytes;
+    a.items = d_items;
+    a.n_items = n_items;
+    const LaunchShape shp{P.grid, P.S, P.G, P.smem, false, true, false, false, false, false, true};
+    void *tk = timing_begin(st);
+    switch (P.msg) {
+        case LBP_MSG_F32: rc = launch_bp_ell_f32(shp, a, P.DC, P.DV, st); break;
+        case LBP_MSG_F16: rc = launch_bp_ell_f16(shp, a, P.DC, P.DV, st); break;
+        default: rc = launch_bp_ell_i8(shp, a, P.DC, P.DV, st); break;
+    }
+    timing_end(tk, st, kTimeBp);
+    if (rc) return rc;
+    rc = check_launch();
+    if (rc) return rc;
+    for (int i = 0; i < n_items && rc == LBP_OK; ++i) {
+        const lbp_batch_item &it = items[i];
+        if (!it.params.osd || it.num_shots == 0) continue;
+        uint8_t *ib = base + P.item_off[i];
+        rc = launch_osd(it.code, it.num_shots, it.syndromes, it.err_out, it.osd_out,
+                        reinterpret_cast<unsigned int *>(ib + P.w[i].counters), ib, P.w[i], P.op[i], P.wp[i],
+                        h[i].osd_list, h[i].osd_llr, st, false);
+    }
+    return rc;
 }
 
 extern "C" int lbp_code_tuned(const lbp_code *code, int32_t msg, int32_t rule, int32_t *groups, int32_t *G,

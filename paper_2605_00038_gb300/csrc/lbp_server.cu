@@ -24,6 +24,13 @@
 //    block scheduler starts it ahead of queued chunks of larger requests.
 // lbp_server_configure sets both.
 //
+// Merged launches (lbp_server_set_batching): the scheduler takes the oldest
+// waiting request and later ones that can share its launch (same message
+// type, min-sum rule, codes of one degree bound) and decodes all of them with
+// lbp_decode_batch, one BP launch over their shots on one stream, so many
+// small requests of different codes fill the GPU together instead of each
+// holding a launch of its own.
+//
 // The arena is one cudaMalloc made at creation; admission uses first-fit over
 // it, so no allocation happens while serving.
 #include <algorithm>
@@ -66,7 +73,8 @@ struct Slot {
     cudaStream_t stream_hi = nullptr;   // highest priority
     cudaEvent_t done = nullptr;
     bool busy = false;
-    Request req;
+    Request req;                        // one request, or the first of a merged launch
+    std::vector<Request> more;          // the other requests of a merged launch
 };
 
 // First-fit allocator over [0, size).
@@ -145,6 +153,7 @@ struct lbp_server {
     int64_t next_ticket = 1;
     int64_t chunk_work = int64_t(16) << 20;   // edge-shots per launch (0: one launch per request)
     bool priority = true;                      // single-launch requests on the high-priority stream
+    int batch_items = 0;                       // merged launches of up to this many requests (0: off)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
@@ -193,6 +202,133 @@ void launch(lbp_server *s, int si) {
     cudaEventRecord(sl.done, st);
 }
 
+// Device buffers of one request of a merged launch (no workspace of its own).
+struct BufLayout {
+    size_t syn, err, conv, osd, iters, total;
+};
+
+BufLayout buf_layout(const lbp_code *c, int64_t B) {
+    const size_t wm = (c->m + 63) / 64, wn = (c->n + 63) / 64;
+    BufLayout L;
+    size_t off = 0;
+    L.syn = off;   off = al256(off + 8 * wm * B);
+    L.err = off;   off = al256(off + 8 * wn * B);
+    L.conv = off;  off = al256(off + B);
+    L.osd = off;   off = al256(off + B);
+    L.iters = off; off = al256(off + 4 * B);
+    L.total = off;
+    return L;
+}
+
+// Whether r can join a merged launch whose first request is f.
+bool mergeable(const Request &f, const Request &r) {
+    return r.params.msg == f.params.msg && r.params.rule == LBP_RULE_MIN_SUM && f.params.rule == LBP_RULE_MIN_SUM &&
+           r.code->d_ell && f.code->d_ell && r.code->ell.idx_bytes == 2 && f.code->ell.idx_bytes == 2 &&
+           r.code->ell.DC == f.code->ell.DC && r.code->ell.DV == f.code->ell.DV;
+}
+
+// Arena bytes of a merged launch: the requests' buffers, then the batch
+// workspace (0 if the requests cannot share a launch).
+size_t merged_bytes(const std::vector<const Request *> &g, std::vector<size_t> *offs, size_t *ws_off) {
+    std::vector<lbp_batch_item> items(g.size());
+    size_t off = 0;
+    offs->clear();
+    for (size_t i = 0; i < g.size(); ++i) {
+        offs->push_back(off);
+        off += buf_layout(g[i]->code, g[i]->shots).total;
+        lbp_batch_item &it = items[i];
+        std::memset(&it, 0, sizeof(it));
+        it.code = g[i]->code;
+        it.params = g[i]->params;
+        it.num_shots = g[i]->shots;
+    }
+    const size_t ws = lbp::batch_workspace_size(items.data(), static_cast<int>(items.size()));
+    if (ws == 0) return 0;
+    *ws_off = off;
+    return off + ws;
+}
+
+void launch_merged(lbp_server *s, int si) {
+    Slot &sl = s->slots[si];
+    std::vector<Request *> rs;
+    rs.push_back(&sl.req);
+    for (auto &r : sl.more) rs.push_back(&r);
+    std::vector<const Request *> g(rs.begin(), rs.end());
+    std::vector<size_t> offs;
+    size_t ws_off = 0;
+    const size_t total = merged_bytes(g, &offs, &ws_off);
+    uint8_t *base = s->arena_base + sl.req.arena_off;
+    cudaStream_t st = sl.stream;
+    int rc = total ? LBP_OK : LBP_ENOSYS;
+    std::vector<lbp_batch_item> items(rs.size());
+    for (size_t i = 0; rc == LBP_OK && i < rs.size(); ++i) {
+        const Request &r = *rs[i];
+        const BufLayout L = buf_layout(r.code, r.shots);
+        uint8_t *b = base + offs[i];
+        const size_t wm = (r.code->m + 63) / 64;
+        if (cudaMemcpyAsync(b + L.syn, r.syn, 8 * wm * r.shots, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = LBP_ECUDA;
+        lbp_batch_item &it = items[i];
+        it.code = r.code;
+        it.params = r.params;
+        it.num_shots = r.shots;
+        it.syndromes = reinterpret_cast<const uint64_t *>(b + L.syn);
+        it.err_out = reinterpret_cast<uint64_t *>(b + L.err);
+        it.converged = b + L.conv;
+        it.osd_out = b + L.osd;
+        it.iters_out = reinterpret_cast<int32_t *>(b + L.iters);
+    }
+    if (rc == LBP_OK)
+        rc = lbp_decode_batch(items.data(), static_cast<int32_t>(items.size()), base + ws_off, total - ws_off, st);
+    for (size_t i = 0; rc == LBP_OK && i < rs.size(); ++i) {
+        Request &r = *rs[i];
+        const BufLayout L = buf_layout(r.code, r.shots);
+        uint8_t *b = base + offs[i];
+        const size_t wn = (r.code->n + 63) / 64;
+        bool ok = cudaMemcpyAsync(r.err, b + L.err, 8 * wn * r.shots, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(r.conv, b + L.conv, r.shots, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(r.iters, b + L.iters, 4 * r.shots, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (r.osd) ok = ok && cudaMemcpyAsync(r.osd, b + L.osd, r.shots, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+        if (!ok) rc = LBP_ECUDA;
+    }
+    if (rc != LBP_OK) cudaGetLastError();
+    for (Request *r : rs) r->status = rc;
+    cudaEventRecord(sl.done, st);
+}
+
+// Admit the oldest waiting request with the later requests that can share
+// its launch (up to batch_items, oldest first, as long as the arena has room
+// for all of them) into slot si.  Returns false when nothing could be admitted.
+bool admit_merged(lbp_server *s, int si) {
+    const Request &f = s->waiting.front();
+    std::vector<size_t> pick{0};
+    for (size_t i = 1; i < s->waiting.size() && static_cast<int>(pick.size()) < s->batch_items; ++i)
+        if (mergeable(f, s->waiting[i])) pick.push_back(i);
+    while (!pick.empty()) {
+        std::vector<const Request *> g;
+        for (size_t i : pick) g.push_back(&s->waiting[i]);
+        std::vector<size_t> offs;
+        size_t ws_off = 0;
+        const size_t bytes = merged_bytes(g, &offs, &ws_off);
+        size_t off = 0;
+        if (bytes && s->arena.alloc(bytes, &off)) {
+            Slot &sl = s->slots[si];
+            sl.req = s->waiting[pick[0]];
+            sl.req.arena_off = off;
+            sl.req.arena_bytes = bytes;
+            sl.req.slot = si;
+            sl.more.clear();
+            for (size_t k = 1; k < pick.size(); ++k) sl.more.push_back(s->waiting[pick[k]]);
+            for (size_t k = pick.size(); k-- > 0;) s->waiting.erase(s->waiting.begin() + static_cast<long>(pick[k]));
+            sl.busy = true;
+            launch_merged(s, si);
+            return true;
+        }
+        pick.pop_back();                     // smaller group, or wait for memory
+    }
+    return false;
+}
+
 void run(lbp_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
@@ -208,11 +344,19 @@ void run(lbp_server *s) {
                 cudaGetLastError();
                 sl.req.status = LBP_ECUDA;
             }
-            const double lat = std::chrono::duration<double>(Clock::now() - sl.req.submitted).count();
+            const auto now = Clock::now();
+            const double lat = std::chrono::duration<double>(now - sl.req.submitted).count();
             s->finished[sl.req.ticket] = {sl.req.status, lat};
             s->arena.release(sl.req.arena_off, sl.req.arena_bytes);
             s->completed += 1;
             s->shots_done += sl.req.shots;
+            for (const Request &r : sl.more) {
+                const int st = q == cudaSuccess ? r.status : LBP_ECUDA;
+                s->finished[r.ticket] = {st, std::chrono::duration<double>(now - r.submitted).count()};
+                s->completed += 1;
+                s->shots_done += r.shots;
+            }
+            sl.more.clear();
             sl.busy = false;
             progressed = true;
         }
@@ -223,6 +367,12 @@ void run(lbp_server *s) {
             for (size_t i = 0; i < s->slots.size(); ++i)
                 if (!s->slots[i].busy) { free_slot = static_cast<int>(i); break; }
             if (free_slot < 0) break;
+            if (s->batch_items > 0 && s->waiting.front().params.rule == LBP_RULE_MIN_SUM &&
+                s->waiting.front().code->d_ell && s->waiting.front().code->ell.idx_bytes == 2) {
+                if (!admit_merged(s, free_slot)) break;           // wait for memory to free up
+                progressed = true;
+                continue;
+            }
             Request &r = s->waiting.front();
             Layout L;
             request_layout(r.code, &r.params, r.shots, chunk_shots(r.code, s->chunk_work, r.shots), &L);
@@ -296,6 +446,13 @@ extern "C" int lbp_server_configure(lbp_server *s, int64_t chunk_work, int prior
     std::lock_guard<std::mutex> lk(s->mu);
     s->chunk_work = chunk_work;
     s->priority = priority != 0;
+    return LBP_OK;
+}
+
+extern "C" int lbp_server_set_batching(lbp_server *s, int32_t max_items) {
+    if (!s || max_items < 0 || max_items > 64) return LBP_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->batch_items = max_items;
     return LBP_OK;
 }
 

@@ -31,6 +31,7 @@ EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_in
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
             "lbp_server_wait", "lbp_server_destroy", "lbp_graph_create", "lbp_graph_launch",
             "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_probe_smem",
+            "lbp_batch_workspace_size", "lbp_decode_batch", "lbp_server_set_batching",
             "lbp_strerror"]
 
 
@@ -41,6 +42,12 @@ class lbp_params(ctypes.Structure):
                 ("msg", ctypes.c_int32), ("lottery_policy", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("shot_offset", ctypes.c_uint64),
                 ("rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class lbp_batch_item(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("params", lbp_params), ("num_shots", ctypes.c_int64),
+                ("syndromes", ctypes.c_void_p), ("err_out", ctypes.c_void_p), ("converged", ctypes.c_void_p),
+                ("osd_out", ctypes.c_void_p), ("iters_out", ctypes.c_void_p)]
 
 
 class LbpError(RuntimeError):
@@ -78,6 +85,12 @@ def lib():
         L.lbp_code_options.argtypes = [vp, vp, vp, vp, vp, vp]
         L.lbp_probe_smem.restype = ctypes.c_int
         L.lbp_probe_smem.argtypes = [i32, vp, vp, vp]
+        L.lbp_batch_workspace_size.restype = sz
+        L.lbp_batch_workspace_size.argtypes = [vp, i32]
+        L.lbp_decode_batch.restype = ctypes.c_int
+        L.lbp_decode_batch.argtypes = [vp, i32, vp, sz, vp]
+        L.lbp_server_set_batching.restype = ctypes.c_int
+        L.lbp_server_set_batching.argtypes = [vp, i32]
         L.lbp_code_rounds.restype = ctypes.c_int
         L.lbp_code_rounds.argtypes = [vp, vp, vp, vp, vp]
         L.lbp_workspace_size.restype = sz
@@ -299,6 +312,25 @@ def lbp_decode_noalloc(code: Code, params: lbp_params, num_shots: int, syndromes
            "lbp_decode_noalloc")
 
 
+def batch_items(entries):
+    """ctypes array of lbp_batch_item from (code, params, num_shots, syndromes,
+    err_out, converged, osd_out, iters_out) tuples of CUDA tensors."""
+    arr = (lbp_batch_item * len(entries))()
+    for i, (code, prm, B, syn, err, conv, osd, iters) in enumerate(entries):
+        arr[i] = lbp_batch_item(code.ptr, prm, B, _dptr(syn), _dptr(err), _dptr(conv), _dptr(osd), _dptr(iters))
+    return arr
+
+
+def lbp_batch_workspace_size(items) -> int:
+    return int(lib().lbp_batch_workspace_size(items, len(items)))
+
+
+def lbp_decode_batch(items, workspace, stream=None):
+    """One BP launch over the shots of several requests (items from batch_items)."""
+    _check(lib().lbp_decode_batch(items, len(items), _dptr(workspace), workspace.numel() * workspace.element_size(),
+                                  _stream_handle(stream)), "lbp_decode_batch")
+
+
 def lbp_timing_enable(on: bool):
     _check(lib().lbp_timing_enable(int(bool(on))), "lbp_timing_enable")
 
@@ -375,6 +407,10 @@ def lbp_server_create(arena_bytes: int, max_inflight: int) -> Server:
 def lbp_server_configure(server: Server, chunk_work: int, priority: bool = True):
     _check(lib().lbp_server_configure(server.ptr, int(chunk_work), int(bool(priority))),
            "lbp_server_configure")
+
+
+def lbp_server_set_batching(server: Server, max_items: int):
+    _check(lib().lbp_server_set_batching(server.ptr, int(max_items)), "lbp_server_set_batching")
 
 
 def lbp_server_submit(server: Server, code: Code, params: lbp_params, num_shots: int, syndromes,

@@ -102,3 +102,15 @@ def test_graph_server_and_tuned_reject_null_without_gpu(L):
     assert L.lbp_server_configure(None, 1 << 20, 1) == lbp.LBP_EINVAL
     g = ctypes.c_int32()
     assert L.lbp_code_tuned(None, 0, 0, None, ctypes.byref(g), None) == lbp.LBP_EINVAL
+
+
+def test_batch_rejects_bad_item_counts_without_a_gpu(L):
+    """lbp_decode_batch / lbp_batch_workspace_size check the item count before
+    any CUDA call."""
+    items = (lbp.lbp_batch_item * 1)()
+    assert L.lbp_batch_workspace_size(items, 0) == 0
+    assert L.lbp_batch_workspace_size(items, 65) == 0
+    assert L.lbp_batch_workspace_size(None, 1) == 0
+    assert L.lbp_decode_batch(items, 0, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_decode_batch(None, 1, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_server_set_batching(None, 4) == lbp.LBP_EINVAL

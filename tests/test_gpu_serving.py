@@ -69,14 +69,16 @@ def _device_bytes(dec, r):
     return lbp.lbp_workspace_size(dec.code, prm, B) + io + 256
 
 
-@pytest.mark.parametrize("tight,inflight,chunk", [(False, 8, None), (True, 4, None), (False, 8, 30000),
-                                                  (True, 3, 0)])
-def test_results_alone_equal_results_in_the_mix(tight, inflight, chunk):
+@pytest.mark.parametrize("tight,inflight,chunk,merge", [(False, 8, None, 0), (True, 4, None, 0),
+                                                        (False, 8, 30000, 0), (True, 3, 0, 0),
+                                                        (False, 8, None, 16), (True, 4, None, 6)])
+def test_results_alone_equal_results_in_the_mix(tight, inflight, chunk, merge):
     """tight: the arena holds about 1.5 of the largest request, so admission
     waits for memory, not for a free stream.  chunk: the server's chunk_work
     (None: default; 30000 edge-shots splits most requests into many launches
     on normal- and high-priority streams; 0: one launch per request, no
-    priorities)."""
+    priorities).  merge: lbp_server_set_batching (requests of one message
+    type and degree bound -- surface or BB codes -- share one BP launch)."""
     codes = _codes()
     decs = [Decoder(h, pri) for h, pri in codes]
     reqs = _requests(codes, 40, seed=int(tight))
@@ -85,6 +87,8 @@ def test_results_alone_equal_results_in_the_mix(tight, inflight, chunk):
     srv = lbp.lbp_server_create(arena, inflight)
     if chunk is not None:
         lbp.lbp_server_configure(srv, chunk, chunk != 0)
+    if merge:
+        lbp.lbp_server_set_batching(srv, merge)
     bufs = []
     for r in reqs:
         h = codes[r["ci"]][0]
