@@ -476,6 +476,7 @@ def run_gpu(args):
         line["bb144_osd_fp16"] = run_c3_leg()
         line["serving"] = run_serving()
         line["serving_one_launch_fifo"] = run_serving(policy=(0, False))
+        line["serving_merged"] = run_serving(merge=16)
         line["matched_ler"] = run_matched()
         line["precision_d7"] = run_precision()
         line["lottery_design_space"] = run_policies()
@@ -783,7 +784,7 @@ def run_c3_leg(shots: int = 1_000_000, oracle_shots: int = 100_000):
     return out
 
 
-def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11, policy=None):
+def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int = 11, policy=None, merge: int = 0):
     """Serving mix: Poisson arrivals of 1-4096-shot requests over ten resident
     codes (rotated surface space-time d = 5..17 with d rounds, BB 72/144/288
     code capacity) and five noise levels 1e-3..5e-3; Lottery BP + OSD-0,
@@ -793,7 +794,8 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     lottery's OSD invoke rate on these surface codes.  policy: None for the
     server's default scheduling (launches of at most 16 Mi edge-shots,
     single-launch requests on a high-priority stream), or (chunk_work,
-    priority) for lbp_server_configure."""
+    priority) for lbp_server_configure; merge > 0 lets the server put up to
+    that many compatible requests into one BP launch (lbp_server_set_batching)."""
     import torch
     from paper_2605_00038_gb300 import lbp
     from paper_2605_00038_gb300.decoder import Decoder
@@ -832,6 +834,8 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     srv = lbp.lbp_server_create(8 << 30, 16)
     if policy is not None:
         lbp.lbp_server_configure(srv, policy[0], policy[1])
+    if merge:
+        lbp.lbp_server_set_batching(srv, merge)
 
     def submit(r):
         return lbp.lbp_server_submit(srv, decs[(r["ci"], r["pi"])].code, r["prm"], r["B"], r["syn"],
@@ -848,7 +852,8 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     total_shots = sum(r["B"] for r in reqs)
     cap_req = len(reqs) / dt
     out = {"policy": ("chunk_work 16 Mi edge-shots, priority" if policy is None else
-                      "chunk_work %d, priority %d" % (policy[0], int(policy[1]))),
+                      "chunk_work %d, priority %d" % (policy[0], int(policy[1]))) +
+                     (", merged launches of up to %d requests" % merge if merge else ""),
            "codes": len(codes), "noise_levels": len(ps), "requests": len(reqs),
            "mean_request_shots": total_shots / len(reqs), "capacity_shots_per_s": total_shots / dt,
            "capacity_requests_per_s": cap_req, "rates": []}

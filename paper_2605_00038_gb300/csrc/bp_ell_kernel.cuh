@@ -35,11 +35,12 @@
 // memory (the image is L2-resident; the state goes to a per-group slice of the
 // workspace).  A state slightly too large for shared memory (the d=25
 // space-time code with binary32 messages) is split (kSplit): the posteriors,
-// syndrome words and the first ks message slots stay in shared memory, the
-// other slots go to the workspace.  The check phase moves those slots as
-// coalesced pairs; the column phase gathers them, which for a space-time
-// matrix touches only the measurement columns, whose messages of one round
-// block are contiguous.
+// syndrome words and the first DC - 2 message slots stay in shared memory,
+// the last two slots go to the workspace.  The check phase moves those slots
+// as coalesced pairs; with the slot-aligned image of a space-time matrix
+// they hold exactly the measurement columns' messages, so the column phase
+// reads each column's messages from one place (those of one round block are
+// contiguous).
 // Lottery: the group's last warp, which has the fewest rounds in both phases,
 // runs it.  For the random-check policies it draws c* right after its
 // check-phase rounds (c* depends only on s_hat(i-1), s and the draw).  The
@@ -82,10 +83,9 @@ struct BpEllArgs {
     uint32_t state_bytes;
     uint32_t off_beta, off_lam, off_s, off_shat, off_misc;
     uint8_t *gstate;          // per-group state slices when not in shared memory
-    // Split state (kSplit): message slots [0, ks) live in shared memory with
-    // the rest of the shot's state, slots [ks, DC) in a per-group workspace
-    // slice of gbeta_bytes at gstate.
-    int32_t ks;
+    // Split state (kSplit): message slots [0, DC - 2) live in shared memory
+    // with the rest of the shot's state, the last two slots in a per-group
+    // workspace slice of gbeta_bytes at gstate.
     uint32_t gbeta_bytes;
     uint32_t magic;           // floor(2^32 / R) + 1: offset / R by multiply-high
     SurfaceDesc surf;         // implicit graph (SurfaceGraph)
@@ -175,6 +175,10 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
     static_assert(!kMulti || (GraphT::kEll && !kGraphSmem && kStateSmem && !kSplit),
                   "a merged launch reads its images from global memory and keeps its states in shared memory");
     using PairT = typename Pair<MsgT>::type;
+    // Message slots a split state keeps in shared memory: all but the last two
+    // (which a slot-aligned space-time image reserves for the measurement
+    // columns).
+    constexpr int kKs = kSplit ? DC - 2 : DC;
     extern __shared__ __align__(16) uint8_t smem[];
     if (kGraphSmem) {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
         if constexpr (kMulti) gr = GraphT(item->img, item->image, item->surf, item->rnd, item->mu_tab, m, n);
         beta = reinterpret_cast<MsgT *>(st + LBP_ARG(off_beta));
         beta2 = reinterpret_cast<PairT *>(beta);
-        ks = kSplit ? a.ks : DC;
+        ks = kKs;
         ksR = static_cast<uint32_t>(ks) * static_cast<uint32_t>(R);
         lam = reinterpret_cast<float *>(st + LBP_ARG(off_lam));
         lam2 = reinterpret_cast<float2 *>(lam);
@@ -376,6 +380,15 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     pfm = gr.mu2_ldg(t);
                 }
             }
+            // A split state over a slot-aligned image: column pairs below
+            // q_lo have every message in shared memory, pairs in [q_hi, q_end)
+            // every message in the workspace; the one or two pairs between
+            // (a round and a measurement column, or the padding column) pick
+            // per message.  Without the aligned layout every pair picks.
+            const int meas0 = kSplit ? LBP_ARG(img.meas0) : 0;
+            const int q_lo = meas0 > 0 ? meas0 >> 1 : 0;
+            const int q_hi = meas0 > 0 ? (meas0 + 1) >> 1 : npairs;
+            const int q_end = meas0 > 0 ? n >> 1 : npairs;
             for (int q = t; q < npairs; q += G) {
                 uint32_t e0[DV], e1[DV];
                 float2 mm;
@@ -391,14 +404,25 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     mm = gr.mu2(q);
                 }
                 float acc0 = mm.x, acc1 = mm.y;
-                #pragma unroll
-                for (int k = 0; k < DV; ++k) {
-                    if (kSplit) {
-                        const MsgT m0 = e0[k] >= ksR ? gbeta[e0[k] - ksR] : beta[e0[k]];
-                        const MsgT m1 = e1[k] >= ksR ? gbeta[e1[k] - ksR] : beta[e1[k]];
-                        acc0 = __fadd_rn(acc0, Msg<MsgT>::load(m0));
-                        acc1 = __fadd_rn(acc1, Msg<MsgT>::load(m1));
+                if (kSplit && q >= q_lo) {
+                    if (q >= q_hi && q < q_end) {
+                        #pragma unroll
+                        for (int k = 0; k < DV; ++k) {
+                            acc0 = __fadd_rn(acc0, Msg<MsgT>::load(gbeta[e0[k] - ksR]));
+                            acc1 = __fadd_rn(acc1, Msg<MsgT>::load(gbeta[e1[k] - ksR]));
+                        }
                     } else {
+                        #pragma unroll
+                        for (int k = 0; k < DV; ++k) {
+                            const MsgT m0 = e0[k] >= ksR ? gbeta[e0[k] - ksR] : beta[e0[k]];
+                            const MsgT m1 = e1[k] >= ksR ? gbeta[e1[k] - ksR] : beta[e1[k]];
+                            acc0 = __fadd_rn(acc0, Msg<MsgT>::load(m0));
+                            acc1 = __fadd_rn(acc1, Msg<MsgT>::load(m1));
+                        }
+                    }
+                } else {
+                    #pragma unroll
+                    for (int k = 0; k < DV; ++k) {
                         acc0 = __fadd_rn(acc0, Msg<MsgT>::load(beta[e0[k]]));
                         acc1 = __fadd_rn(acc1, Msg<MsgT>::load(beta[e1[k]]));
                     }

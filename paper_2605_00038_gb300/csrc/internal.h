@@ -38,6 +38,11 @@ struct EllImage {
     int32_t DC, DV;
     int32_t Mp, Np;          // m and n rounded up to even (paired accesses)
     int32_t idx_bytes;       // 2 (uint16 indices) or 4 (uint32, image read from global memory)
+    // Slot-aligned layout (space-time matrices whose image and FP32 state do
+    // not fit shared memory together): every check's round columns in slots
+    // 0 .. DC-3, its measurement columns of blocks t-1 and t in slots DC-2
+    // and DC-1; meas0 = the first measurement column (0: not aligned).
+    int32_t meas0;
 };
 
 // Space-time matrix of the unrotated surface code (Eq. 1 with one check type

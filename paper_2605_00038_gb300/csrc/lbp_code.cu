@@ -468,6 +468,30 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
             off = tab_bytes;
         }
         e.bytes = off;
+        // Slot-aligned layout for a space-time matrix of Eq. 1 whose image and
+        // FP32 state do not fit shared memory together (the kernel then reads
+        // the image from global memory and may split the state): a check's
+        // round columns fill slots 0 .. DC-3 (padded with column n), its
+        // measurement column of block t-1 goes to slot DC-2 and that of block
+        // t to slot DC-1.  Every message of a measurement column then sits in
+        // the last two slots, which a split state keeps in the workspace, and
+        // every message of a round column in the others.  The check update
+        // and the lottery do not depend on slot order, so results are the same.
+        lbp::RoundDesc rd;
+        std::vector<uint8_t> rdimg;
+        const bool aligned = !c->tab_R && ell_dc == 6 && ell_dv == 2 && fits16 &&
+                             static_cast<size_t>(off) + lbp::ell_state_bytes(4, ell_dc, R, Np, m) >
+                                 static_cast<size_t>(c->smem_optin) &&
+                             detect_round(m, n, row_ptr, col_idx, mu, ell_dc, ell_dv, Mp, &rd, &rdimg);
+        const int64_t M0 = aligned ? static_cast<int64_t>(rd.T) * rd.nr : 0;
+        e.meas0 = static_cast<int32_t>(M0);
+        // Slot of column v in row r.
+        auto slot_of = [&](int32_t r, int32_t v, int32_t k_sorted) -> int32_t {
+            if (!aligned) return k_sorted;
+            if (v < M0) return k_sorted;                       // round columns come first, ascending
+            const int64_t blk = (v - M0) / rd.mr, t = r / rd.mr;
+            return blk == t ? ell_dc - 1 : ell_dc - 2;
+        };
         std::vector<uint8_t> img(off, 0);
         auto put = [&](uint32_t base, size_t i, uint32_t v) {
             if (ib == 2) reinterpret_cast<uint16_t *>(img.data() + base)[i] = static_cast<uint16_t>(v);
@@ -476,8 +500,10 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         float *mu_e = reinterpret_cast<float *>(img.data() + e.off_mu);
         for (int32_t r = 0; r < Mp; ++r) {
             const int32_t a = r < m ? row_ptr[r] : 0, deg = r < m ? row_ptr[r + 1] - a : 0;
-            for (int k = 0; k < e.DC; ++k)
-                put(e.off_cidx, static_cast<size_t>(k) * Mp + r, static_cast<uint32_t>(k < deg ? col_idx[a + k] : n));
+            for (int k = 0; k < e.DC; ++k) put(e.off_cidx, static_cast<size_t>(k) * Mp + r, static_cast<uint32_t>(n));
+            for (int k = 0; k < deg; ++k)
+                put(e.off_cidx, static_cast<size_t>(slot_of(r, col_idx[a + k], k)) * Mp + r,
+                    static_cast<uint32_t>(col_idx[a + k]));
         }
         for (int32_t v = 0; v < Np; ++v) {
             const int32_t a = v < n ? col_ptr[v] : 0, deg = v < n ? col_ptr[v + 1] - a : 0;
@@ -485,7 +511,7 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
                 uint32_t ent = static_cast<uint32_t>(Mp);         // padding: message beta[0][Mp] = +0
                 if (k < deg) {
                     const int32_t r = csc_row[a + k];
-                    const int32_t slot = csc_edge[a + k] - row_ptr[r];
+                    const int32_t slot = slot_of(r, v, csc_edge[a + k] - row_ptr[r]);
                     ent = static_cast<uint32_t>(slot * R + r);
                 }
                 put(e.off_vent, static_cast<size_t>(k) * Np + v, ent);

@@ -212,16 +212,17 @@ int plan_bp(const lbp_code *c, int msg, int rule, int64_t num_shots, BpPlan *out
             req_S = c->tuned_groups[mi];
             req_G = c->tuned_G[mi];
         }
-        // Split state: when one shot's state does not fit, the largest number
-        // of message slots that fits stays in shared memory with the
-        // posteriors and syndrome words (one shot per CTA of 512, 768 or 1024
-        // threads: the tuned or requested width, else 1024), the other slots
-        // go to a per-group workspace slice.  A request for several groups
+        // Split state: when one shot's state does not fit, all message slots
+        // but the last two stay in shared memory with the posteriors and
+        // syndrome words, if they fit (one shot per CTA of 512, 768 or 1024
+        // threads: the tuned or requested width, else 1024); the last two
+        // slots go to a per-group workspace slice.  A request for several groups
         // (S > 1) or for 256 threads keeps the whole state in the workspace.
         const int s_eff = req_G > 0 ? std::min(req_S > 0 ? req_S : 1, 1024 / req_G) : 1;
         const bool split_req = req_G == 0 || (s_eff <= 1 && (req_G == 512 || req_G == 768 || req_G == 1024));
         if (!p.state_smem && !p.idx32 && split_req) {
-            for (int ks = c->ell.DC - 1; ks >= 1; --ks) {
+            const int ks = c->ell.DC - 2;            // the last two slots go to the workspace
+            {
                 const uint32_t o = state_layout(c->ell.Mp + 2, ks);
                 if (o <= budget0) {
                     p.split = true;
@@ -665,7 +666,6 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
         e.state_bytes = a.state_bytes; e.off_beta = a.off_beta; e.off_lam = a.off_lam;
         e.off_s = a.off_s; e.off_shat = a.off_shat; e.off_misc = a.off_misc;
         e.gstate = (bp.state_smem && !bp.split) ? nullptr : base + w.gstate;
-        e.ks = bp.split ? bp.ks : 0;
         e.gbeta_bytes = bp.gbeta_bytes;
         const int R = bp.tab ? c->tab_R : c->ell.Mp + 2;
         e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(R) + 1);
