@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
         I = LBP_ARG(max_iter);
         Mp = LBP_ARG(img.Mp);
         Np = LBP_ARG(img.Np);
-        R = (kTab && a.tab_R > 0) ? a.tab_R : Mp + 2;
+        // The message row stride the image's offsets were built with: the
+        // bank-aware stride when the code has one (a merged launch reads such
+        // an image from global memory, without its pair table), else Mp + 2.
+        R = ((kTab || kMulti) && LBP_ARG(tab_R) > 0) ? LBP_ARG(tab_R) : Mp + 2;
         ptab = (kTab && a.off_ptab != 0u) ? reinterpret_cast<const uint16_t *>(smem + a.off_ptab) : nullptr;
         mpairs = Mp >> 1;
         npairs = Np >> 1;

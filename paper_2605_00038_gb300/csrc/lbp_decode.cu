@@ -963,7 +963,7 @@ int plan_batch(const lbp_batch_item *items, int n, BatchPlan *P, bool size_only 
         if (i == 0) { P->DC = c->ell.DC; P->DV = c->ell.DV; }
         if (c->ell.DC != P->DC || c->ell.DV != P->DV) return LBP_ENOSYS;
         const int W32 = (c->m + 31) / 32;
-        const int R = c->ell.Mp + 2;
+        const int R = c->tab_R > 0 ? c->tab_R : c->ell.Mp + 2;   // the stride of the image's offsets
         uint32_t o = align16u(static_cast<uint32_t>(msg_bytes(P->msg)) * P->DC * R);
         P->off_lam[i] = o;  o = align16u(o + 4u * (c->ell.Np + 2));
         P->off_s[i] = o;    o = align16u(o + 4u * W32);
@@ -1062,7 +1062,9 @@ extern "C" int lbp_decode_batch(const lbp_batch_item *items, int32_t n_items, vo
         e.osd_llr = it.params.osd ? reinterpret_cast<float *>(ib + P.w[i].osd_llr) : nullptr;
         e.state_bytes = P.state_bytes;
         e.off_beta = 0; e.off_lam = P.off_lam[i]; e.off_s = P.off_s[i]; e.off_shat = P.off_shat[i];
-        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(c->ell.Mp + 2) + 1);
+        const int R = c->tab_R > 0 ? c->tab_R : c->ell.Mp + 2;
+        e.tab_R = c->tab_R;
+        e.magic = static_cast<uint32_t>((1ull << 32) / static_cast<uint64_t>(R) + 1);
         e.first = first;
         first += it.num_shots;
     }
