@@ -48,7 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--shots", type=int, default=1 << 18, help="shots per step per rank")
+    ap.add_argument("--workload", choices=["d25", "d11"], default="d25",
+                    help="d25: the rotated d=25 space-time code, Lottery BP, FP32 (the headline); "
+                         "d11: the rotated d=11 space-time code, Lottery BP + OSD-0, FP32")
+    ap.add_argument("--shots", type=int, default=None,
+                    help="shots per step per rank (default 2^18 for d25, 10^6 for d11)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=6144, help="oracle shots for cpu_baseline")
@@ -137,9 +141,16 @@ def job_value(world: int, shots: int, steps: int, elapsed_ms_per_rank, dist=None
     return max_ms, world * shots * steps / (max_ms / 1e3)
 
 
-def workload(shots):
+def workload(shots, which: str = "d25"):
     from paper_2605_00038_gb300.inputs import workloads
-    return workloads.c5_d25_spacetime(msg=0, shots=shots)
+    if which == "d11":
+        return workloads.c2_d11_spacetime(shots=shots or 1_000_000, osd=1)
+    return workloads.c5_d25_spacetime(msg=0, shots=shots or (1 << 18))
+
+
+def code_text(w):
+    d = 25 if w.h.m == 7800 else 11
+    return "rotated surface d=%d, %d noisy rounds, space-time H %dx%d nnz %d" % (d, d, w.h.m, w.h.n, w.h.nnz)
 
 
 def state_bytes_per_iteration(h, msg_bytes):
@@ -171,7 +182,7 @@ def roofline_model(w, iters_total, shots):
 # 4,096-shot launch, divided by the shot-iterations it ran; the traffic of a
 # full launch scales with its shot-iterations.  Valid for the kernel sources
 # whose hash is recorded with it (None until captured).
-KBP_TRAFFIC = {"bytes_per_shot_iteration": None, "source_sha1": None}
+KBP_TRAFFIC = {"bytes_per_shot_iteration": 12.27, "source_sha1": "acf298ee388a"}
 
 
 def kbp_source_sha1():
@@ -260,7 +271,7 @@ def run_reference(args):
         return
     import oracle
     from paper_2605_00038_gb300.inputs import sampler
-    w = workload(args.shots)
+    w = workload(args.shots, args.workload)
     cores = os.cpu_count() or 1
     sample = max(1, min(args.ref_sample, w.shots))
     _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=sample * (args.steps + 1))
@@ -304,8 +315,9 @@ def run_gpu(args):
     from paper_2605_00038_gb300.decoder import Decoder
     from paper_2605_00038_gb300.inputs import sampler
 
-    w = workload(args.shots)
+    w = workload(args.shots, args.workload)
     B = w.shots
+    d25 = args.workload == "d25"
     dec = Decoder(w.h, w.priors, device="cuda:%d" % local)
     wm, wn = (w.h.m + 63) // 64, (w.h.n + 63) // 64
 
@@ -371,12 +383,11 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name,
-                   "code": "rotated surface d=25, 25 noisy rounds, space-time H %dx%d nnz %d"
-                           % (w.h.m, w.h.n, w.h.nnz),
-                   "noise": "iid p_data=p_meas=0.004", "shots_per_step_per_rank": B,
-                   "configuration_shots": N_BATCHES * B,
-                   "decoder": "lottery_bp(proposed rule, skip 6, adaptive scale, I=100), no OSD",
+        "config": {"workload": w.name, "code": code_text(w),
+                   "noise": "iid p_data=p_meas=%s" % ("0.004" if d25 else "0.003"),
+                   "shots_per_step_per_rank": B, "configuration_shots": N_BATCHES * B,
+                   "decoder": "lottery_bp(proposed rule, skip 6, adaptive scale, I=100)" +
+                              (", no OSD" if d25 else " + osd0"),
                    "msg": "f32",
                    "l2": "%d rotating input batches of %d MB syndromes, each > L2" % (
                        N_BATCHES, B * wm * 8 // 2 ** 20),
@@ -391,7 +402,7 @@ def run_gpu(args):
     alg_bytes = iters_per_step * b_it + B * io_bytes_per_shot(w.h)
     peak_gbs, peak_basis = hbm_peak_gbs()
     traffic = None
-    if KBP_TRAFFIC["bytes_per_shot_iteration"] and kbp_source_sha1() == KBP_TRAFFIC["source_sha1"]:
+    if d25 and KBP_TRAFFIC["bytes_per_shot_iteration"] and kbp_source_sha1() == KBP_TRAFFIC["source_sha1"]:
         traffic = KBP_TRAFFIC["bytes_per_shot_iteration"] * iters_per_step
     ops, _ = roofline_model(w, iters_per_step, B)
     line["roofline"] = {
@@ -459,7 +470,7 @@ def run_gpu(args):
         o = outs[0]
         step(0)
         torch.cuda.synchronize()
-        spec = evaluate.surface_spec(25, 25, w.h.n)
+        spec = evaluate.surface_spec(25, 25, w.h.n) if d25 else evaluate.surface_spec(11, 11, w.h.n)
         f = evaluate.logical_failures(spec, torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err,
                                       o.converged, o.osd)
         k = int(f.sum().item())
@@ -467,7 +478,7 @@ def run_gpu(args):
                            "note": "BP alone (no OSD in this configuration): an unconverged shot counts as a "
                                    "logical failure"}
 
-    if not args.no_extras and rank == 0 and world == 1:
+    if not args.no_extras and rank == 0 and world == 1 and d25:
         del outs, ws
         dec.close()
         torch.cuda.empty_cache()
@@ -483,7 +494,7 @@ def run_gpu(args):
         line["check_rule"] = run_sum_product()
     else:
         dec.close()
-    if not args.no_extras and rank == 0 and world == 1:
+    if not args.no_extras and rank == 0 and world == 1 and d25:
         import oracle
         cores = os.cpu_count() or 1
         S = sampler.unpack(syn_h[0][: args.cpu_sample], w.h.m)
