@@ -313,40 +313,18 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             // With the index image in global memory (L2), each trip's index
             // words are loaded one trip ahead, so their latency overlaps the
             // previous pair's work.
-            // A pair-ordered image also gives the trip's check pair, prefetched
-            // with its words.
             typename GraphT::IP pfc[DC];
-            int pfp = 0;
-            bool ord = false;
             if constexpr (kPf) {
-                ord = !kMulti && gr.ordered();
-                if (t < mpairs) {
-                    if (ord) {
-                        pfp = static_cast<int>(gr.pair_at(t));
-                        gr.pcols2_raw(t, pfc);
-                    } else {
-                        gr.cols2_raw(t, pfc);
-                    }
-                }
+                if (t < mpairs) gr.cols2_raw(t, pfc);
             }
             for (int ip = t; ip < mpairs; ip += G) {
-                int pr = (kTab && ptab) ? static_cast<int>(ptab[ip]) : ip;
-                if constexpr (kPf) {
-                    if (ord) pr = pfp;
-                }
+                const int pr = (kTab && ptab) ? static_cast<int>(ptab[ip]) : ip;
                 const int c = 2 * pr;
                 float al0[DC], al1[DC];
                 uint32_t v0[DC], v1[DC];
                 if constexpr (kPf) {
                     GraphT::template unpack<DC>(pfc, v0, v1);
-                    if (ip + G < mpairs) {
-                        if (ord) {
-                            pfp = static_cast<int>(gr.pair_at(ip + G));
-                            gr.pcols2_raw(ip + G, pfc);
-                        } else {
-                            gr.cols2_raw(ip + G, pfc);
-                        }
-                    }
+                    if (ip + G < mpairs) gr.cols2_raw(ip + G, pfc);
                 } else {
                     gr.cols2(pr, v0, v1);
                 }

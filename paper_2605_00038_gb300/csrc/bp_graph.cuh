@@ -54,8 +54,6 @@ struct EllGraph {
     const IP *vent2;
     const float *mu_;
     const float2 *mu2_;
-    const IP *pcidx2;        // pair-ordered check side (null when the image has none)
-    const uint16_t *pord;
     int Mp, Np, mpairs, npairs;
     uint32_t pad;            // column id of absent neighbours (n)
     static constexpr uint32_t ent_end = 0xffffffffu;   // absent checks: offset Mp (row Mp >= m)
@@ -69,8 +67,6 @@ struct EllGraph {
         vent2 = reinterpret_cast<const IP *>(vent);
         mu_ = reinterpret_cast<const float *>(gbase + img.off_mu);
         mu2_ = reinterpret_cast<const float2 *>(mu_);
-        pcidx2 = img.off_pcidx ? reinterpret_cast<const IP *>(gbase + img.off_pcidx) : nullptr;
-        pord = img.off_pord ? reinterpret_cast<const uint16_t *>(gbase + img.off_pord) : nullptr;
         Mp = img.Mp;
         Np = img.Np;
         mpairs = Mp >> 1;
@@ -106,13 +102,6 @@ struct EllGraph {
         for (int k = 0; k < DV; ++k) w[k] = __ldg(vent2 + k * npairs + q);
     }
     __device__ __forceinline__ float2 mu2_ldg(int q) const { return __ldg(mu2_ + q); }
-    // Pair-ordered form: trip ip's check pair and its index words.
-    __device__ __forceinline__ bool ordered() const { return pcidx2 != nullptr; }
-    __device__ __forceinline__ uint32_t pair_at(int ip) const { return __ldg(pord + ip); }
-    __device__ __forceinline__ void pcols2_raw(int ip, IP (&w)[DC]) const {
-        #pragma unroll
-        for (int k = 0; k < DC; ++k) w[k] = __ldg(pcidx2 + k * mpairs + ip);
-    }
     template <int N>
     static __device__ __forceinline__ void unpack(const IP (&w)[N], uint32_t (&x)[N], uint32_t (&y)[N]) {
         #pragma unroll

@@ -43,12 +43,6 @@ struct EllImage {
     // 0 .. DC-3, its measurement columns of blocks t-1 and t in slots DC-2
     // and DC-1; meas0 = the first measurement column (0: not aligned).
     int32_t meas0;
-    // Pair-ordered copy of the check side for an image read from global
-    // memory (0: none): the check phase's trip ip takes check pair
-    // pord[ip] (u16, pord[ip] = ip mod 32 per lane, chosen to spread the
-    // posterior gathers over the banks) and reads its index words at
-    // pcidx[k][ip], so the words stay coalesced.
-    uint32_t off_pcidx, off_pord;
 };
 
 // Space-time matrix of the unrotated surface code (Eq. 1 with one check type

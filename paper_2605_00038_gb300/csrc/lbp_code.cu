@@ -485,16 +485,6 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
                              detect_round(m, n, row_ptr, col_idx, mu, ell_dc, ell_dv, Mp, &rd, &rdimg);
         const int64_t M0 = aligned ? static_cast<int64_t>(rd.T) * rd.nr : 0;
         e.meas0 = static_cast<int32_t>(M0);
-        // The same codes read the image from global memory: a pair-ordered copy
-        // of the check side spreads the check phase's posterior gathers over the
-        // shared-memory banks (see EllImage).
-        if (aligned) {
-            e.off_pcidx = off;
-            off = align16(off + ib * e.DC * Mp);
-            e.off_pord = off;
-            off = align16(off + 2u * static_cast<uint32_t>(Mp / 2));
-            e.bytes = off;
-        }
         // Slot of column v in row r.
         auto slot_of = [&](int32_t r, int32_t v, int32_t k_sorted) -> int32_t {
             if (!aligned) return k_sorted;
@@ -528,21 +518,6 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
             }
         }
         for (int32_t v = 0; v < Np + 2; ++v) mu_e[v] = v < n ? mu[v] : INFINITY;
-        if (e.off_pcidx) {
-            const std::vector<uint16_t> ord = pair_table(img, e.off_cidx, e.DC, Mp);
-            const uint16_t *ci = reinterpret_cast<const uint16_t *>(img.data() + e.off_cidx);
-            uint16_t *pc = reinterpret_cast<uint16_t *>(img.data() + e.off_pcidx);
-            uint16_t *po = reinterpret_cast<uint16_t *>(img.data() + e.off_pord);
-            const int32_t mp = Mp / 2;
-            for (int32_t ip = 0; ip < mp; ++ip) {
-                const int32_t pr = ord[ip];
-                po[ip] = static_cast<uint16_t>(pr);
-                for (int k = 0; k < e.DC; ++k) {
-                    pc[static_cast<size_t>(k) * Mp + 2 * ip] = ci[static_cast<size_t>(k) * Mp + 2 * pr];
-                    pc[static_cast<size_t>(k) * Mp + 2 * ip + 1] = ci[static_cast<size_t>(k) * Mp + 2 * pr + 1];
-                }
-            }
-        }
         if (c->tab_R) {
             const std::vector<uint16_t> tab = pair_table(img, e.off_cidx, e.DC, Mp);
             std::memcpy(img.data() + c->tab_off_ptab, tab.data(), 2u * tab.size());
