@@ -373,10 +373,12 @@ def run_gpu(args):
     # Work actually done in the timed steps (iterations per batch decoded).
     iters_total = 0
     unconverged = 0
+    osd_total = 0
     for k in range(args.steps):
         o = outs[k % N_BATCHES]
         iters_total += int(o.iters.sum().item())
         unconverged += int((o.converged == 0).sum().item())
+        osd_total += int((o.osd != 0).sum().item())
     hist = histogram([outs[k].iters for k in range(min(args.steps, N_BATCHES))])
 
     line = {
@@ -430,6 +432,7 @@ def run_gpu(args):
                        "osd_ms_per_step": osd_ms / args.steps,
                        "mean_iters": iters_total / (B * args.steps),
                        "unconverged_rate": unconverged / (B * args.steps),
+                       "osd_invoke_rate": osd_total / (B * args.steps),
                        "iteration_histogram": hist}
 
     # End to end through the host-buffer entry point (pinned memory).
