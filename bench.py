@@ -865,9 +865,33 @@ def run_serving(seconds_per_rate: float = 3.0, n_requests: int = 600, seed: int 
     dt = time.perf_counter() - t0
     total_shots = sum(r["B"] for r in reqs)
     cap_req = len(reqs) / dt
+    # The same shots decoded as large device-resident batches, one per code and
+    # noise level (8,192 shots each, default launch shape): the time the mix's
+    # shots would take without serving (no copies, no small launches).
+    rate = {}
+    for key, dec in decs.items():
+        used = [r for r in reqs if (r["ci"], r["pi"]) == key]
+        if not used:
+            continue
+        h = dec.h
+        nb = 8192
+        _, sb = sampler.sample(h, dec_priors(dec), seed=seed + 1000 + key[0], num_shots=nb)
+        x = torch.from_numpy(sb.view(np.int64)).cuda()
+        prm = dec.params(max_iter=100, lottery=1, osd=1, msg=2, seed=seed)
+        dec.decode(x, prm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dec.decode(x, prm)
+        e1.record()
+        torch.cuda.synchronize()
+        rate[key] = nb / (e0.elapsed_time(e1) / 1e3)
+    ideal_s = sum(r["B"] / rate[(r["ci"], r["pi"])] for r in reqs)
     out = {"policy": ("chunk_work 16 Mi edge-shots, priority" if policy is None else
                       "chunk_work %d, priority %d" % (policy[0], int(policy[1]))) +
                      (", merged launches of up to %d requests" % merge if merge else ""),
+           "batched_equivalent_shots_per_s": total_shots / ideal_s,
+           "serving_efficiency": (total_shots / dt) / (total_shots / ideal_s),
            "codes": len(codes), "noise_levels": len(ps), "requests": len(reqs),
            "mean_request_shots": total_shots / len(reqs), "capacity_shots_per_s": total_shots / dt,
            "capacity_requests_per_s": cap_req, "rates": []}

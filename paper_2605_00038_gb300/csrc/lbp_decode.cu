@@ -950,6 +950,7 @@ int plan_batch(const lbp_batch_item *items, int n, BatchPlan *P, bool size_only 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LBP_ECUDA; }
     uint32_t maxst = 16;
+    int maxpairs = 1;
     for (int i = 0; i < n; ++i) {
         const lbp_batch_item &it = items[i];
         const int rc = check_common(it.code, &it.params, it.num_shots);
@@ -969,19 +970,21 @@ int plan_batch(const lbp_batch_item *items, int n, BatchPlan *P, bool size_only 
         P->off_s[i] = o;    o = align16u(o + 4u * W32);
         P->off_shat[i] = o; o = align16u(o + 12u * W32);
         if (o > maxst) maxst = o;
+        maxpairs = std::max(maxpairs, std::max(c->ell.Mp, c->ell.Np) / 2);
         P->total += it.num_shots;
     }
     if (P->total > (1ll << 31)) return LBP_EINVAL;
     const lbp_code *c0 = items[0].code;
     P->state_bytes = maxst;
     // Groups per CTA: as many states (plus their 16-byte shot slots) as fit,
-    // at most 15 named barriers; threads per group: the widest of 192, 128, 64
-    // that keeps the CTA at 1024 threads or fewer.
+    // at most 15 named barriers; threads per group: about one per six pairs
+    // of the largest code's checks or columns (64, 128 or 192), narrowed so
+    // the CTA keeps at most 1024 threads.
     const size_t budget = static_cast<size_t>(c0->smem_optin);
     int S = static_cast<int>(budget / (static_cast<size_t>(maxst) + 16));
     if (S < 1) return LBP_ENOSYS;
     if (S > 15) S = 15;
-    int G = 192;
+    int G = maxpairs > 6 * 128 ? 192 : (maxpairs > 6 * 64 ? 128 : 64);
     while (G > 64 && S * G > 1024) G = G == 192 ? 128 : 64;
     if (S * G > 1024) S = 1024 / G;
     P->S = S;

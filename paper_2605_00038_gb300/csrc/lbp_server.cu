@@ -220,11 +220,15 @@ BufLayout buf_layout(const lbp_code *c, int64_t B) {
     return L;
 }
 
-// Whether r can join a merged launch whose first request is f.
+// Whether r can join a merged launch whose first request is f: the launch's
+// conditions, and codes within a factor of two in size (a launch sizes every
+// group's state and width for its largest code, which would idle most of a
+// small code's threads).
 bool mergeable(const Request &f, const Request &r) {
+    const int64_t nf = f.code->n, nr = r.code->n;
     return r.params.msg == f.params.msg && r.params.rule == LBP_RULE_MIN_SUM && f.params.rule == LBP_RULE_MIN_SUM &&
            r.code->d_ell && f.code->d_ell && r.code->ell.idx_bytes == 2 && f.code->ell.idx_bytes == 2 &&
-           r.code->ell.DC == f.code->ell.DC && r.code->ell.DV == f.code->ell.DV;
+           r.code->ell.DC == f.code->ell.DC && r.code->ell.DV == f.code->ell.DV && nr <= 2 * nf && nf <= 2 * nr;
 }
 
 // Arena bytes of a merged launch: the requests' buffers, then the batch
