@@ -583,3 +583,17 @@ def test_environment_switches_read_at_load(monkeypatch):
     assert lbp.lbp_code_options(dec.code)[0] == 3
     dec.close()
     plain.close()
+
+
+@pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_I8])
+def test_slot_aligned_image_cyclic_boundary(msg):
+    """Rotated d=25 with a cyclic time boundary (7,800 x 23,425): its image is
+    slot-aligned (the t-1 measurement block of round 0 wraps to block 24 and
+    still takes slot 4), and FP32 runs the split state.  A sample of shots
+    matches the oracle."""
+    hz, _ = rotated_surface(25)
+    st = spacetime(hz, 25, "cyclic")
+    pri = spacetime_priors(hz, 25, 0.004, 0.004, "cyclic")
+    _, syn = sampler.sample(st, pri, seed=71, num_shots=48)
+    kw = dict(max_iter=40, lottery=1, lottery_skip=2, msg=msg, seed=3)
+    assert_parity(gpu_decode(st, pri, syn, **kw), oracle_decode(st, pri, syn, **kw))
