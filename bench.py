@@ -979,11 +979,12 @@ def _served(dec, prms, hs, hbuf, load, rng):
 def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load: float = 0.8):
     """Matched-LER head-to-head on identical shots: (A) plain NMS BP + OSD-0
     with FP32 messages against Lottery BP + OSD-0 with INT8 (Int3.4) messages
-    and the paper's rule (Alg. 3), on the code families the paper evaluates
-    (the BB [[144,12,12]] code at p = 0.05, code capacity; the unrotated
-    surface code's space-time matrix, Table III rows, d = 7, 7 rounds,
-    p = 0.01) and on the rotated d = 7 space-time code (p = 0.012), where the
-    worst-check / least-reliable-column rule of Sec. III-B is added.  Every
+    and the paper's rule (Alg. 3), and with the worst-check /
+    least-reliable-column rule of Sec. III-B, on the code families the paper
+    evaluates (the BB [[144,12,12]] code at p = 0.03 and 0.05, code capacity;
+    the unrotated surface code's space-time matrix, Table III rows, d = 7,
+    7 rounds, p = 0.01) and on the rotated d = 7 space-time code (p = 0.012);
+    at BB144 p = 0.05 also the lottery's start iteration (6, 12, 20, 40).  Every
     arm is timed the same two ways: one device-resident lbp_decode of all
     shots, and served through lbp_server from host buffers in 4096-shot
     requests (capacity with every request queued; then open-loop Poisson
@@ -999,6 +1000,7 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
 
     fams = []
     hx, _ = bb_code("bb144")
+    fams.append(("bb144_cc_p0.03", hx, np.full(hx.n, 0.03), evaluate.bb_spec("bb144")))
     fams.append(("bb144_cc_p0.05", hx, np.full(hx.n, 0.05), evaluate.bb_spec("bb144")))
     _, uz = unrotated_surface(7)
     ust = spacetime(uz, 7)
@@ -1022,10 +1024,9 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
         hbuf = (pin((shots, wn), torch.int64), pin(shots, torch.uint8), pin(shots, torch.uint8),
                 pin(shots, torch.int32))
         arms = [("plain_bp_osd_fp32", dict(lottery=0, msg=0, lottery_policy=0)),
-                ("lottery_alg3_bp_osd_int8", dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_PROPOSED))]
-        if name.startswith("rotated"):
-            arms.append(("lottery_worst_unreliable_bp_osd_int8",
-                         dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE)))
+                ("lottery_alg3_bp_osd_int8", dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_PROPOSED)),
+                ("lottery_worst_unreliable_bp_osd_int8",
+                 dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE))]
         fam = {"shape": [h.m, h.n, h.nnz]}
         fa = None
         for arm, kw in arms:
@@ -1058,6 +1059,20 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
                             "mcnemar_discordant": [only_a, only_b],
                             "mcnemar_p": evaluate.mcnemar_p(only_a, only_b)})
             fam[arm] = res
+        if name == "bb144_cc_p0.05":
+            # The lottery's start iteration (Sec. III-B skips 6, chosen at low
+            # p): Alg. 3 + OSD-0, INT8, batched, against the plain arm above.
+            sweep = {}
+            for skip in (6, 12, 20, 40):
+                prm = dec.params(max_iter=100, osd=1, seed=seed, lottery=1, msg=2, lottery_skip=skip)
+                r = dec.decode(sd, prm)
+                torch.cuda.synchronize()
+                f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+                k = int(f.sum().item())
+                sweep[str(skip)] = {"ler": k / shots, "ler_relative_difference": (k - ka) / max(ka, 1),
+                                    "osd_invoke_rate": float((r.osd != 0).float().mean().item()),
+                                    "mean_iters": float(r.iters.float().mean().item())}
+            fam["lottery_alg3_skip_sweep"] = sweep
         out["families"][name] = fam
         dec.close()
     return out
