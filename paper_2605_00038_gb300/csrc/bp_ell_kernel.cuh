@@ -308,7 +308,6 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             const bool early = lottery_random_check(LBP_ARG(policy));
             int cpre = -1;
             uint32_t u2pre = 0;
-            uint32_t lot_v = 0xffffffffu;     // c*'s slot-`lane` column, read early (global image)
             LotteryPrep lp;          // index-image instantiations in shared memory only
             // ---- C2V, two adjacent checks per thread ---------------------------
             // With the index image in global memory (L2), each trip's index
@@ -371,13 +370,6 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                 } else {
                     cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
                                              LBP_ARG(policy), lam, u2pre);
-                    // With the image in global memory the column step after the
-                    // termination test waits on two dependent L2 reads (c*'s
-                    // columns, then their checks): read the columns now; their
-                    // lines are prefetched into L1 at the end of the column phase.
-                    if constexpr (kPf) {
-                        if (cpre >= 0 && lane < DC) lot_v = gr.col(lane, cpre);
-                    }
                 }
             }
             group_sync<G>(bar);
@@ -453,31 +445,19 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     }
                 }
             }
-            if constexpr (kPf) {
-                // The lottery warp's column step reads c*'s columns and their
-                // checks right after the termination test: bring those lines
-                // into L1 now, while the other warps finish the column phase.
-                if (lot && lw && cpre >= 0 && lane < DC) {
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(gr.cidx + lane * Mp + cpre));
-                    if (lot_v != gr.pad && lot_v != 0xffffffffu) {
-                        #pragma unroll
-                        for (int kk = 0; kk < DV; ++kk)
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(gr.vent + kk * Np + lot_v));
-                    }
-                }
-            }
             group_sync<G>(bar);
             // ---- lottery (Alg. 3, or a baseline policy of Sec. III-B) ---------
-            // Its inputs (s_hat(i-1), s, lambda(i)) are complete here, so the
+            // Index-image instantiations in shared memory (kTab): the lottery's
+            // inputs (s_hat(i-1), s, lambda(i)) are complete here, so the
             // lottery warp picks and flips v* now, alongside the termination
-            // test, and the test's barrier also orders the flip before the
-            // next check phase.  If the shot has converged the flip is undone
-            // before the results read lambda (the lottery acts only on
-            // unconverged iterations).
+            // test, whose barrier also orders the flip before the next check
+            // phase; if the shot has converged the flip is undone before the
+            // results read lambda.  The other instantiations run the lottery
+            // after the test, behind a barrier of its own.
             int vflip = -1;
-            if (lot && lw) {
-                const uint32_t *sp = shat + prev * W32;
-                if constexpr (kTab) {
+            if constexpr (kTab) {
+                if (lot && lw) {
+                    const uint32_t *sp = shat + prev * W32;
                     if (!early) {
                         uint32_t u2 = 0;
                         const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b,
@@ -485,14 +465,8 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                         lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, LBP_ARG(policy), m, R, LBP_ARG(magic));
                     }
                     vflip = lottery_finish(lp, lam);
-                } else {
-                    if (!early)
-                        cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it, LBP_ARG(policy),
-                                                 lam, u2pre);
-                    vflip = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, LBP_ARG(policy), lam, m, R,
-                                                   LBP_ARG(magic));
+                    if (lane == 0 && vflip >= 0) lam[vflip] = -lam[vflip];
                 }
-                if (lane == 0 && vflip >= 0) lam[vflip] = -lam[vflip];
             }
             // ---- early termination ------------------------------------------
             bool mism = false;
@@ -502,10 +476,26 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                 sh_nxt[w] = 0u;
             }
             if (!group_sync_or<G>(bar, mism)) {
-                if (lane == 0 && vflip >= 0) lam[vflip] = -lam[vflip];
-                group_sync<G>(bar);
+                if constexpr (kTab) {
+                    if (lane == 0 && vflip >= 0) lam[vflip] = -lam[vflip];
+                    group_sync<G>(bar);
+                }
                 converged = true;
                 break;
+            }
+            if constexpr (!kTab) {
+                if (lot) {
+                    if (lw) {
+                        const uint32_t *sp = shat + prev * W32;
+                        if (!early)
+                            cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
+                                                     LBP_ARG(policy), lam, u2pre);
+                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, LBP_ARG(policy), lam, m, R,
+                                                              LBP_ARG(magic));
+                        if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
+                    }
+                    group_sync<G>(bar);
+                }
             }
             const int tmp = prev; prev = cur; cur = nxt; nxt = tmp;
         }
