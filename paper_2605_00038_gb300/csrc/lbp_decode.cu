@@ -469,10 +469,11 @@ WsLayout layout(const lbp_code *c, const lbp_params *prm, int64_t num_shots, con
     if (bp && (!bp->state_smem || bp->split)) {
         // Sized for every launch shape (at most 1024 / 256 groups per CTA, one
         // CTA per SM), so lbp_tune's candidates and any tuned shape fit; a
-        // split state needs the slice of its workspace slots per group.
+        // split state (one group per CTA in every shape) needs the slice of
+        // its workspace slots per CTA.
         w.gstate = off;
         const size_t slice = bp->split ? bp->gbeta_bytes : bp->state_bytes;
-        off = align256(off + static_cast<size_t>(c->sm_count) * 4 * slice);
+        off = align256(off + static_cast<size_t>(c->sm_count) * (bp->split ? 1 : 4) * slice);
     }
     if (prm->osd) {
         w.osd_list = off; off = align256(off + 4ull * num_shots);

@@ -52,12 +52,17 @@ def _same(a, b):
     assert np.all(np.abs(a["llr"] - b["llr"]) <= LLR_RTOL * np.abs(a["llr"]) + 1e-30)
 
 
-@pytest.mark.parametrize("which", ["bb144_osd_fp16", "d11_spacetime_fp32"])
+@pytest.mark.parametrize("which", ["bb144_osd_fp16", "d11_spacetime_fp32", "d25_split_state_fp32"])
 def test_noalloc_matches_workspace_decode_twice(which):
     if which == "bb144_osd_fp16":
         w = workloads.c3_bb144(0.05, shots=3000)
-    else:
+    elif which == "d11_spacetime_fp32":
         w = workloads.c2_d11_spacetime(shots=2000, osd=0)
+    else:
+        # The d=25 space-time code with FP32 messages keeps part of each
+        # shot's state in the scratch array (its split state).
+        w = workloads.c5_d25_spacetime(msg=0, shots=300)
+        w.decoder = dict(w.decoder, max_iter=30)
     dec = Decoder(w.h, w.priors)
     for call, offset in enumerate((0, 50_000)):
         _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots, shot_offset=offset)
