@@ -129,7 +129,8 @@ void lbp_params_default(lbp_params *p);
  * code object, so decodes never depend on the environment at call time:
  * LBP_BANK_LAYOUT, LBP_GRAPH (graph form, see lbp_code_surface),
  * LBP_BP_SHAPE ("S,G": BP groups per CTA and threads per group),
- * LBP_OSD_POOL_ROWS and LBP_OSD_LAT (see lbp_workspace_size). */
+ * LBP_OSD_POOL_ROWS, LBP_OSD_LAT (see lbp_workspace_size) and LBP_OSD_DENSE
+ * (see lbp_code_osd_form). */
 int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                   const double *priors, lbp_code **out);
 
@@ -140,6 +141,19 @@ int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *c
  * (code NULL). */
 int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int32_t *G,
                      int32_t *pool_rows, int32_t *osd_latency);
+
+/* OSD form of a loaded code (Alg. 2, Sec. III-B).  Codes with m <= 128,
+ * n + 1 <= 256 and 16-bit indices take the dense form: one warp per shot
+ * holds all of [H | s] as packed 64-bit rows in registers (lane l: rows l,
+ * l + 32, ...) and runs Gauss-Jordan elimination over the columns in the
+ * LLR-sorted order of Alg. 2, stopping after rank(H) pivots (rank(H) over
+ * GF(2) is computed at load).  Other codes take the event-driven warp kernel
+ * and its block-wide fallback.  Both forms return the same e and status.
+ * LBP_OSD_DENSE=0 (read at load) keeps a small code on the event-driven
+ * kernels.  *dense = 1 for the dense form, else 0; *rank = rank(H) in the
+ * dense form, else -1.  Any output pointer may be NULL.  Errors: LBP_EINVAL
+ * (code NULL). */
+int lbp_code_osd_form(const lbp_code *code, int32_t *dense, int32_t *rank);
 
 /* Release a code object (synchronous; no call using it may be in flight). */
 int lbp_free_code(lbp_code *code);
@@ -177,7 +191,8 @@ int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r
  * parameters (0 on invalid input).  The size grows linearly with num_shots
  * only when params->osd is set (the LLRs of shots handed to OSD).
  *
- * Tuning: OSD keeps rows of H sparse until an elimination changes them; the
+ * Tuning (codes on the event-driven OSD kernels, see lbp_code_osd_form):
+ * OSD keeps rows of H sparse until an elimination changes them; the
  * changed rows take dense copies from a per-warp pool of C rows, by default
  * max(192, m / 2) (at most m), lowered so that the pools of all warps stay
  * within 1 GiB but never below min(m, 192).  The environment variable

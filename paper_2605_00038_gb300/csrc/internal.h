@@ -165,6 +165,11 @@ struct lbp_code {
     // so that decodes of a loaded code never depend on the environment at
     // call time: LBP_GRAPH (0 unset, 1 table, 2 implicit, 3 round),
     // LBP_BP_SHAPE "S,G" (0, 0 unset), LBP_OSD_POOL_ROWS (0 unset) and
-    // LBP_OSD_LAT (0: latency layout off).
-    int env_graph, env_S, env_G, env_pool_rows, env_osd_lat;
+    // LBP_OSD_LAT (0: latency layout off), LBP_OSD_DENSE (0: dense OSD off).
+    int env_graph, env_S, env_G, env_pool_rows, env_osd_lat, env_osd_dense;
+    // Dense OSD (K_osd_dense) for codes with m <= 128 and n + 1 <= 256 and a
+    // 16-bit image: rows per lane, 64-bit words per augmented row, rank(H)
+    // over GF(2); osd_dense = 0 when the code takes the event-driven kernels.
+    int osd_dense, osd_RL, osd_WN;
+    int32_t osd_rank;
 };

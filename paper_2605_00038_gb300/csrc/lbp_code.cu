@@ -322,9 +322,43 @@ void read_env_switches(lbp_code *c) {
     }
     const char *lat = std::getenv("LBP_OSD_LAT");
     c->env_osd_lat = (lat && !std::strcmp(lat, "0")) ? 0 : 1;
+    const char *dn = std::getenv("LBP_OSD_DENSE");
+    c->env_osd_dense = (dn && !std::strcmp(dn, "0")) ? 0 : 1;
+}
+
+// Rank of H over GF(2) (rows as packed 64-bit words, forward elimination).
+int32_t gf2_rank(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx) {
+    const int32_t wn = (n + 63) / 64;
+    std::vector<uint64_t> a(static_cast<size_t>(m) * wn, 0ull);
+    for (int32_t r = 0; r < m; ++r)
+        for (int32_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+            a[static_cast<size_t>(r) * wn + col_idx[e] / 64] |= 1ull << (col_idx[e] % 64);
+    int32_t rank = 0;
+    for (int32_t v = 0; v < n && rank < m; ++v) {
+        const int32_t w = v / 64;
+        const uint64_t bit = 1ull << (v % 64);
+        int32_t p = -1;
+        for (int32_t r = rank; r < m; ++r)
+            if (a[static_cast<size_t>(r) * wn + w] & bit) { p = r; break; }
+        if (p < 0) continue;
+        for (int32_t k = 0; k < wn; ++k)
+            std::swap(a[static_cast<size_t>(p) * wn + k], a[static_cast<size_t>(rank) * wn + k]);
+        for (int32_t r = rank + 1; r < m; ++r)
+            if (a[static_cast<size_t>(r) * wn + w] & bit)
+                for (int32_t k = 0; k < wn; ++k) a[static_cast<size_t>(r) * wn + k] ^= a[static_cast<size_t>(rank) * wn + k];
+        ++rank;
+    }
+    return rank;
 }
 
 }  // namespace
+
+extern "C" int lbp_code_osd_form(const lbp_code *code, int32_t *dense, int32_t *rank) {
+    if (!code) return LBP_EINVAL;
+    if (dense) *dense = code->osd_dense;
+    if (rank) *rank = code->osd_dense ? code->osd_rank : -1;
+    return LBP_OK;
+}
 
 extern "C" int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int32_t *G,
                                 int32_t *pool_rows, int32_t *osd_latency) {
@@ -542,6 +576,15 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         }
     }
     if (rc != LBP_OK) { release(c); return rc; }
+    // Dense OSD: the whole augmented matrix of a small code in one warp's
+    // registers (32 rows per row slot, 64 columns per word, the syndrome bit
+    // in column n).
+    if (c->d_image && c->env_osd_dense && m >= 1 && m <= 128 && n + 1 <= 256) {
+        c->osd_dense = 1;
+        c->osd_RL = (m + 31) / 32;
+        c->osd_WN = (n + 1 + 63) / 64;
+        c->osd_rank = gf2_rank(m, n, row_ptr, col_idx);
+    }
     *out = c;
     return LBP_OK;
 }

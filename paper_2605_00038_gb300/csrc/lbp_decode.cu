@@ -33,6 +33,7 @@
 #include "bp_kernel.cuh"
 #include "internal.h"
 #include "launch.h"
+#include "osd_dense_kernel.cuh"
 #include "osd_kernel.cuh"
 #include "osd_warp_kernel.cuh"
 #include "timing.h"
@@ -534,6 +535,30 @@ int launch_osd(const lbp_code *c, int64_t B, const uint64_t *syn, uint64_t *err,
                unsigned int *counters, uint8_t *base, const WsLayout &w, const OsdPlan &op, OsdWarpPlan wp,
                uint32_t *osd_list, float *osd_llr, cudaStream_t stream, bool alone) {
     int rc = LBP_OK;
+    if (c->osd_dense) {
+        // Small code: K_osd_dense solves every queued shot (no pool, no
+        // hand-over to K_osd).
+        OsdDenseArgs d;
+        std::memset(&d, 0, sizeof(d));
+        d.image = c->d_image;
+        d.img = c->img;
+        d.image_bytes = c->img.off_col_ptr;       // row_ptr and col_idx only
+        d.m = c->m; d.n = c->n; d.wn = (c->n + 63) / 64; d.rank = c->osd_rank;
+        d.syn = syn; d.err = err; d.osd_out = osd_out;
+        d.counters = counters;
+        d.osd_list = osd_list; d.osd_llr = osd_llr;
+        d.off_perm = align16u(4u * static_cast<uint32_t>(c->n));
+        d.off_x = d.off_perm + align16u(2u * static_cast<uint32_t>(c->n));
+        d.region_bytes = d.off_x + align16u(8u * static_cast<uint32_t>(d.wn));
+        const int64_t need = (B + kOsdDenseWarps - 1) / kOsdDenseWarps;
+        const int64_t cap = 2 * static_cast<int64_t>(c->sm_count);
+        const int grid = static_cast<int>(need < 1 ? 1 : (need < cap ? need : cap));
+        const size_t smem = d.image_bytes + static_cast<size_t>(kOsdDenseWarps) * d.region_bytes;
+        void *td = timing_begin(stream);
+        rc = launch_osd_dense(d, c->osd_RL, c->osd_WN, grid, smem, stream);
+        timing_end(td, stream, kTimeOsd);
+        return rc;
+    }
     if (wp.ok) {
         OsdWarpPlan lp;
         if (alone && plan_osd_lat(c, B, wp, &lp)) wp = lp;

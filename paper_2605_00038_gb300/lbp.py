@@ -26,7 +26,7 @@ LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
  LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM) = range(5)
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface",
-            "lbp_code_rounds", "lbp_code_tuned", "lbp_code_options",
+            "lbp_code_rounds", "lbp_code_tuned", "lbp_code_options", "lbp_code_osd_form",
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
             "lbp_server_wait", "lbp_server_destroy", "lbp_graph_create", "lbp_graph_launch",
@@ -83,6 +83,8 @@ def lib():
         L.lbp_code_tuned.argtypes = [vp, i32, i32, vp, vp, vp]
         L.lbp_code_options.restype = ctypes.c_int
         L.lbp_code_options.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.lbp_code_osd_form.restype = ctypes.c_int
+        L.lbp_code_osd_form.argtypes = [vp, vp, vp]
         L.lbp_probe_smem.restype = ctypes.c_int
         L.lbp_probe_smem.argtypes = [i32, vp, vp, vp]
         L.lbp_batch_workspace_size.restype = sz
@@ -220,6 +222,13 @@ def lbp_code_tuned(code: Code, msg: int, rule: int = 0):
     _check(lib().lbp_code_tuned(code.ptr, msg, rule, ctypes.byref(S), ctypes.byref(G), ctypes.byref(gf)),
            "lbp_code_tuned")
     return S.value, G.value, gf.value
+
+
+def lbp_code_osd_form(code: Code):
+    """(dense, rank): 1 and rank(H) when OSD runs the dense register form, else 0 and -1."""
+    d, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lbp_code_osd_form(code.ptr, ctypes.byref(d), ctypes.byref(r)), "lbp_code_osd_form")
+    return d.value, r.value
 
 
 def lbp_code_options(code: Code):

@@ -268,8 +268,10 @@ def test_osd_bit_exact_on_gpu_llrs():
 @pytest.mark.parametrize("pool", ["1", "3"])
 def test_osd_pool_overflow_falls_back_to_block_kernel(pool, monkeypatch):
     """A tiny dense-row pool sends most OSD shots to the block-wide kernel;
-    results stay bit-identical."""
+    results stay bit-identical.  (BB144 would take the dense OSD form, which
+    has no pool: LBP_OSD_DENSE=0 keeps it on the event-driven kernels.)"""
     monkeypatch.setenv("LBP_OSD_POOL_ROWS", pool)
+    monkeypatch.setenv("LBP_OSD_DENSE", "0")
     for h, pri, msg in [(workloads.c3_bb144(0.05).h, np.full(144, 0.05), lbp.LBP_MSG_F16),
                         (workloads.c2_d11_spacetime().h, workloads.c2_d11_spacetime().priors,
                          lbp.LBP_MSG_F32)]:
@@ -285,9 +287,11 @@ def test_osd_latency_layout_small_batches(pool, monkeypatch):
     """Batches of at most one shot per SM run K_osd_warp's latency layout (one
     warp per CTA, lambda order bits and the row pool in shared memory): the
     same outputs as the oracle and as the throughput layout; with a 2-row pool
-    most shots overflow to K_osd, still bit-identical."""
+    most shots overflow to K_osd, still bit-identical.  LBP_OSD_DENSE=0 keeps
+    BB144 on the event-driven kernels."""
     if pool:
         monkeypatch.setenv("LBP_OSD_POOL_ROWS", pool)
+    monkeypatch.setenv("LBP_OSD_DENSE", "0")
     hz, _ = rotated_surface(13)
     st = spacetime(hz, 13)
     pri = spacetime_priors(hz, 13, 0.006, 0.006)
