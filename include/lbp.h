@@ -142,8 +142,8 @@ int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const int32_t *c
 int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int32_t *G,
                      int32_t *pool_rows, int32_t *osd_latency);
 
-/* OSD form of a loaded code (Alg. 2, Sec. III-B).  Codes with m <= 128,
- * n + 1 <= 256 and 16-bit indices take the dense form: one warp per shot
+/* OSD form of a loaded code (Alg. 2, Sec. III-B).  Codes with m <= 160,
+ * n + 1 <= 320 and 16-bit indices take the dense form: one warp per shot
  * holds all of [H | s] as packed 64-bit rows in registers (lane l: rows l,
  * l + 32, ...) and runs Gauss-Jordan elimination over the columns in the
  * LLR-sorted order of Alg. 2, stopping after rank(H) pivots (rank(H) over

@@ -579,7 +579,7 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
     // Dense OSD: the whole augmented matrix of a small code in one warp's
     // registers (32 rows per row slot, 64 columns per word, the syndrome bit
     // in column n).
-    if (c->d_image && c->env_osd_dense && m >= 1 && m <= 128 && n + 1 <= 256) {
+    if (c->d_image && c->env_osd_dense && m >= 1 && m <= 160 && n + 1 <= 320) {
         c->osd_dense = 1;
         c->osd_RL = (m + 31) / 32;
         c->osd_WN = (n + 1 + 63) / 64;

@@ -1,5 +1,5 @@
 // K_osd_dense instantiations: rows per lane RL and 64-bit words per
-// augmented row WN, 1..4 each (m <= 128, n + 1 <= 256).
+// augmented row WN, 1..5 each (m <= 160, n + 1 <= 320).
 #include <cuda_runtime.h>
 
 #include "osd_dense_kernel.cuh"
@@ -27,6 +27,7 @@ int launch_r(const OsdDenseArgs &a, int WN, int grid, size_t smem, cudaStream_t 
         case 2: return launch_rw<RL, 2>(a, grid, smem, st);
         case 3: return launch_rw<RL, 3>(a, grid, smem, st);
         case 4: return launch_rw<RL, 4>(a, grid, smem, st);
+        case 5: return launch_rw<RL, 5>(a, grid, smem, st);
         default: return LBP_ENOSYS;
     }
 }
@@ -39,6 +40,7 @@ int launch_osd_dense(const OsdDenseArgs &a, int RL, int WN, int grid, size_t sme
         case 2: return launch_r<2>(a, WN, grid, smem, st);
         case 3: return launch_r<3>(a, WN, grid, smem, st);
         case 4: return launch_r<4>(a, WN, grid, smem, st);
+        case 5: return launch_r<5>(a, WN, grid, smem, st);
         default: return LBP_ENOSYS;
     }
 }

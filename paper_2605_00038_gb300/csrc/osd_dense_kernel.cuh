@@ -1,8 +1,8 @@
 // K_osd_dense: OSD-0 (Alg. 2) for small codes, one warp per shot, the whole
 // augmented matrix [H | s] in registers.
 //
-// For m <= 32 RL rows and n + 1 <= 64 WN columns (the BB [[144,12,12]] code:
-// RL = 3, WN = 3) every row of H, with its syndrome bit at column n, is
+// For m <= 32 RL rows and n + 1 <= 64 WN columns, RL and WN up to 5 (the
+// BB [[144,12,12]] code: RL = 3, WN = 3; BB [[288,12,18]]: RL = 5, WN = 5) every row of H, with its syndrome bit at column n, is
 // packed into WN 64-bit words, and lane l holds rows l, l + 32, ... .  Per
 // shot:
 //   1. LLR sorting: the rank of column v in the order of Alg. 2 (lambda

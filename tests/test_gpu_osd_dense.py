@@ -1,11 +1,11 @@
 """The dense OSD form (K_osd_dense, Alg. 2 on [H | s] held in one warp's
 registers) against the oracle and against the event-driven OSD kernels.
 
-Codes with m <= 128 and n + 1 <= 256 take the dense form.  Every case decodes
+Codes with m <= 160 and n + 1 <= 320 take the dense form.  Every case decodes
 the same shots twice, with the dense form and with LBP_OSD_DENSE=0 (the
 event-driven K_osd_warp / K_osd path), and against the oracle in the same
 message precision: error estimates, OSD status, convergence and iteration
-counts must be identical.  The shapes cover 1..4 row slots per lane and 1..4
+counts must be identical.  The shapes cover 1..5 row slots per lane and 1..5
 words per row, sizes at the word boundaries (n + 1 = 64 and 65, m = 32 and
 33), rank-deficient codes with syndromes outside the column space (status
 NO_SOLUTION, the BP estimate kept) and an all-zero row."""
@@ -92,20 +92,22 @@ def test_bb144_dense_osd(msg, monkeypatch):
 
 
 def test_small_codes_dense_osd(monkeypatch):
-    """BB72 (36 x 72), the d=3 code (4 x 9: 1 slot, 1 word), the d=5
-    space-time code (60 x 173)."""
+    """BB72 (36 x 72), BB288 (144 x 288: 5 slots, 5 words), the d=3 code
+    (4 x 9: 1 slot, 1 word), the d=5 space-time code (60 x 173)."""
     hx, _ = bb_code("bb72")
+    h288, _ = bb_code("bb288")
     hz3, _ = rotated_surface(3)
     hz5, _ = rotated_surface(5)
     st5 = spacetime(hz5, 5)
-    cases = [(hx, np.full(hx.n, 0.07)), (hz3, np.full(hz3.n, 0.12)),
+    cases = [(hx, np.full(hx.n, 0.07)), (h288, np.full(h288.n, 0.06)), (hz3, np.full(hz3.n, 0.12)),
              (st5, spacetime_priors(hz5, 5, 0.02, 0.02))]
     for h, pri in cases:
         _, syn = sampler.sample(h, pri, seed=42, num_shots=2000)
         check_both_forms(h, pri, syn, monkeypatch, max_iter=8, lottery=1, lottery_skip=2, osd=1, seed=5)
 
 
-@pytest.mark.parametrize("m,n", [(32, 63), (33, 64), (96, 191), (128, 255), (100, 127), (7, 128)])
+@pytest.mark.parametrize("m,n", [(32, 63), (33, 64), (96, 191), (128, 255), (100, 127), (7, 128),
+                                 (160, 319), (129, 256)])
 def test_shapes_and_unsatisfiable_syndromes(m, n, monkeypatch):
     """Random codes at the slot and word boundaries; half the syndromes are
     random bits, so rank-deficient codes see syndromes outside the column
