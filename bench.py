@@ -48,11 +48,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["d25", "d11"], default="d25",
+    ap.add_argument("--workload", choices=["d25", "d11", "bb144"], default="d25",
                     help="d25: the rotated d=25 space-time code, Lottery BP, FP32 (the headline); "
-                         "d11: the rotated d=11 space-time code, Lottery BP + OSD-0, FP32")
+                         "d11: the rotated d=11 space-time code, Lottery BP + OSD-0, FP32; "
+                         "bb144: BB [[144,12,12]] at p = 0.05, Lottery BP + OSD-0, FP16")
     ap.add_argument("--shots", type=int, default=None,
-                    help="shots per step per rank (default 2^18 for d25, 10^6 for d11)")
+                    help="shots per step per rank (default 2^18 for d25, 10^6 for d11 and bb144)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip latency sweep, LER and CPU baseline")
     ap.add_argument("--cpu-sample", type=int, default=6144, help="oracle shots for cpu_baseline")
@@ -145,10 +146,18 @@ def workload(shots, which: str = "d25"):
     from paper_2605_00038_gb300.inputs import workloads
     if which == "d11":
         return workloads.c2_d11_spacetime(shots=shots or 1_000_000, osd=1)
+    if which == "bb144":
+        return workloads.c3_bb144(0.05, shots=shots or 1_000_000)
     return workloads.c5_d25_spacetime(msg=0, shots=shots or (1 << 18))
 
 
+MSG_NAME = {0: "f32", 1: "f16", 2: "i8"}
+MSG_BYTES = {0: 4, 1: 2, 2: 1}
+
+
 def code_text(w):
+    if w.name.startswith("bb144"):
+        return "BB [[144,12,12]] H_X %dx%d nnz %d, code capacity" % (w.h.m, w.h.n, w.h.nnz)
     d = 25 if w.h.m == 7800 else 11
     return "rotated surface d=%d, %d noisy rounds, space-time H %dx%d nnz %d" % (d, d, w.h.m, w.h.n, w.h.nnz)
 
@@ -318,6 +327,7 @@ def run_gpu(args):
     w = workload(args.shots, args.workload)
     B = w.shots
     d25 = args.workload == "d25"
+    msg = w.decoder["msg"]
     dec = Decoder(w.h, w.priors, device="cuda:%d" % local)
     wm, wn = (w.h.m + 63) // 64, (w.h.n + 63) // 64
 
@@ -384,13 +394,14 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": MSG_NAME[msg], "data": "synthetic",
         "config": {"workload": w.name, "code": code_text(w),
-                   "noise": "iid p_data=p_meas=%s" % ("0.004" if d25 else "0.003"),
+                   "noise": {"d25": "iid p_data=p_meas=0.004", "d11": "iid p_data=p_meas=0.003",
+                             "bb144": "iid p=0.05"}[args.workload],
                    "shots_per_step_per_rank": B, "configuration_shots": N_BATCHES * B,
                    "decoder": "lottery_bp(proposed rule, skip 6, adaptive scale, I=100)" +
                               (", no OSD" if d25 else " + osd0"),
-                   "msg": "f32",
+                   "msg": MSG_NAME[msg],
                    "l2": "%d rotating input batches of %d MB syndromes, each > L2" % (
                        N_BATCHES, B * wm * 8 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -400,7 +411,7 @@ def run_gpu(args):
     sm_mhz = line["clocks"]["sm_mhz"] or 2070.0
     iters_per_step = iters_total / args.steps
     bp_avg_s = bp_ms / max(bp_n, 1) / 1e3
-    b_it = state_bytes_per_iteration(w.h, 4)
+    b_it = state_bytes_per_iteration(w.h, MSG_BYTES[msg])
     alg_bytes = iters_per_step * b_it + B * io_bytes_per_shot(w.h)
     peak_gbs, peak_basis = hbm_peak_gbs()
     traffic = None
@@ -414,18 +425,19 @@ def run_gpu(args):
         "bytes_per_shot_iteration": b_it, "shot_iterations_per_launch": iters_per_step,
         "algorithmic_bytes_per_launch": alg_bytes, "peak_basis": peak_basis,
         "dram_gbs_from_traffic": (traffic / bp_avg_s / 1e9) if traffic else None,
-        "note": "algorithmic bytes = state read and written once per shot-iteration, 2 (E 4 + 4 n), "
-                "plus I/O; the posteriors, syndrome words and four of six message slots stay in "
-                "shared memory, the other two slots in an L2-resident workspace slice, so DRAM "
-                "carries far less than the algorithmic bytes (traffic)",
+        "note": "algorithmic bytes = state read and written once per shot-iteration, 2 (E b + 4 n), "
+                "plus I/O" + ("; the posteriors, syndrome words and four of six message slots stay in "
+                              "shared memory, the other two slots in an L2-resident workspace slice, so "
+                              "DRAM carries far less than the algorithmic bytes (traffic)" if d25 else
+                              "; the whole state stays in shared memory"),
         "alu": {"achieved_tops": ops / bp_avg_s / 1e12, "peak_tops": alu_peak_ops(sm_mhz) / 1e12,
                 "frac": ops / bp_avg_s / alu_peak_ops(sm_mhz),
                 "peak_basis": "152 SMs x 128 lanes x median SM clock %.0f MHz (derived)" % sm_mhz}}
     smem_bps, smem_clk = smem_peak(stream)
-    smem_alg = iters_per_step * smem_bytes_per_iteration(w.h, 4)
+    smem_alg = iters_per_step * smem_bytes_per_iteration(w.h, MSG_BYTES[msg])
     line["roofline"]["smem"] = {"achieved_tbs": smem_alg / bp_avg_s / 1e12, "peak_tbs": smem_bps / 1e12,
                                 "frac": smem_alg / bp_avg_s / smem_bps,
-                                "bytes_per_shot_iteration": smem_bytes_per_iteration(w.h, 4),
+                                "bytes_per_shot_iteration": smem_bytes_per_iteration(w.h, MSG_BYTES[msg]),
                                 "peak_basis": "measured by lbp_probe_smem (conflict-free 16-byte loads), "
                                               "SM clock %s MHz while it ran" % smem_clk.get("sm_mhz")}
     line["kernels"] = {"bp_launch": launch, "bp_ms_per_step": bp_ms / args.steps,
@@ -473,13 +485,15 @@ def run_gpu(args):
         o = outs[0]
         step(0)
         torch.cuda.synchronize()
-        spec = evaluate.surface_spec(25, 25, w.h.n) if d25 else evaluate.surface_spec(11, 11, w.h.n)
+        spec = {"d25": lambda: evaluate.surface_spec(25, 25, w.h.n),
+                "d11": lambda: evaluate.surface_spec(11, 11, w.h.n),
+                "bb144": lambda: evaluate.bb_spec("bb144")}[args.workload]()
         f = evaluate.logical_failures(spec, torch.from_numpy(err_h[0].view(np.int64)).cuda(), o.err,
                                       o.converged, o.osd)
         k = int(f.sum().item())
         line["quality"] = {"ler": k / B, "ler_ci95": evaluate.wilson(k, B), "shots": B, "logical_failures": k,
                            "note": "BP alone (no OSD in this configuration): an unconverged shot counts as a "
-                                   "logical failure"}
+                                   "logical failure" if d25 else "Lottery BP + OSD-0"}
 
     if not args.no_extras and rank == 0 and world == 1 and d25:
         del outs, ws
