@@ -361,6 +361,9 @@ def run_gpu(args):
         S_t, G_t, gf_t = lbp.lbp_code_tuned(dec.code, prms[0].msg, prms[0].rule)
         launch = {"groups_per_cta": S_t, "threads_per_shot": G_t,
                   "graph": {0: "default", 1: "index image", 2: "implicit", 3: "round"}.get(gf_t, str(gf_t))}
+        _, S_e, G_e, _, _ = lbp.lbp_code_options(dec.code)
+        if S_e and G_e:          # LBP_BP_SHAPE, read at load, takes precedence over the tuned shape
+            launch.update(groups_per_cta=S_e, threads_per_shot=G_e, source="LBP_BP_SHAPE")
     for k in range(args.warmup):
         step(k)
     barrier()
