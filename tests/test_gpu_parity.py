@@ -139,17 +139,19 @@ def test_d25_split_state_equals_workspace_state(policy, monkeypatch):
     """FP32 messages at d=25 do not fit shared memory beside the posteriors,
     so by default the state is split: the first message slots stay in shared
     memory, the rest go to the workspace.  Forcing the whole state into the
-    workspace (two 512-thread groups per CTA) must give the same bits, and
-    both must match the oracle."""
+    workspace must give the same bits, with two 512-thread groups per CTA
+    (LBP_BP_SHAPE=2,512) and with four 256-thread groups (4,256); the split
+    one must match the oracle."""
     w = workloads.c5_d25_spacetime(msg=lbp.LBP_MSG_F32, shots=160)
     _, syn = sampler.sample(w.h, w.priors, seed=w.seed + policy, num_shots=w.shots)
     kw = dict(w.decoder, max_iter=50, lottery_policy=policy, seed=11)
     split = gpu_decode(w.h, w.priors, syn, **kw)
-    monkeypatch.setenv("LBP_BP_SHAPE", "2,512")
-    whole = gpu_decode(w.h, w.priors, syn, **kw)
-    for k in ("err", "conv", "iters", "osd"):
-        assert np.array_equal(split[k], whole[k]), k
-    assert np.array_equal(split["llr"].view(np.uint32), whole["llr"].view(np.uint32))
+    for shape in ("2,512", "4,256"):
+        monkeypatch.setenv("LBP_BP_SHAPE", shape)
+        other = gpu_decode(w.h, w.priors, syn, **kw)
+        for k in ("err", "conv", "iters", "osd"):
+            assert np.array_equal(split[k], other[k]), (shape, k)
+        assert np.array_equal(split["llr"].view(np.uint32), other["llr"].view(np.uint32)), shape
     assert_parity(split, oracle_decode(w.h, w.priors, syn, **kw))
 
 
