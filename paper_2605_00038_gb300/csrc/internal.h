@@ -165,8 +165,9 @@ struct lbp_code {
     // so that decodes of a loaded code never depend on the environment at
     // call time: LBP_GRAPH (0 unset, 1 table, 2 implicit, 3 round),
     // LBP_BP_SHAPE "S,G" (0, 0 unset), LBP_OSD_POOL_ROWS (0 unset) and
-    // LBP_OSD_LAT (0: latency layout off), LBP_OSD_DENSE (0: dense OSD off).
-    int env_graph, env_S, env_G, env_pool_rows, env_osd_lat, env_osd_dense;
+    // LBP_OSD_LAT (0: latency layout off), LBP_OSD_DENSE (0: dense OSD off),
+    // LBP_BANK_LAYOUT (0: bank-aware index image off).
+    int env_graph, env_S, env_G, env_pool_rows, env_osd_lat, env_osd_dense, env_bank_layout;
     // Dense OSD (K_osd_dense) for codes with m <= 160 and n + 1 <= 320 and a
     // 16-bit image: rows per lane, 64-bit words per augmented row, rank(H)
     // over GF(2); osd_dense = 0 when the code takes the event-driven kernels.

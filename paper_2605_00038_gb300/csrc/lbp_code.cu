@@ -324,6 +324,8 @@ void read_env_switches(lbp_code *c) {
     c->env_osd_lat = (lat && !std::strcmp(lat, "0")) ? 0 : 1;
     const char *dn = std::getenv("LBP_OSD_DENSE");
     c->env_osd_dense = (dn && !std::strcmp(dn, "0")) ? 0 : 1;
+    const char *bl = std::getenv("LBP_BANK_LAYOUT");
+    c->env_bank_layout = (bl && !std::strcmp(bl, "0")) ? 0 : 1;
 }
 
 // Rank of H over GF(2) (rows as packed 64-bit words, forward elimination).
@@ -492,8 +494,7 @@ extern "C" int lbp_load_code(int32_t m, int32_t n, const int32_t *row_ptr, const
         // pattern of its checks), and the pair table regroups the check phase.
         const int32_t Rr = (R + 31) & ~31;
         const uint32_t tab_bytes = align16(off + 2u * static_cast<uint32_t>(Mp / 2));
-        const char *bl = std::getenv("LBP_BANK_LAYOUT");
-        if (!(bl && !std::strcmp(bl, "0")) && fits16 && static_cast<int64_t>(ell_dc) * Rr < 65536 &&
+        if (c->env_bank_layout && fits16 && static_cast<int64_t>(ell_dc) * Rr < 65536 &&
             static_cast<size_t>(tab_bytes) + lbp::ell_state_bytes(4, ell_dc, Rr, Np, m) <=
                 static_cast<size_t>(c->smem_optin)) {
             R = Rr;
