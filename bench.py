@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=6144, help="oracle shots for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=192, help="oracle shots per step of --impl reference")
     ap.add_argument("--no-tune", action="store_true", help="skip lbp_tune (default launch shape)")
+    ap.add_argument("--rule", choices=["min_sum", "sum_product"], default="min_sum",
+                    help="check-node rule of the main line (the configurations use min-sum)")
     ap.add_argument("--serving-only", action="store_true", help="print the serving and matched-LER results only")
     return ap.parse_args()
 
@@ -325,6 +327,8 @@ def run_gpu(args):
     from paper_2605_00038_gb300.inputs import sampler
 
     w = workload(args.shots, args.workload)
+    if args.rule == "sum_product":
+        w.decoder["rule"] = lbp.LBP_RULE_SUM_PRODUCT
     B = w.shots
     d25 = args.workload == "d25"
     msg = w.decoder["msg"]
@@ -404,7 +408,7 @@ def run_gpu(args):
                    "shots_per_step_per_rank": B, "configuration_shots": N_BATCHES * B,
                    "decoder": "lottery_bp(proposed rule, skip 6, adaptive scale, I=100)" +
                               (", no OSD" if d25 else " + osd0"),
-                   "msg": MSG_NAME[msg],
+                   "msg": MSG_NAME[msg], "check_rule": args.rule,
                    "l2": "%d rotating input batches of %d MB syndromes, each > L2" % (
                        N_BATCHES, B * wm * 8 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single"},
