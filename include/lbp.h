@@ -440,6 +440,14 @@ int lbp_timing_read(double *bp_ms, int64_t *bp_launches, double *osd_ms, int64_t
  * [1, 2^20], NULL outputs), LBP_ENOMEM, LBP_ECUDA. */
 int lbp_probe_smem(int32_t trips, double *bytes, float *ms, void *stream);
 
+/* Gallager's function phi(x) = ln((e^x + 1) / (e^x - 1)) as the sum-product
+ * check-node rule evaluates it on the device (the magnitude rule of the
+ * tanh form, 2 atanh(prod tanh(|a|/2)) = phi(sum phi(|a|))): out[i] =
+ * phi(x[i]) for n device floats x >= 0, asynchronous on `stream`.  For
+ * measuring that evaluation's accuracy; not part of a decode.  Errors:
+ * LBP_EINVAL (n < 0, NULL buffers with n > 0), LBP_ECUDA. */
+int lbp_probe_phi(const float *x, float *out, int64_t n, void *stream);
+
 /* Static text for an LBP_* code. */
 const char *lbp_strerror(int code);
 

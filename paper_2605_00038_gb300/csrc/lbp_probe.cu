@@ -86,3 +86,27 @@ extern "C" int lbp_probe_smem(int32_t trips, double *bytes, float *ms, void *str
     cudaEventDestroy(b);
     return rc;
 }
+
+// lbp_probe_phi: out[i] = phi(x[i]) with the device function the sum-product
+// check-node rule uses (bp_common.cuh), so that its accuracy can be measured
+// against a binary64 evaluation.
+#include "bp_common.cuh"
+
+namespace {
+
+__global__ void phi_probe_kernel(const float *x, float *out, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = lbp::gallager_phi(x[i]);
+}
+
+}  // namespace
+
+extern "C" int lbp_probe_phi(const float *x, float *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) return LBP_EINVAL;
+    if (n == 0) return LBP_OK;
+    const int64_t blocks = (n + 255) / 256;
+    phi_probe_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0,
+                       static_cast<cudaStream_t>(stream)>>>(x, out, n);
+    return cudaGetLastError() == cudaSuccess ? LBP_OK : LBP_ECUDA;
+}

@@ -30,7 +30,7 @@ EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_in
             "lbp_workspace_size", "lbp_decode", "lbp_tune", "lbp_host_workspace_size", "lbp_decode_host",
             "lbp_server_create", "lbp_server_configure", "lbp_server_submit", "lbp_server_poll",
             "lbp_server_wait", "lbp_server_destroy", "lbp_graph_create", "lbp_graph_launch",
-            "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_probe_smem",
+            "lbp_graph_destroy", "lbp_decode_noalloc", "lbp_timing_enable", "lbp_timing_read", "lbp_probe_smem", "lbp_probe_phi",
             "lbp_batch_workspace_size", "lbp_decode_batch", "lbp_server_set_batching",
             "lbp_strerror"]
 
@@ -87,6 +87,8 @@ def lib():
         L.lbp_code_osd_form.argtypes = [vp, vp, vp]
         L.lbp_probe_smem.restype = ctypes.c_int
         L.lbp_probe_smem.argtypes = [i32, vp, vp, vp]
+        L.lbp_probe_phi.restype = ctypes.c_int
+        L.lbp_probe_phi.argtypes = [vp, vp, i64, vp]
         L.lbp_batch_workspace_size.restype = sz
         L.lbp_batch_workspace_size.argtypes = [vp, i32]
         L.lbp_decode_batch.restype = ctypes.c_int
@@ -237,6 +239,11 @@ def lbp_code_options(code: Code):
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().lbp_code_options(code.ptr, *[ctypes.byref(x) for x in v]), "lbp_code_options")
     return tuple(x.value for x in v)
+
+
+def lbp_probe_phi(x, out, stream=None):
+    """out[i] = phi(x[i]) on the device (float32 tensors, same length)."""
+    _check(lib().lbp_probe_phi(_dptr(x), _dptr(out), int(x.numel()), _stream_handle(stream)), "lbp_probe_phi")
 
 
 def lbp_probe_smem(trips: int = 4096, stream=None):
