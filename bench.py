@@ -563,7 +563,7 @@ def latency_sweep(dec, prm, syn_d, sizes, stream):
 
 
 def run_c5_precision(syn0, err0, args, timed_shots: int = 1 << 18, oracle_shots: int = 4096):
-    """Precision sweep of the d=25 workload (BASELINE's fifth configuration):
+    """Precision sweep of the d=25 workload (rotated d=25 space-time code, 2^20 shots):
     FP32 / FP16 / INT8 messages on the same shots, each timed on one batch of
     2^18 shots (tuned launch shape), with its logical error rate (BP alone, an
     unconverged shot fails) and the paired comparison with the FP64 oracle on
@@ -648,7 +648,7 @@ def lbp_tuned(dec, prm):
 
 
 def run_c2_leg(args, shots: int = 1_000_000, steps: int = 5, warmup: int = 3):
-    """The rotated d=11 space-time workload (BASELINE's second configuration):
+    """The rotated d=11 space-time workload (10^6 shots, Lottery BP + OSD-0, FP32):
     Lottery BP + OSD-0, FP32 messages, 10^6 shots per step, three rotating
     batches (88 MB of syndromes each), tuned launch shape; shots/s device
     resident and end to end, kernel times, OSD invoke rate, iteration
@@ -764,7 +764,7 @@ def run_c2_leg(args, shots: int = 1_000_000, steps: int = 5, warmup: int = 3):
 
 
 def run_c3_leg(shots: int = 1_000_000, oracle_shots: int = 100_000):
-    """BB [[144,12,12]] code capacity (BASELINE's third configuration):
+    """BB [[144,12,12]] code capacity (10^6 shots per p, Lottery BP + OSD-0, FP16):
     Lottery BP + OSD-0 with FP16 messages, p in {0.01, 0.03, 0.05}, 10^6 shots
     each (tuned launch shape): shots/s, OSD invoke rate, mean iterations,
     logical error rate with its Wilson interval, and the paired comparison

@@ -54,7 +54,7 @@ def test_c1_ler_matches_fp64_oracle_over_1e6_shots():
 
 
 def test_bb144_ler_matches_fp64_oracle_over_1e6_shots():
-    """BB [[144,12,12]] at p = 0.05 (BASELINE's third configuration), Lottery
+    """BB [[144,12,12]] at p = 0.05 (code capacity, 10^6 shots), Lottery
     BP + OSD-0: FP32 GPU against the FP64 oracle on the same 10^6 shots."""
     w = workloads.c3_bb144(0.05, shots=1_000_000)
     kw = dict(w.decoder, msg=lbp.LBP_MSG_F32, seed=3)
