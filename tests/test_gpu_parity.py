@@ -535,6 +535,47 @@ def test_bench_launch_config_full_size_sampled():
         assert not bad.any()
 
 
+@pytest.mark.parametrize("p", [0.01, 0.05])
+def test_bb144_full_size_sampled(p):
+    """BB [[144,12,12]] at the benchmark's 10^6 shots per p, FP16 messages, in
+    its launch configuration (lbp_tune on the first 16,384 shots, then one
+    decode; OSD-0 in the dense register form): sampled shots, a quarter of
+    them OSD shots, match the FP16 oracle one by one (decisions, flags,
+    iteration counts, OSD status), and every converged or OSD shot reproduces
+    its syndrome (H e_hat = s, on the GPU)."""
+    w = workloads.c3_bb144(p)
+    _, syn = sampler.sample(w.h, w.priors, seed=w.seed, num_shots=w.shots)
+    dec = Decoder(w.h, w.priors)
+    prm = dec.params(**w.decoder, seed=w.seed)
+    x = torch.from_numpy(syn.view(np.int64)).cuda()
+    dec.tune(x[:16384].contiguous(), prm)
+    out = dec.decode(x, prm)
+    torch.cuda.synchronize()
+    g = dict(err=sampler.unpack(out.err.cpu().numpy().view(np.uint64), w.h.n), conv=out.converged.cpu().numpy(),
+             osd=out.osd.cpu().numpy(), iters=out.iters.cpu().numpy())
+    dec.close()
+    rng = np.random.default_rng(1)
+    osd_shots = np.nonzero(g["osd"] != lbp.LBP_OSD_NOT_RUN)[0]
+    assert osd_shots.size >= 100
+    pick = np.unique(np.concatenate([rng.choice(w.shots, size=300, replace=False),
+                                     rng.choice(osd_shots, size=100, replace=False)]))
+    for b in pick:
+        r = oracle_decode(w.h, w.priors, syn[b:b + 1], shot_offset=int(b), **dict(w.decoder, seed=w.seed))
+        osd_ref = (lbp.LBP_OSD_APPLIED if r.osd_used[0] else
+                   (lbp.LBP_OSD_NO_SOLUTION if r.osd_nosol[0] else lbp.LBP_OSD_NOT_RUN))
+        assert g["conv"][b] == r.converged[0] and g["iters"][b] == r.iters[0], b
+        assert g["osd"][b] == osd_ref, b
+        assert np.array_equal(g["err"][b], r.err[0]), b
+    Hd = torch.from_numpy(w.h.to_dense().astype(np.float32)).cuda()
+    ok = (g["conv"] == 1) | (g["osd"] == lbp.LBP_OSD_APPLIED)
+    assert ok.mean() > 0.99
+    for lo in range(0, w.shots, 200_000):
+        e = torch.from_numpy(g["err"][lo:lo + 200_000].astype(np.float32)).cuda()
+        s_ = torch.from_numpy(sampler.unpack(syn[lo:lo + 200_000], w.h.m).astype(np.float32)).cuda()
+        bad = (torch.remainder(e @ Hd.T, 2) != s_).any(1).cpu().numpy() & ok[lo:lo + 200_000]
+        assert not bad.any()
+
+
 def test_bench_headline_launch_config_sampled():
     """The d=25 workload at the benchmark's batch (2^18 shots, a quarter of
     the configuration's 2^20) in the benchmark's launch configuration
