@@ -1094,6 +1094,34 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
                                     "osd_invoke_rate": float((r.osd != 0).float().mean().item()),
                                     "mean_iters": float(r.iters.float().mean().item())}
             fam["lottery_alg3_skip_sweep"] = sweep
+        # The iteration cap: the same shots at I = 300 (the cap the paper's
+        # accuracy comparisons quote), batched, each arm against plain BP +
+        # OSD-0 at I = 100 above and at I = 300.
+        cap = {}
+        f300 = None
+        for arm, kw in (("plain_bp_osd_fp32", dict(lottery=0, msg=0)),
+                        ("lottery_alg3_bp_osd_int8", dict(lottery=1, msg=2)),
+                        ("lottery_alg3_bp_osd_fp32", dict(lottery=1, msg=0)),
+                        ("lottery_worst_unreliable_bp_osd_int8",
+                         dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE))):
+            prm = dec.params(max_iter=300, osd=1, seed=seed, **kw)
+            r = dec.decode(sd, prm)
+            torch.cuda.synchronize()
+            f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+            k = int(f.sum().item())
+            res = {"ler": k / shots, "osd_invoke_rate": float((r.osd != 0).float().mean().item()),
+                   "mean_iters": float(r.iters.float().mean().item()),
+                   "ler_relative_difference_vs_plain_i100": (k - ka) / max(ka, 1),
+                   "mcnemar_p_vs_plain_i100": evaluate.mcnemar_p(int((fa & ~f).sum().item()),
+                                                                 int((f & ~fa).sum().item()))}
+            if f300 is None:
+                f300, k300 = f, k
+            else:
+                res["ler_relative_difference_vs_plain_i300"] = (k - k300) / max(k300, 1)
+                res["mcnemar_p_vs_plain_i300"] = evaluate.mcnemar_p(int((f300 & ~f).sum().item()),
+                                                                    int((f & ~f300).sum().item()))
+            cap[arm] = res
+        fam["iteration_cap_300"] = cap
         out["families"][name] = fam
         dec.close()
     return out
