@@ -1000,8 +1000,10 @@ def _served(dec, prms, hs, hbuf, load, rng):
 def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load: float = 0.8):
     """Matched-LER head-to-head on identical shots: (A) plain NMS BP + OSD-0
     with FP32 messages against Lottery BP + OSD-0 with INT8 (Int3.4) messages
-    and the paper's rule (Alg. 3), and with the worst-check /
-    least-reliable-column rule of Sec. III-B, on the code families the paper
+    and the paper's rule (Alg. 3), with the worst-check /
+    least-reliable-column rule of Sec. III-B, and with Alg. 3 drawing from
+    this iteration's s_hat instead of the previous one (an ablation of the
+    delay the paper adopts for pipelining), on the code families the paper
     evaluates (the BB [[144,12,12]] code at p = 0.03 and 0.05, code capacity;
     the unrotated surface code's space-time matrix, Table III rows, d = 7,
     7 rounds, p = 0.01) and on the rotated d = 7 space-time code (p = 0.012);
@@ -1047,7 +1049,10 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
         arms = [("plain_bp_osd_fp32", dict(lottery=0, msg=0, lottery_policy=0)),
                 ("lottery_alg3_bp_osd_int8", dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_PROPOSED)),
                 ("lottery_worst_unreliable_bp_osd_int8",
-                 dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE))]
+                 dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_WORST_UNRELIABLE)),
+                # Alg. 3 with U from this iteration's s_hat (an ablation of its delay).
+                ("lottery_alg3_current_syndrome_bp_osd_int8",
+                 dict(lottery=1, msg=2, lottery_policy=lbp.LBP_LOTTERY_PROPOSED_CURRENT))]
         fam = {"shape": [h.m, h.n, h.nnz]}
         fa = None
         for arm, kw in arms:
@@ -1122,6 +1127,23 @@ def run_matched(shots: int = 1 << 20, request: int = 4096, seed: int = 21, load:
                                                                     int((f & ~f300).sum().item()))
             cap[arm] = res
         fam["iteration_cap_300"] = cap
+        # Ablation of the lottery's delay (reading R6): Alg. 3 with U from this
+        # iteration's s_hat (policy 5), INT8, batched, at I = 300 (its I = 100
+        # arm is served above).
+        abl = {}
+        for cap_i, ref_f, ref_k in ((300, f300, k300),):
+            prm = dec.params(max_iter=cap_i, osd=1, seed=seed, lottery=1, msg=2,
+                             lottery_policy=lbp.LBP_LOTTERY_PROPOSED_CURRENT)
+            r = dec.decode(sd, prm)
+            torch.cuda.synchronize()
+            f = evaluate.logical_failures(spec, true_d, r.err, r.converged, r.osd)
+            k = int(f.sum().item())
+            abl["I%d" % cap_i] = {"ler": k / shots, "osd_invoke_rate": float((r.osd != 0).float().mean().item()),
+                                  "mean_iters": float(r.iters.float().mean().item()),
+                                  "ler_relative_difference_vs_plain_same_cap": (k - ref_k) / max(ref_k, 1),
+                                  "mcnemar_p_vs_plain_same_cap": evaluate.mcnemar_p(
+                                      int((ref_f & ~f).sum().item()), int((f & ~ref_f).sum().item()))}
+        fam["lottery_alg3_current_syndrome_int8"] = abl
         out["families"][name] = fam
         dec.close()
     return out

@@ -63,6 +63,9 @@ extern "C" {
 #define LBP_LOTTERY_WORST_RANDOM      2
 #define LBP_LOTTERY_RANDOM_UNRELIABLE 3
 #define LBP_LOTTERY_RANDOM_RANDOM     4
+/* Not Alg. 3: an ablation of its delay.  As LBP_LOTTERY_PROPOSED, but U is
+ * built from this iteration's s_hat(i) instead of s_hat(i-1). */
+#define LBP_LOTTERY_PROPOSED_CURRENT  5
 
 /* Check-node rule.  LBP_RULE_MIN_SUM is the normalised min-sum update of
  * Alg. 1.  LBP_RULE_SUM_PRODUCT is the tanh rule

@@ -66,7 +66,8 @@ typedef struct {
     int32_t rule;         /* 0: normalised min-sum (Alg. 1); 1: sum-product tanh rule */
     int32_t policy;       /* lottery policy, Sec. III-B: 0 proposed (Alg. 3), 1 worst CN +
                              unreliable VN, 2 worst CN + random VN, 3 random CN + unreliable VN,
-                             4 random CN + random VN */
+                             4 random CN + random VN; 5 (an ablation, not in the paper) as 0
+                             with U from this iteration's s_hat(i) */
     uint64_t seed;
     uint64_t shot_offset;
 } oracle_params;
@@ -448,12 +449,13 @@ static void decode_one(shot_ws *w, uint64_t gshot, const uint8_t *s, uint8_t *e_
             int match = 1;
             for (int c = 0; c < m; ++c) if (w->shat[c] != (s[c] & 1)) { match = 0; break; }
             if (match) { converged = 1; iters = i + 1; break; }
-            /* Alg. 3, from s_hat(i-1). */
+            /* Alg. 3, from s_hat(i-1) (policy 5: from s_hat(i), otherwise policy 0). */
             if (prm->lottery && i >= prm->lottery_skip && i < I - 1) {
-                for (int c = 0; c < m; ++c) w->U[c] = (uint8_t)(w->shat_prev[c] ^ (s[c] & 1));
+                const uint8_t *sh = prm->policy == 5 ? w->shat : w->shat_prev;
+                for (int c = 0; c < m; ++c) w->U[c] = (uint8_t)(sh[c] ^ (s[c] & 1));
                 uint64_t ctr = (gshot << 24) + (uint64_t)i;
                 uint64_t r = oracle_splitmix64_at(prm->seed, ctr);
-                int vstar = lottery_select(g, w->U, w->lam, r, prm->policy, NULL);
+                int vstar = lottery_select(g, w->U, w->lam, r, prm->policy == 5 ? 0 : prm->policy, NULL);
                 if (vstar >= 0) w->lam[vstar] = -w->lam[vstar];
             }
         }
@@ -528,7 +530,7 @@ int oracle_decode(int m, int n, const int32_t *row_ptr, const int32_t *col_idx,
     if (prm->prec < PREC_F64 || prm->prec > PREC_I8) return -1;
     if (prm->rule == RULE_SUM_PRODUCT && prm->prec != PREC_F64) return -1;
     if (prm->lottery_skip < 0 || prm->max_iter >= (1 << 24)) return -1;
-    if (prm->policy < 0 || prm->policy > 4) return -1;
+    if (prm->policy < 0 || prm->policy > 5) return -1;
     graph_t g;
     int rc = graph_init(&g, m, n, row_ptr, col_idx);
     if (rc) return rc;

@@ -54,7 +54,7 @@ class OracleParams:
     prec: int = PREC_F64
     early_exit: bool = True
     rule: int = RULE_MIN_SUM
-    policy: int = 0              # lottery policy: 0 proposed, 1..4 baselines (Sec. III-B)
+    policy: int = 0              # lottery policy: 0 proposed, 1..4 baselines (Sec. III-B), 5 ablation (U from s_hat(i))
     seed: int = 0
     shot_offset: int = 0
 

@@ -206,7 +206,10 @@ __global__ void __launch_bounds__(1024, 1) bp_kernel(const BpArgs a) {
             // ---- lottery (Alg. 3, or a baseline policy of Sec. III-B) ---------
             if (a.lottery && it >= a.lottery_skip && it < I - 1) {
                 if (t < 32) {
-                    const uint32_t *sp = shat + prev * W32;
+                    // The ablation policy draws like Alg. 3 from this iteration's s_hat.
+                    const bool cur_u = a.policy == LBP_LOTTERY_PROPOSED_CURRENT;
+                    const int pol = cur_u ? LBP_LOTTERY_PROPOSED : a.policy;
+                    const uint32_t *sp = cur_u ? sh_cur : shat + prev * W32;
                     uint32_t N = 0;
                     for (int w0 = 0; w0 < W32; w0 += 32) {
                         const int w = w0 + lane;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(1024, 1) bp_kernel(const BpArgs a) {
                         const uint64_t r64 = splitmix64_at(a.seed, (g << 24) + static_cast<uint64_t>(it));
                         const uint32_t u = static_cast<uint32_t>(r64), u2 = static_cast<uint32_t>(r64 >> 32);
                         int cstar = -1;
-                        if (a.policy == LBP_LOTTERY_WORST_UNRELIABLE || a.policy == LBP_LOTTERY_WORST_RANDOM) {
+                        if (pol == LBP_LOTTERY_WORST_UNRELIABLE || pol == LBP_LOTTERY_WORST_RANDOM) {
                             // Worst CN: most columns estimated in error, lowest row on ties.
                             int bn = -1, bcr = 0x7fffffff;
                             for (int w = lane; w < W32; w += 32) {
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(1024, 1) bp_kernel(const BpArgs a) {
                         }
                         int bc = -1, bv = 0x7fffffff;
                         float ba = 0.0f;
-                        if (a.policy == LBP_LOTTERY_WORST_RANDOM || a.policy == LBP_LOTTERY_RANDOM_RANDOM) {
+                        if (pol == LBP_LOTTERY_WORST_RANDOM || pol == LBP_LOTTERY_RANDOM_RANDOM) {
                             // Random VN: column floor(u2 deg / 2^32) of c*.
                             const int e0 = row_ptr[cstar];
                             const int deg = row_ptr[cstar + 1] - e0;
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(1024, 1) bp_kernel(const BpArgs a) {
                             if (lane < deg) {
                                 bv = col_idx[e0 + lane];
                                 bc = 0;
-                                if (a.policy == LBP_LOTTERY_PROPOSED) {
+                                if (pol == LBP_LOTTERY_PROPOSED) {
                                     for (int j = col_ptr[bv]; j < col_ptr[bv + 1]; ++j) {
                                         const int r = csc_row[j];
                                         bc += ((sp[r >> 5] ^ s_w[r >> 5]) >> (r & 31)) & 1u;

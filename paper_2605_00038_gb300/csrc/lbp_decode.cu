@@ -96,7 +96,7 @@ int validate_params(const lbp_params *p) {
     if (p->lottery_skip < 0) return LBP_EINVAL;
     if (p->osd != 0 && p->osd != 1) return LBP_EINVAL;
     if (p->msg != LBP_MSG_F32 && p->msg != LBP_MSG_F16 && p->msg != LBP_MSG_I8) return LBP_EINVAL;
-    if (p->lottery_policy < LBP_LOTTERY_PROPOSED || p->lottery_policy > LBP_LOTTERY_RANDOM_RANDOM) return LBP_EINVAL;
+    if (p->lottery_policy < LBP_LOTTERY_PROPOSED || p->lottery_policy > LBP_LOTTERY_PROPOSED_CURRENT) return LBP_EINVAL;
     if (p->rule != LBP_RULE_MIN_SUM && p->rule != LBP_RULE_SUM_PRODUCT) return LBP_EINVAL;
     if (p->reserved != 0) return LBP_EINVAL;
     return LBP_OK;

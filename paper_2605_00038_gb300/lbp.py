@@ -23,7 +23,7 @@ LBP_MSG_F32, LBP_MSG_F16, LBP_MSG_I8 = 0, 1, 2
 LBP_SCALE_CONST, LBP_SCALE_ADAPTIVE = 0, 1
 LBP_RULE_MIN_SUM, LBP_RULE_SUM_PRODUCT = 0, 1
 (LBP_LOTTERY_PROPOSED, LBP_LOTTERY_WORST_UNRELIABLE, LBP_LOTTERY_WORST_RANDOM,
- LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM) = range(5)
+ LBP_LOTTERY_RANDOM_UNRELIABLE, LBP_LOTTERY_RANDOM_RANDOM, LBP_LOTTERY_PROPOSED_CURRENT) = range(6)
 
 EXPORTED = ["lbp_params_default", "lbp_load_code", "lbp_free_code", "lbp_code_info", "lbp_code_surface",
             "lbp_code_rounds", "lbp_code_tuned", "lbp_code_options", "lbp_code_osd_form",

@@ -72,7 +72,7 @@ def test_decode_rejects_bad_params_without_gpu(L):
     rc = L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(bad), 1, None, None, None, None, None,
                       None, None, 0, None)
     assert rc == lbp.LBP_EINVAL
-    for kw in (dict(msg=7), dict(scale_mode=5), dict(lottery=2), dict(lottery_policy=5), dict(rule=2), dict(reserved=1),
+    for kw in (dict(msg=7), dict(scale_mode=5), dict(lottery=2), dict(lottery_policy=6), dict(rule=2), dict(reserved=1),
                dict(scale_mode=0, scale_const=0.0), dict(lottery_skip=-1)):
         p = lbp.lbp_params_default(**kw)
         assert L.lbp_decode(ctypes.c_void_p(1), ctypes.byref(p), 1, None, None, None, None, None,

@@ -134,7 +134,7 @@ def test_c5_d25_spacetime_precisions(msg):
     assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
 
 
-@pytest.mark.parametrize("policy", [0, 1, 4])
+@pytest.mark.parametrize("policy", [0, 1, 4, 5])
 def test_d25_split_state_equals_workspace_state(policy, monkeypatch):
     """FP32 messages at d=25 do not fit shared memory beside the posteriors,
     so by default the state is split: the first message slots stay in shared
@@ -167,9 +167,10 @@ def test_c5_d25_xz_stress_form(msg):
     assert_parity(gpu_decode(w.h, w.priors, syn, **kw), oracle_decode(w.h, w.priors, syn, **kw))
 
 
-@pytest.mark.parametrize("policy", [1, 2, 3, 4])
+@pytest.mark.parametrize("policy", [1, 2, 3, 4, 5])
 def test_lottery_baseline_policies(policy):
-    """The four baseline sign-flip policies of Sec. III-B, on the bounded-degree
+    """The four baseline sign-flip policies of Sec. III-B and the ablation that
+    draws Alg. 3 from this iteration's s_hat (policy 5), on the bounded-degree
     kernel (d=7 space-time code, BB72) and the general kernel (high degree)."""
     hz, _ = rotated_surface(7)
     st = spacetime(hz, 7)
@@ -208,7 +209,7 @@ def test_bank_layout_changes_nothing(msg, rule, monkeypatch):
         assert_parity(a, oracle_decode(w.h, w.priors, syn, **kw))
 
 
-@pytest.mark.parametrize("policy", range(5))
+@pytest.mark.parametrize("policy", range(6))
 @pytest.mark.parametrize("msg", [lbp.LBP_MSG_F32, lbp.LBP_MSG_F16, lbp.LBP_MSG_I8])
 def test_small_batch_wide_groups(policy, msg, monkeypatch):
     """A batch of at most one shot per SM runs one shot per CTA with a thread

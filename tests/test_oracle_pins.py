@@ -605,3 +605,35 @@ def test_lottery_reads_previous_iteration_syndrome():
     assert r.converged[0] == 0 and r.iters[0] == 2
     assert r.llr[0].tolist() == want
     assert r.err[0].tolist() == [0, 1, 0]
+
+
+def test_lottery_ablation_reads_current_syndrome():
+    """Policy 5 (an ablation of reading R6, not in the paper) builds U from this
+    iteration's s_hat(i) and otherwise follows Alg. 3.  On the chain of the
+    previous pin: s_hat(0) = (1, 1), so U = {c1} and c* = c1; v1 and v2 each
+    meet one member of U, and |lambda_2| = 1.5 < |lambda_1| = 3.5 picks v2:
+    lambda_2 -> -1.5.  Iteration 1 (f = 3/4), from the flipped posterior:
+    alpha = (mu0, 1.5 | -4, -2) up to the exact mu, beta = (-0.75 alpha_1c0,
+    -0.75 alpha_0c0 | 0.75 alpha_2c1, 0.75 alpha_1c1), lambda ~ (8.875, -8, -2):
+    e_hat = {v1, v2}, s_hat = (1, 0) = s, so the decode converges at
+    iteration 1.  The expected bits repeat these operations in numpy float64."""
+    h = SparseH.from_rows([[0, 1], [1, 2]], 3)
+    target = np.array([10.0, 1.0, 1.0])
+    p = 1.0 / (1.0 + np.exp(target))
+    mu = mu_of(p)
+    S = np.array([[1, 0]], dtype=np.uint8)
+    r = oracle.decode(h, p, S, OracleParams(max_iter=2, lottery=True, lottery_skip=0, osd=False, prec=PREC_F64,
+                                            policy=5), want_llr=True)
+    b00, b10, b11, b21 = -(0.5 * mu[1]), -(0.5 * mu[0]), 0.5 * mu[2], 0.5 * mu[1]
+    lam = np.array([mu[0] + b00, (mu[1] + b10) + b11, mu[2] + b21])
+    assert abs(lam[2]) < abs(lam[1])
+    lam[2] = -lam[2]                                              # c* = c1, v* = v2
+    a00, a10, a11, a21 = lam[0] - b00, lam[1] - b10, lam[1] - b11, lam[2] - b21
+    assert a00 > 0 and a10 > 0 and a11 < 0 and a21 < 0
+    b00, b10 = -(0.75 * a10), -(0.75 * a00)
+    b11, b21 = 0.75 * a21, 0.75 * a11
+    want = [mu[0] + b00, (mu[1] + b10) + b11, mu[2] + b21]
+    assert want[0] > 0 and want[1] <= 0 and want[2] <= 0
+    assert r.converged[0] == 1 and r.iters[0] == 2
+    assert r.llr[0].tolist() == want
+    assert r.err[0].tolist() == [0, 1, 1]
