@@ -64,7 +64,10 @@ extern "C" {
 #define LBP_LOTTERY_RANDOM_UNRELIABLE 3
 #define LBP_LOTTERY_RANDOM_RANDOM     4
 /* Not Alg. 3: an ablation of its delay.  As LBP_LOTTERY_PROPOSED, but U is
- * built from this iteration's s_hat(i) instead of s_hat(i-1). */
+ * built from this iteration's s_hat(i) instead of s_hat(i-1).  Built into the
+ * index-image form in shared memory and the general kernel; a decode whose
+ * plan takes another form (a code whose image does not fit shared memory, the
+ * implicit or round-periodic graph, a merged launch) returns LBP_ENOSYS. */
 #define LBP_LOTTERY_PROPOSED_CURRENT  5
 
 /* Check-node rule.  LBP_RULE_MIN_SUM is the normalised min-sum update of

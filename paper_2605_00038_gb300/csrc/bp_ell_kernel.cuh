@@ -305,10 +305,10 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             // lottery; a random check is drawn while the other warps finish
             // their check-phase rounds.
             const bool lw = t >= G - 32;
-            const bool early = lottery_random_check(LBP_ARG(policy));
-            // The ablation policy draws like Alg. 3 from this iteration's s_hat.
-            const bool cur_u = LBP_ARG(policy) == LBP_LOTTERY_PROPOSED_CURRENT;
-            const int pol = cur_u ? LBP_LOTTERY_PROPOSED : LBP_ARG(policy);
+            // (The ablation policy, U from this iteration's s_hat, exists in the
+            // shared-image form only and draws after the column phase.)
+            const bool early = lottery_random_check(LBP_ARG(policy)) &&
+                               !(kTab && LBP_ARG(policy) == LBP_LOTTERY_PROPOSED_CURRENT);
             int cpre = -1;
             uint32_t u2pre = 0;
             LotteryPrep lp;          // index-image instantiations in shared memory only
@@ -368,11 +368,11 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
                     uint32_t u2 = 0;
                     const uint32_t *sp = shat + prev * W32;
                     const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
-                                                          pol, lam, u2);
-                    lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, pol, m, R, LBP_ARG(magic));
+                                                          LBP_ARG(policy), lam, u2);
+                    lp = lottery_prepare<DC, DV>(gr, cs, u2, sp, s_w, lane, LBP_ARG(policy), m, R, LBP_ARG(magic));
                 } else {
                     cpre = lottery_check<DC>(gr, shat + prev * W32, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
-                                             pol, lam, u2pre);
+                                             LBP_ARG(policy), lam, u2pre);
                 }
             }
             group_sync<G>(bar);
@@ -460,6 +460,9 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             int vflip = -1;
             if constexpr (kTab) {
                 if (lot && lw) {
+                    // The ablation policy draws like Alg. 3 from this iteration's s_hat.
+                    const bool cur_u = LBP_ARG(policy) == LBP_LOTTERY_PROPOSED_CURRENT;
+                    const int pol = cur_u ? LBP_LOTTERY_PROPOSED : LBP_ARG(policy);
                     const uint32_t *sp = cur_u ? sh_cur : shat + prev * W32;
                     if (!early) {
                         uint32_t u2 = 0;
@@ -489,11 +492,11 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             if constexpr (!kTab) {
                 if (lot) {
                     if (lw) {
-                        const uint32_t *sp = cur_u ? sh_cur : shat + prev * W32;
+                        const uint32_t *sp = shat + prev * W32;
                         if (!early)
                             cpre = lottery_check<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b, it,
-                                                     pol, lam, u2pre);
-                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, pol, lam, m, R,
+                                                     LBP_ARG(policy), lam, u2pre);
+                        const int vs = lottery_column<DC, DV>(gr, cpre, u2pre, sp, s_w, lane, LBP_ARG(policy), lam, m, R,
                                                               LBP_ARG(magic));
                         if (lane == 0 && vs >= 0) lam[vs] = -lam[vs];
                     }

@@ -29,11 +29,9 @@
 namespace lbp {
 
 // True for the policies whose check depends only on U and the draw, not on
-// the posteriors of this iteration (so it can be drawn early).  The ablation
-// policy's U is this iteration's, so it is drawn after the column phase.
+// the posteriors of this iteration (so it can be drawn early).
 __device__ __forceinline__ bool lottery_random_check(int policy) {
-    return policy != LBP_LOTTERY_WORST_UNRELIABLE && policy != LBP_LOTTERY_WORST_RANDOM &&
-           policy != LBP_LOTTERY_PROPOSED_CURRENT;
+    return policy != LBP_LOTTERY_WORST_UNRELIABLE && policy != LBP_LOTTERY_WORST_RANDOM;
 }
 
 // First half: the check c* (or -1 when U is empty) and the high 32 bits u2

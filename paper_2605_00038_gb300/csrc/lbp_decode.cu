@@ -636,6 +636,11 @@ int decode_device_shaped(const lbp_code *c, const lbp_params *prm, int64_t B, co
     BpPlan bp;
     int rc = plan_bp(c, prm->msg, prm->rule, B, &bp, req_S, req_G, req_graph, alone);
     if (rc) return rc;
+    // The lottery ablation (U from this iteration's s_hat) is built into the
+    // index-image form in shared memory and the general kernel only.
+    if (prm->lottery_policy == LBP_LOTTERY_PROPOSED_CURRENT && bp.ell &&
+        !(bp.graph_smem && !bp.surface && !bp.round))
+        return LBP_ENOSYS;
     OsdPlan op;
     OsdWarpPlan wp;
     if (prm->osd) {
@@ -986,6 +991,7 @@ int plan_batch(const lbp_batch_item *items, int n, BatchPlan *P, bool size_only 
         if (it.code->device != dev) return LBP_EINVAL;
         const lbp_code *c = it.code;
         if (it.params.msg != P->msg || it.params.rule != LBP_RULE_MIN_SUM) return LBP_ENOSYS;
+        if (it.params.lottery_policy == LBP_LOTTERY_PROPOSED_CURRENT) return LBP_ENOSYS;
         if (!c->d_ell || c->ell.idx_bytes != 2) return LBP_ENOSYS;
         if (i == 0) { P->DC = c->ell.DC; P->DV = c->ell.DV; }
         if (c->ell.DC != P->DC || c->ell.DV != P->DV) return LBP_ENOSYS;
