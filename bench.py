@@ -193,7 +193,7 @@ def roofline_model(w, iters_total, shots):
 # 4,096-shot launch, divided by the shot-iterations it ran; the traffic of a
 # full launch scales with its shot-iterations.  Valid for the kernel sources
 # whose hash is recorded with it (None until captured).
-KBP_TRAFFIC = {"bytes_per_shot_iteration": 12.08, "source_sha1": "4613dd490f8a"}
+KBP_TRAFFIC = {"bytes_per_shot_iteration": 12.30, "source_sha1": "e101fdb95106"}
 
 
 def kbp_source_sha1():

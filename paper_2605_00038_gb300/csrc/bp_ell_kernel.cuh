@@ -460,11 +460,13 @@ __global__ void __launch_bounds__(kSplit ? G : 1024, 1) bp_ell_kernel(const BpEl
             int vflip = -1;
             if constexpr (kTab) {
                 if (lot && lw) {
-                    // The ablation policy draws like Alg. 3 from this iteration's s_hat.
-                    const bool cur_u = LBP_ARG(policy) == LBP_LOTTERY_PROPOSED_CURRENT;
-                    const int pol = cur_u ? LBP_LOTTERY_PROPOSED : LBP_ARG(policy);
-                    const uint32_t *sp = cur_u ? sh_cur : shat + prev * W32;
+                    const uint32_t *sp = shat + prev * W32;
                     if (!early) {
+                        // The ablation policy draws like Alg. 3 from this
+                        // iteration's s_hat (and is not drawn early).
+                        const bool cur_u = LBP_ARG(policy) == LBP_LOTTERY_PROPOSED_CURRENT;
+                        if (cur_u) sp = sh_cur;
+                        const int pol = cur_u ? LBP_LOTTERY_PROPOSED : LBP_ARG(policy);
                         uint32_t u2 = 0;
                         const int cs = lottery_check_fast<DC>(gr, sp, s_w, W32, lane, LBP_ARG(seed), LBP_ARG(shot_offset) + b,
                                                               it, pol, lam, u2);
