@@ -32,7 +32,9 @@
  *   sign(x) = -1 iff x < 0 (so both zeros count as +1);
  *   e_v = 1 iff lambda_v <= 0 (Alg. 1 hard decision);
  *   the lottery at iteration i uses U from s_hat of iteration i-1, with
- *   s_hat(-1) = 0; it runs for lottery_skip <= i < I-1;
+ *   s_hat(-1) = 0; it runs for lottery_skip <= i < I-1 (policy 5, an
+ *   ablation outside the paper, takes U from s_hat of iteration i and
+ *   otherwise follows policy 0);
  *   RandomSelect: u = low 32 bits of SplitMix64 at counter (g << 24) + i for
  *   global shot index g, k = floor(u * N / 2^32), c* = k-th unsatisfied
  *   check in ascending row order (a random column, for the baseline policies,
