@@ -227,7 +227,7 @@ BufLayout buf_layout(const lbp_code *c, int64_t B) {
 bool mergeable(const Request &f, const Request &r) {
     const int64_t nf = f.code->n, nr = r.code->n;
     return r.params.msg == f.params.msg && r.params.rule == LBP_RULE_MIN_SUM && f.params.rule == LBP_RULE_MIN_SUM &&
-           r.code->d_ell && f.code->d_ell && r.code->ell.idx_bytes == 2 && f.code->ell.idx_bytes == 2 &&
+           r.params.lottery_policy != LBP_LOTTERY_PROPOSED_CURRENT && r.code->d_ell && f.code->d_ell && r.code->ell.idx_bytes == 2 && f.code->ell.idx_bytes == 2 &&
            r.code->ell.DC == f.code->ell.DC && r.code->ell.DV == f.code->ell.DV && nr <= 2 * nf && nf <= 2 * nr;
 }
 
@@ -302,8 +302,12 @@ void launch_merged(lbp_server *s, int si) {
 
 // Admit the oldest waiting request with the later requests that can share
 // its launch (up to batch_items, oldest first, as long as the arena has room
-// for all of them) into slot si.  Returns false when nothing could be admitted.
-bool admit_merged(lbp_server *s, int si) {
+// for all of them) into slot si.  Returns 1 when a group was admitted, 0 when
+// the arena has no room for it yet, and -1 when the oldest request cannot
+// take a merged launch even alone (lbp_decode_batch cannot plan it, or its
+// merged layout, which holds every shot's workspace at once, exceeds the
+// arena): it then runs as a single request.
+int admit_merged(lbp_server *s, int si) {
     const Request &f = s->waiting.front();
     std::vector<size_t> pick{0};
     for (size_t i = 1; i < s->waiting.size() && static_cast<int>(pick.size()) < s->batch_items; ++i)
@@ -314,6 +318,7 @@ bool admit_merged(lbp_server *s, int si) {
         std::vector<size_t> offs;
         size_t ws_off = 0;
         const size_t bytes = merged_bytes(g, &offs, &ws_off);
+        if (pick.size() == 1 && (bytes == 0 || bytes > s->arena.size)) return -1;
         size_t off = 0;
         if (bytes && s->arena.alloc(bytes, &off)) {
             Slot &sl = s->slots[si];
@@ -326,11 +331,11 @@ bool admit_merged(lbp_server *s, int si) {
             for (size_t k = pick.size(); k-- > 0;) s->waiting.erase(s->waiting.begin() + static_cast<long>(pick[k]));
             sl.busy = true;
             launch_merged(s, si);
-            return true;
+            return 1;
         }
         pick.pop_back();                     // smaller group, or wait for memory
     }
-    return false;
+    return 0;
 }
 
 void run(lbp_server *s) {
@@ -373,9 +378,12 @@ void run(lbp_server *s) {
             if (free_slot < 0) break;
             if (s->batch_items > 0 && s->waiting.front().params.rule == LBP_RULE_MIN_SUM &&
                 s->waiting.front().code->d_ell && s->waiting.front().code->ell.idx_bytes == 2) {
-                if (!admit_merged(s, free_slot)) break;           // wait for memory to free up
-                progressed = true;
-                continue;
+                const int a = admit_merged(s, free_slot);
+                if (a == 0) break;                                 // wait for memory to free up
+                if (a > 0) {
+                    progressed = true;
+                    continue;
+                }
             }
             Request &r = s->waiting.front();
             Layout L;

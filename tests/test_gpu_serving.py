@@ -4,7 +4,9 @@ Requests of several codes and sizes are submitted from two host threads while
 others run; every request's result must equal the same request decoded alone
 with lbp_decode (bit-identical: the decode of a shot depends only on its
 syndrome, the code and the parameters)."""
+import ctypes
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -146,4 +148,82 @@ def test_request_larger_than_the_arena_is_refused():
                               np.zeros(B, np.uint8), None, np.zeros(B, np.int32))
     assert ei.value.code == lbp.LBP_E2BIG
     srv.close()
+    dec.close()
+
+
+def _al256(x):
+    return (x + 255) // 256 * 256
+
+
+def _single_layout_bytes(dec, prm, B, chunk):
+    """Arena bytes of a request run alone: its buffers for B shots, then the
+    workspace of one launch of min(chunk, B) shots."""
+    h = dec.h
+    off = _al256(8 * ((h.m + 63) // 64) * B)
+    off = _al256(off + 8 * ((h.n + 63) // 64) * B)
+    off = _al256(off + B)
+    off = _al256(off + B)
+    off = _al256(off + 4 * B)
+    return _al256(off + lbp.lbp_workspace_size(dec.code, prm, min(chunk, B)))
+
+
+def _poll_all(srv, tickets, limit_s=120.0):
+    """Poll every ticket until it completes.  A request the scheduler never
+    admits fails the test instead of blocking it; the server is then left
+    undestroyed, since destroying it drains the queue."""
+    deadline = time.monotonic() + limit_s
+    pending = set(range(len(tickets)))
+    while pending:
+        for i in sorted(pending):
+            if lbp.lbp_server_poll(srv, tickets[i])[0]:
+                pending.discard(i)
+        if pending and time.monotonic() > deadline:
+            srv.ptr = ctypes.c_void_p()
+            pytest.fail(f"{len(pending)} of {len(tickets)} requests never completed")
+        threading.Event().wait(0.001)
+
+
+def test_requests_that_cannot_merge_run_alone():
+    """With merged launches on, a request that lbp_decode_batch cannot plan
+    (the lottery ablation policy) or whose merged layout, which holds the
+    workspace of every shot at once, exceeds the arena (a long request split
+    into 69-shot launches) runs as a single request; the requests behind it
+    still merge.  Every result equals the same request decoded alone."""
+    hx, _ = bb_code("bb144")
+    pri = np.full(hx.n, 0.02)
+    dec = Decoder(hx, pri)
+    chunk_work = 30000
+    chunk = chunk_work // hx.nnz
+    big = 20000
+    sizes = [big, 300, 200, 250, 180, 400, 220]
+    pols = [0, 5, 0, 5, 0, 0, 5]
+    reqs = []
+    for i, (B, pol) in enumerate(zip(sizes, pols)):
+        _, syn = sampler.sample(hx, pri, seed=60 + i, num_shots=B, shot_offset=1000 * i)
+        reqs.append(dict(B=B, off=1000 * i, syn=syn,
+                         prm=dec.params(max_iter=60, lottery=1, lottery_policy=pol, osd=1, seed=5,
+                                        shot_offset=1000 * i)))
+    ref = []
+    for r in reqs:
+        out = dec.decode(torch.from_numpy(r["syn"].view(np.int64)).cuda(), r["prm"])
+        torch.cuda.synchronize()
+        ref.append((out.err.cpu().numpy().view(np.uint64), out.converged.cpu().numpy(),
+                    out.osd.cpu().numpy(), out.iters.cpu().numpy()))
+    alone = _single_layout_bytes(dec, reqs[0]["prm"], big, chunk)
+    arena = _al256(alone * 5 // 4)
+    # The long request's merged workspace alone exceeds the arena.
+    assert lbp.lbp_workspace_size(dec.code, reqs[0]["prm"], big) > arena
+    srv = lbp.lbp_server_create(arena, 4)
+    lbp.lbp_server_configure(srv, chunk_work, True)
+    lbp.lbp_server_set_batching(srv, 8)
+    bufs = [dict(err=np.zeros((r["B"], (hx.n + 63) // 64), np.uint64), conv=np.zeros(r["B"], np.uint8),
+                 osd=np.zeros(r["B"], np.uint8), iters=np.zeros(r["B"], np.int32)) for r in reqs]
+    tickets = [lbp.lbp_server_submit(srv, dec.code, r["prm"], r["B"], r["syn"], b["err"], b["conv"],
+                                     b["osd"], b["iters"]) for r, b in zip(reqs, bufs)]
+    _poll_all(srv, tickets)
+    srv.close()
+    for i, (e, c, o, it) in enumerate(ref):
+        b = bufs[i]
+        assert np.array_equal(b["err"], e) and np.array_equal(b["conv"], c), i
+        assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it), i
     dec.close()
