@@ -108,3 +108,16 @@ def test_roofline_bytes_and_iteration_histogram():
     b = torch.tensor([100, 100, 7], dtype=torch.int32)
     assert bench.histogram([a, b]) == {"1": 1, "3": 2, "7": 1, "100": 3}
     assert bench.histogram([b, a]) == {"1": 1, "3": 2, "7": 1, "100": 3}
+
+
+def test_kbp_traffic_names_the_current_kernel_sources():
+    """roofline.traffic scales a per-shot-iteration DRAM figure from one ncu
+    capture of K_bp; it applies only to the kernel sources it was captured
+    from.  The figure, its profile summary and the sources as they stand
+    name the same hash: a kernel change without a new capture fails here."""
+    from pathlib import Path
+    t = bench.KBP_TRAFFIC
+    assert t["bytes_per_shot_iteration"] and t["source_sha1"] == bench.kbp_source_sha1()
+    prof = (Path(bench.__file__).parent / "profiles" / "bp_ell_kernel_rotated_d25_st25_split.md").read_text()
+    assert f"`{t['source_sha1']}`" in prof
+    assert f"| DRAM bytes per shot-iteration | {t['bytes_per_shot_iteration']:.1f} " in prof
