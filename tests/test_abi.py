@@ -114,3 +114,19 @@ def test_batch_rejects_bad_item_counts_without_a_gpu(L):
     assert L.lbp_decode_batch(items, 0, None, 0, None) == lbp.LBP_EINVAL
     assert L.lbp_decode_batch(None, 1, None, 0, None) == lbp.LBP_EINVAL
     assert L.lbp_server_set_batching(None, 4) == lbp.LBP_EINVAL
+
+
+def test_empty_and_negative_batches_without_gpu(L):
+    """num_shots = 0 is a valid empty decode: LBP_OK with nothing enqueued and
+    no buffer read, before any CUDA call.  A negative count, or a non-empty
+    batch with a missing buffer, is LBP_EINVAL, also before any CUDA call."""
+    p = lbp.lbp_params_default(osd=1)
+    code = ctypes.c_void_p(1)
+    decode_like = (L.lbp_decode, L.lbp_decode_host)
+    for fn in decode_like:
+        assert fn(code, ctypes.byref(p), 0, None, None, None, None, None, None, None, 0, None) == lbp.LBP_OK
+        assert fn(code, ctypes.byref(p), -1, None, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
+        assert fn(code, ctypes.byref(p), 4, None, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_tune(code, ctypes.byref(p), 0, None, None, None, None, None, None, 0, None) == lbp.LBP_OK
+    assert L.lbp_tune(code, ctypes.byref(p), -1, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
+    assert L.lbp_tune(code, ctypes.byref(p), 4, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
