@@ -10,6 +10,8 @@ tests (bit-identical decisions, LLRs to 1e-5 relative).  The file sorts last
 so that a run stopping at the first failure has already run the others; it
 also passes on its own in a fresh process.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -87,4 +89,7 @@ def test_noalloc_rejects_requests_beyond_its_area():
         lbp.lbp_decode_noalloc(dec.code, prm, B, s, out.err, out.converged, out.osd, out.iters,
                                None, None)
     assert ei.value.code == lbp.LBP_E2BIG
+    # An empty batch is a valid decode that enqueues nothing.
+    assert lbp.lib().lbp_decode_noalloc(dec.code.ptr, ctypes.byref(prm), 0, None, None, None, None, None,
+                                        None, None) == lbp.LBP_OK
     dec.close()
