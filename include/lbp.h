@@ -223,8 +223,12 @@ size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_
  *   workspace        lbp_workspace_size() bytes, 256-byte aligned, owned by the
  *                    caller; contents on entry are ignored.
  * Shot b's result depends only on its syndrome, the code, the parameters and
- * shot_offset + b (not on num_shots or on other shots).  Errors: LBP_EINVAL,
- * LBP_ENOMEM (workspace too small), LBP_ENOSYS, LBP_ECUDA. */
+ * shot_offset + b (not on num_shots or on other shots).  num_shots = 0 is an
+ * empty decode: LBP_OK, nothing enqueued, no buffer read (lbp_decode_host,
+ * lbp_tune and lbp_decode_noalloc do the same; lbp_graph_create and
+ * lbp_server_submit want at least one shot).  Errors: LBP_EINVAL (also
+ * num_shots < 0 or above 2^31), LBP_ENOMEM (workspace too small), LBP_ENOSYS,
+ * LBP_ECUDA. */
 int lbp_decode(const lbp_code *code, const lbp_params *params, int64_t num_shots,
                const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                uint8_t *osd_out, int32_t *iters_out, float *llr_out,
