@@ -272,7 +272,9 @@ size_t lbp_host_workspace_size(const lbp_code *code, const lbp_params *params, i
  * (events keep the copies after `stream`'s earlier work and `stream`'s later
  * work after the copies); results are those of one call.  Pinned host memory
  * makes the copies asynchronous; the caller synchronises the stream before
- * reading the outputs. */
+ * reading the outputs.  On an error after copies were queued, `stream` is
+ * still ordered after every one of them, so once it has drained the caller
+ * may reuse its buffers and the workspace. */
 int lbp_decode_host(const lbp_code *code, const lbp_params *params, int64_t num_shots,
                     const uint64_t *syndromes, uint64_t *err_out, uint8_t *converged,
                     uint8_t *osd_out, int32_t *iters_out, float *llr_out,

@@ -944,6 +944,13 @@ extern "C" int lbp_decode_host(const lbp_code *code, const lbp_params *params, i
     }
     ok = ok && cudaEventRecord(ev_end, cs.out) == cudaSuccess;
     ok = ok && cudaStreamWaitEvent(s, ev_end, 0) == cudaSuccess;
+    if (rc || !ok) {
+        // The pipeline stopped early: order the caller's stream after every
+        // copy already queued on the copy streams, so that the caller may
+        // reuse its buffers and the workspace once its stream has drained.
+        for (cudaStream_t q : {cs.in, cs.out})
+            if (cudaEventRecord(ev_start, q) == cudaSuccess) cudaStreamWaitEvent(s, ev_start, 0);
+    }
     release();
     if (rc) return rc;
     if (!ok) { cudaGetLastError(); return LBP_ECUDA; }
