@@ -62,7 +62,9 @@ struct Request {
     uint8_t *conv, *osd;
     int32_t *iters;
     Clock::time_point submitted;
+    int64_t fit_chunk = 0;              // shots per launch whose layout was checked against the arena
     // While in flight:
+    int64_t chunk = 0;                  // shots per launch, fixed at admission
     int slot = -1;
     size_t arena_off = 0, arena_bytes = 0;
     int status = LBP_OK;
@@ -168,7 +170,7 @@ void launch(lbp_server *s, int si) {
     Slot &sl = s->slots[si];
     Request &r = sl.req;
     const int64_t B = r.shots;
-    const int64_t chunk = chunk_shots(r.code, s->chunk_work, B);
+    const int64_t chunk = r.chunk;
     Layout L;
     request_layout(r.code, &r.params, B, chunk, &L);
     uint8_t *base = s->arena_base + r.arena_off;
@@ -386,12 +388,21 @@ void run(lbp_server *s) {
                 }
             }
             Request &r = s->waiting.front();
+            // The chunk size of the policy in force now; when lbp_server_configure
+            // has grown it since submission past what the arena holds, the size
+            // checked at submission.
+            int64_t chunk = chunk_shots(r.code, s->chunk_work, r.shots);
             Layout L;
-            request_layout(r.code, &r.params, r.shots, chunk_shots(r.code, s->chunk_work, r.shots), &L);
+            request_layout(r.code, &r.params, r.shots, chunk, &L);
+            if (L.total > s->arena.size) {
+                chunk = r.fit_chunk;
+                request_layout(r.code, &r.params, r.shots, chunk, &L);
+            }
             size_t off = 0;
             if (!s->arena.alloc(L.total, &off)) break;           // wait for memory to free up
             Slot &sl = s->slots[free_slot];
             sl.req = r;
+            sl.req.chunk = chunk;
             sl.req.arena_off = off;
             sl.req.arena_bytes = L.total;
             sl.req.slot = free_slot;
@@ -478,7 +489,8 @@ extern "C" int lbp_server_submit(lbp_server *s, const lbp_code *code, const lbp_
     if (code->device != s->device) return LBP_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     Layout L;
-    if (!request_layout(code, params, num_shots, chunk_shots(code, s->chunk_work, num_shots), &L))
+    const int64_t fit_chunk = chunk_shots(code, s->chunk_work, num_shots);
+    if (!request_layout(code, params, num_shots, fit_chunk, &L))
         return LBP_EINVAL;
     if (L.total > s->arena.size) return LBP_E2BIG;            // can never be admitted
     if (s->stop) return LBP_EINVAL;
@@ -493,6 +505,7 @@ extern "C" int lbp_server_submit(lbp_server *s, const lbp_code *code, const lbp_
     r.osd = osd_out;
     r.iters = iters_out;
     r.submitted = Clock::now();
+    r.fit_chunk = fit_chunk;
     s->waiting.push_back(r);
     s->known[r.ticket] = true;
     *ticket = r.ticket;

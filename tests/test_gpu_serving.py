@@ -227,3 +227,45 @@ def test_requests_that_cannot_merge_run_alone():
         assert np.array_equal(b["err"], e) and np.array_equal(b["conv"], c), i
         assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it), i
     dec.close()
+
+
+def test_configure_after_submission_keeps_a_launch_size_that_fits():
+    """Two long requests whose layout fits the arena only as 69-shot launches:
+    the first holds the arena while the second waits, then
+    lbp_server_configure turns chunking off.  The waiting request cannot take
+    one launch for all its shots (that layout exceeds the arena), so it runs
+    with the launch size checked when it was submitted.  Results equal the
+    requests decoded alone."""
+    hx, _ = bb_code("bb144")
+    pri = np.full(hx.n, 0.02)
+    dec = Decoder(hx, pri)
+    chunk_work = 30000
+    chunk = chunk_work // hx.nnz
+    big = 20000
+    reqs = []
+    for i in range(2):
+        _, syn = sampler.sample(hx, pri, seed=70 + i, num_shots=big, shot_offset=50_000 * i)
+        reqs.append(dict(syn=syn, prm=dec.params(max_iter=60, lottery=1, osd=1, seed=5,
+                                                 shot_offset=50_000 * i)))
+    ref = []
+    for r in reqs:
+        out = dec.decode(torch.from_numpy(r["syn"].view(np.int64)).cuda(), r["prm"])
+        torch.cuda.synchronize()
+        ref.append((out.err.cpu().numpy().view(np.uint64), out.converged.cpu().numpy(),
+                    out.osd.cpu().numpy(), out.iters.cpu().numpy()))
+    arena = _al256(_single_layout_bytes(dec, reqs[0]["prm"], big, chunk) * 5 // 4)
+    assert lbp.lbp_workspace_size(dec.code, reqs[0]["prm"], big) > arena
+    srv = lbp.lbp_server_create(arena, 2)
+    lbp.lbp_server_configure(srv, chunk_work, True)
+    bufs = [dict(err=np.zeros((big, (hx.n + 63) // 64), np.uint64), conv=np.zeros(big, np.uint8),
+                 osd=np.zeros(big, np.uint8), iters=np.zeros(big, np.int32)) for _ in reqs]
+    tickets = [lbp.lbp_server_submit(srv, dec.code, r["prm"], big, r["syn"], b["err"], b["conv"],
+                                     b["osd"], b["iters"]) for r, b in zip(reqs, bufs)]
+    lbp.lbp_server_configure(srv, 0, False)
+    _poll_all(srv, tickets)
+    srv.close()
+    for i, (e, c, o, it) in enumerate(ref):
+        b = bufs[i]
+        assert np.array_equal(b["err"], e) and np.array_equal(b["conv"], c), i
+        assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it), i
+    dec.close()
