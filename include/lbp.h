@@ -161,10 +161,12 @@ int lbp_code_options(const lbp_code *code, int32_t *graph, int32_t *groups, int3
  * (code NULL). */
 int lbp_code_osd_form(const lbp_code *code, int32_t *dense, int32_t *rank);
 
-/* Release a code object (synchronous; no call using it may be in flight). */
+/* Release a code object (synchronous; no call using it may be in flight).
+ * Errors: LBP_EINVAL (code NULL). */
 int lbp_free_code(lbp_code *code);
 
-/* Sizes of a loaded code (any pointer may be NULL). */
+/* Sizes of a loaded code (any output pointer may be NULL).  Errors:
+ * LBP_EINVAL (code NULL). */
 int lbp_code_info(const lbp_code *code, int32_t *m, int32_t *n, int32_t *nnz);
 
 /* Whether lbp_load_code recognised H as the space-time matrix (Eq. 1) of the
@@ -212,6 +214,12 @@ int lbp_code_rounds(const lbp_code *code, int32_t *T, int32_t *m_r, int32_t *n_r
 size_t lbp_workspace_size(const lbp_code *code, const lbp_params *params, int64_t num_shots);
 
 /* Decode num_shots syndromes on `stream` (a cudaStream_t, NULL = legacy default).
+ * Every shot runs the BP of Alg. 1 with the check-node rule params->rule
+ * (normalised min-sum by default; messages stored as params->msg),
+ * with the lottery sign flip of Alg. 3 (or the policy params->lottery_policy
+ * names) when params->lottery is set, and stops at the first iteration whose
+ * hard decision reproduces s.  When params->osd is set, the shots that did
+ * not converge then take OSD-0 (Alg. 2) on their final posteriors.
  *
  * Device buffers, all [num_shots][...] row-major:
  *   syndromes   in   [B][ceil(m/64)] uint64, packed s
@@ -372,13 +380,17 @@ int lbp_server_submit(lbp_server *server, const lbp_code *code, const lbp_params
 /* Non-blocking: *done = 1 once the request's outputs are in its host buffers,
  * then *latency_s (nullable) is submission-to-completion time in seconds and
  * the return value is the request's status; a completed ticket is forgotten
- * after it has been reported once. */
+ * after it has been reported once.  Errors: LBP_EINVAL (server or done NULL,
+ * a ticket never issued or already reported). */
 int lbp_server_poll(lbp_server *server, int64_t ticket, int *done, double *latency_s);
 
-/* Blocking version of lbp_server_poll. */
+/* Blocking version of lbp_server_poll, with its errors.  When several
+ * callers wait on one ticket, one of them gets the request's status and the
+ * others LBP_EINVAL. */
 int lbp_server_wait(lbp_server *server, int64_t ticket, double *latency_s);
 
-/* Drain every queued and in-flight request, then release the server. */
+/* Drain every queued and in-flight request, then release the server.
+ * Errors: LBP_EINVAL (server NULL). */
 int lbp_server_destroy(lbp_server *server);
 
 /* Same decode as lbp_decode, for callers that cannot allocate device memory
@@ -431,7 +443,8 @@ int lbp_graph_create(const lbp_code *code, const lbp_params *params, int64_t num
 /* Replay the captured decode on `stream` (a cudaStream_t, NULL = legacy
  * default).  Replays of one graph must not overlap each other. */
 int lbp_graph_launch(lbp_graph *graph, void *stream);
-/* Release the graph (not its buffers).  Replays already launched finish. */
+/* Release the graph (not its buffers).  Replays already launched finish.
+ * Errors: LBP_EINVAL (graph NULL). */
 int lbp_graph_destroy(lbp_graph *graph);
 
 /* Kernel timing instrumentation, off by default.  While enabled, every

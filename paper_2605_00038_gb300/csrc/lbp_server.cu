@@ -524,6 +524,7 @@ extern "C" int lbp_server_poll(lbp_server *s, int64_t ticket, int *done, double 
     const int st = it->second.first;
     s->finished.erase(it);
     s->known.erase(ticket);
+    s->cv_done.notify_all();                              // waiters on this ticket
     return st;
 }
 
@@ -531,12 +532,14 @@ extern "C" int lbp_server_wait(lbp_server *s, int64_t ticket, double *latency_s)
     if (!s) return LBP_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     if (!s->known.count(ticket)) return LBP_EINVAL;
-    s->cv_done.wait(lk, [&] { return s->finished.count(ticket) > 0; });
+    s->cv_done.wait(lk, [&] { return s->finished.count(ticket) > 0 || !s->known.count(ticket); });
     auto it = s->finished.find(ticket);
+    if (it == s->finished.end()) return LBP_EINVAL;      // another caller collected it meanwhile
     if (latency_s) *latency_s = it->second.second;
     const int st = it->second.first;
     s->finished.erase(it);
     s->known.erase(ticket);
+    s->cv_done.notify_all();                              // other waiters on this ticket
     return st;
 }
 

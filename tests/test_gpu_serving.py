@@ -269,3 +269,31 @@ def test_configure_after_submission_keeps_a_launch_size_that_fits():
         assert np.array_equal(b["err"], e) and np.array_equal(b["conv"], c), i
         assert np.array_equal(b["osd"], o) and np.array_equal(b["iters"], it), i
     dec.close()
+
+
+def test_two_waiters_on_one_ticket():
+    """Two host threads wait on one ticket: one gets the request's status,
+    the other LBP_EINVAL, and neither blocks for good."""
+    hx, _ = bb_code("bb72")
+    pri = np.full(hx.n, 0.03)
+    dec = Decoder(hx, pri)
+    B = 2000
+    _, syn = sampler.sample(hx, pri, seed=80, num_shots=B)
+    srv = lbp.lbp_server_create(64 << 20, 2)
+    buf = dict(err=np.zeros((B, (hx.n + 63) // 64), np.uint64), conv=np.zeros(B, np.uint8),
+               osd=np.zeros(B, np.uint8), iters=np.zeros(B, np.int32))
+    t = lbp.lbp_server_submit(srv, dec.code, dec.params(osd=1), B, syn, buf["err"], buf["conv"],
+                              buf["osd"], buf["iters"])
+    codes = []
+    th = [threading.Thread(target=lambda: codes.append(lbp.lib().lbp_server_wait(srv.ptr, t, None)),
+                           daemon=True) for _ in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join(timeout=120)
+    if any(x.is_alive() for x in th):
+        srv.ptr = ctypes.c_void_p()
+        pytest.fail("a waiter never returned")
+    srv.close()
+    assert sorted(codes) == sorted([lbp.LBP_OK, lbp.LBP_EINVAL])
+    dec.close()
