@@ -389,8 +389,11 @@ int lbp_server_poll(lbp_server *server, int64_t ticket, int *done, double *laten
  * others LBP_EINVAL. */
 int lbp_server_wait(lbp_server *server, int64_t ticket, double *latency_s);
 
-/* Drain every queued and in-flight request, then release the server.
- * Errors: LBP_EINVAL (server NULL). */
+/* Drain every queued and in-flight request, then release the server.  No
+ * other call on the server may be running (a thread blocked in
+ * lbp_server_wait included) or follow.  Tickets not yet collected are
+ * dropped; their outputs are in their host buffers.  Errors: LBP_EINVAL
+ * (server NULL). */
 int lbp_server_destroy(lbp_server *server);
 
 /* Same decode as lbp_decode, for callers that cannot allocate device memory
