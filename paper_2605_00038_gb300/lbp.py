@@ -281,6 +281,26 @@ def _hptr(a):
     return a.data_ptr()
 
 
+def _nbytes(buf) -> int:
+    if isinstance(buf, np.ndarray):
+        return buf.nbytes
+    return buf.numel() * buf.element_size()
+
+
+def _check_io(code: Code, num_shots: int, syndromes, err_out, converged, osd_out, iters_out, llr_out=None):
+    """Every per-shot buffer holds at least num_shots rows of its documented
+    shape, so no kernel or copy of the call runs past a buffer's end; the
+    library itself sees only pointers.  None buffers are the library's to
+    accept or refuse."""
+    B = max(int(num_shots), 0)
+    wm, wn = (code.m + 63) // 64, (code.n + 63) // 64
+    for name, buf, need in (("syndromes", syndromes, 8 * wm * B), ("err_out", err_out, 8 * wn * B),
+                            ("converged", converged, B), ("osd_out", osd_out, B),
+                            ("iters_out", iters_out, 4 * B), ("llr_out", llr_out, 4 * code.n * B)):
+        if buf is not None and _nbytes(buf) < need:
+            raise ValueError(f"{name} holds {_nbytes(buf)} bytes; {num_shots} shots need {need}")
+
+
 def _stream_handle(stream):
     if stream is None:
         import torch
@@ -291,6 +311,7 @@ def _stream_handle(stream):
 def lbp_decode(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
                osd_out, iters_out, llr_out, workspace, stream=None):
     """Enqueue a decode on `stream` (default: torch's current stream)."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out, llr_out)
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(lib().lbp_decode(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
                             _dptr(err_out), _dptr(converged), _dptr(osd_out), _dptr(iters_out),
@@ -301,6 +322,7 @@ def lbp_decode(code: Code, params: lbp_params, num_shots: int, syndromes, err_ou
 def lbp_decode_host(code: Code, params: lbp_params, num_shots: int, syndromes, err_out,
                     converged, osd_out, iters_out, llr_out, workspace, stream=None):
     """Host-buffer variant: copies in, decodes and copies out on `stream`."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out, llr_out)
     ws_bytes = workspace.numel() * workspace.element_size()
     _check(lib().lbp_decode_host(code.ptr, ctypes.byref(params), num_shots, _hptr(syndromes),
                                  _hptr(err_out), _hptr(converged), _hptr(osd_out),
@@ -312,6 +334,7 @@ def lbp_decode_host(code: Code, params: lbp_params, num_shots: int, syndromes, e
 def lbp_tune(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
              osd_out, iters_out, workspace, stream=None):
     """Time each BP launch shape on this batch and keep the fastest in `code`."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out)
     ws_bytes = workspace.numel() * workspace.element_size()
     _check(lib().lbp_tune(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
                           _dptr(err_out), _dptr(converged), _dptr(osd_out), _dptr(iters_out),
@@ -322,6 +345,7 @@ def lbp_decode_noalloc(code: Code, params: lbp_params, num_shots: int, syndromes
                        converged, osd_out, iters_out, llr_out, stream=None):
     """lbp_decode without a workspace: scratch is the library's fixed device
     array (for callers that cannot allocate device memory)."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out, llr_out)
     _check(lib().lbp_decode_noalloc(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
                                     _dptr(err_out), _dptr(converged), _dptr(osd_out),
                                     _dptr(iters_out), _dptr(llr_out), _stream_handle(stream)),
@@ -333,6 +357,7 @@ def batch_items(entries):
     err_out, converged, osd_out, iters_out) tuples of CUDA tensors."""
     arr = (lbp_batch_item * len(entries))()
     for i, (code, prm, B, syn, err, conv, osd, iters) in enumerate(entries):
+        _check_io(code, B, syn, err, conv, osd, iters)
         arr[i] = lbp_batch_item(code.ptr, prm, B, _dptr(syn), _dptr(err), _dptr(conv), _dptr(osd), _dptr(iters))
     return arr
 
@@ -383,6 +408,7 @@ class Graph:
 def lbp_graph_create(code: Code, params: lbp_params, num_shots: int, syndromes, err_out, converged,
                      osd_out, iters_out, llr_out, workspace) -> Graph:
     """Capture the decode lbp_decode would run for these device buffers."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out, llr_out)
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     out = ctypes.c_void_p()
     _check(lib().lbp_graph_create(code.ptr, ctypes.byref(params), num_shots, _dptr(syndromes),
@@ -433,6 +459,7 @@ def lbp_server_submit(server: Server, code: Code, params: lbp_params, num_shots:
                       err_out, converged, osd_out, iters_out) -> int:
     """Queue a decode with host buffers; returns the ticket.  The buffers must
     stay alive (and unchanged) until the request completes."""
+    _check_io(code, num_shots, syndromes, err_out, converged, osd_out, iters_out)
     t = ctypes.c_int64()
     _check(lib().lbp_server_submit(server.ptr, code.ptr, ctypes.byref(params), num_shots,
                                    _hptr(syndromes), _hptr(err_out), _hptr(converged),

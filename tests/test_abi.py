@@ -130,3 +130,28 @@ def test_empty_and_negative_batches_without_gpu(L):
     assert L.lbp_tune(code, ctypes.byref(p), 0, None, None, None, None, None, None, 0, None) == lbp.LBP_OK
     assert L.lbp_tune(code, ctypes.byref(p), -1, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
     assert L.lbp_tune(code, ctypes.byref(p), 4, None, None, None, None, None, None, 0, None) == lbp.LBP_EINVAL
+
+
+def test_buffer_sizes_are_checked_before_the_library():
+    """The binding refuses a per-shot buffer shorter than num_shots rows of
+    its documented shape before any library call: the library sees only
+    pointers, and a short buffer would let a kernel or a copy run past it."""
+    torch = pytest.importorskip("torch")
+    code = lbp.Code(0, 72, 144, 432)   # m = 72: 2 syndrome words; n = 144: 3 error words
+    B = 5
+    ok = dict(syndromes=np.zeros((B, 2), np.uint64), err_out=np.zeros((B, 3), np.uint64),
+              converged=np.zeros(B, np.uint8), osd_out=np.zeros(B, np.uint8),
+              iters_out=torch.zeros(B, dtype=torch.int32), llr_out=torch.zeros((B, 144)))
+    lbp._check_io(code, B, **ok)
+    lbp._check_io(code, 0, None, None, None, None, None)
+    for k in ok:
+        short = dict(ok, **{k: ok[k][:B - 1]})
+        with pytest.raises(ValueError, match=k):
+            lbp._check_io(code, B, **short)
+    p = lbp.lbp_params_default()
+    with pytest.raises(ValueError, match="err_out"):
+        lbp.lbp_server_submit(None, code, p, B, ok["syndromes"], ok["err_out"][:2], ok["converged"],
+                              None, ok["iters_out"])
+    with pytest.raises(ValueError, match="syndromes"):
+        lbp.lbp_decode_host(code, p, B, ok["syndromes"][:1], ok["err_out"], ok["converged"], None,
+                            ok["iters_out"], None, None)
