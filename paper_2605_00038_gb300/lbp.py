@@ -181,6 +181,8 @@ def lbp_load_code(m: int, n: int, row_ptr, col_idx, priors) -> Code:
     pr = np.ascontiguousarray(priors, dtype=np.float64)
     if rp.shape != (m + 1,) or pr.shape != (n,):
         raise ValueError("row_ptr must have m+1 entries and priors n entries")
+    if ci.ndim != 1 or ci.size < rp[-1]:
+        raise ValueError(f"col_idx holds {ci.size} entries; row_ptr[m] = {rp[-1]} are read")
     out = ctypes.c_void_p()
     _check(lib().lbp_load_code(m, n, rp.ctypes.data, ci.ctypes.data if ci.size else None,
                                pr.ctypes.data if pr.size else None, ctypes.byref(out)),

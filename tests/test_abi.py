@@ -60,6 +60,12 @@ def test_load_code_rejects_malformed_input(L, rows, n, pri):
     assert ei.value.code == lbp.LBP_EINVAL
 
 
+def test_load_code_refuses_short_col_idx(L):
+    # row_ptr[m] = 4 column indices are read; three are given.
+    with pytest.raises(ValueError, match="col_idx"):
+        lbp.lbp_load_code(2, 4, np.array([0, 2, 4]), np.array([0, 1, 2]), np.full(4, 0.1))
+
+
 def test_rejects_row_heavier_than_32(L):
     n = 33
     with pytest.raises(lbp.LbpError):
